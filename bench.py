@@ -1,0 +1,363 @@
+"""K-truss benchmark: Medges/s at fixed K on one GB300 (JSON line on stdout).
+
+Workload (default): R-MAT scale 20, edge factor 16, (a,b,c,d) = (.57,.19,.19,.05),
+symmetrised, de-duplicated, upper-triangular int32 CSR with original vertex ids,
+seed 0; K = 3.  A step is one whole K-truss computation (every peel round:
+support, prune, compaction, convergence test, final outputs) of that graph.
+
+  value     = edges / device time of ktruss_run, graph resident in HBM
+  e2e       = the same metric through the public C ABI with host buffers:
+              ktruss_load_csr from pinned host memory + ktruss_run with pinned
+              host outputs + ktruss_free, all inside the timed region
+  roofline  = the support step (dominant) against measured HBM bandwidth, with
+              algorithmic bytes per round 4*W + 8*m + 16*T + 8*(n+1)
+              (W = sum over live edges of tail + row-kappa lengths)
+  cpu_baseline = the CPU oracle, single thread, on a bounded sample
+
+Between timed steps L2 is flushed by writing a buffer larger than L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload rmat20|rmat20r|rmat23c|er2000] [--K 3] [--kernel balanced|edge]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "K-truss Medges/s at fixed K on 1 GB300"
+UNIT = "Medges/s"
+WORKLOAD_DESC = {
+    "rmat20": "RMAT scale 20, edge factor 16, a=.57 b=.19 c=.19 d=.05, original ids, seed 0",
+    "rmat20r": "RMAT scale 20, edge factor 16, degree-ascending relabel, seed 0",
+    "rmat23c": "RMAT scale 23, edge factor 16, 64 planted cliques 20..200, seed 0",
+    "er2000": "Erdos-Renyi G(n=2000, m=16000), seed 0",
+}
+CPU_SAMPLE = ("rmat", 17)  # oracle sample: R-MAT scale 17, same recipe, full K-truss run
+L2_FLUSH_BYTES = 512 << 20
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def algorithmic_bytes(n, live, merge, tris):
+    return 4 * merge + 8 * live + 16 * tris + 8 * (n + 1)
+
+
+def traffic_record():
+    """Per-launch DRAM traffic of the support step from the committed ncu
+    summary, if it was taken on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "support_traffic.json")
+    try:
+        with open(p) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    src = os.path.join(ROOT, "paper_2009_07929_gb300", "csrc", "support_balanced.cu")
+    with open(src, "rb") as f:
+        h = hashlib.sha256(f.read()).hexdigest()
+    if rec.get("source_sha256") != h:
+        return None
+    return rec
+
+
+def cpu_baseline(seconds_cap=30.0):
+    import graphgen as gg
+    import oracle
+    g = gg.rmat(CPU_SAMPLE[1], 16, 0)
+    runs, t0 = 0, time.perf_counter()
+    while True:
+        oracle.ktruss(g.row_ptr, g.col, 3)
+        runs += 1
+        el = time.perf_counter() - t0
+        if el > seconds_cap / 3 or runs >= 3:
+            break
+    return {"value": round(g.m * runs / el / 1e6, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"full K=3 run of the single-thread C oracle on R-MAT scale {CPU_SAMPLE[1]}, "
+                      f"edge factor 16 (same recipe, {g.m} edges), {runs} run(s), "
+                      f"{el:.1f} s on {os.cpu_count()} host cores (1 used)"}
+
+
+def run_reference(args, world, rank):
+    """Reference arm: the CPU oracle as it stands, on a bounded sample."""
+    if rank != 0:
+        return
+    import graphgen as gg
+    import oracle
+    oracle.build()
+    g = gg.rmat(CPU_SAMPLE[1], 16, 0)
+    for _ in range(args.warmup):
+        oracle.ktruss(g.row_ptr, g.col, args.K)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.ktruss(g.row_ptr, g.col, args.K)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = g.m * args.steps / tot / 1e6
+    sample = (f"each step: full K={args.K} run of the single-thread C oracle on R-MAT scale "
+              f"{CPU_SAMPLE[1]}, edge factor 16 (same recipe as the workload, {g.m} edges)")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1000 * tot / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC[args.workload] + f", K={args.K}",
+                   "reference_sample": f"rmat{CPU_SAMPLE[1]}", "K": args.K},
+        "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rmat20", choices=sorted(WORKLOAD_DESC))
+    ap.add_argument("--K", type=int, default=3)
+    ap.add_argument("--kernel", default="balanced", choices=["balanced", "edge"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world, rank, local = dist_setup()
+
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import numpy as np
+    import torch
+
+    import graphgen as gg
+    import paper_2009_07929_gb300 as kt
+
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    lib = kt.lib()
+    g = gg.cached_workload(args.workload, 0)
+    n, m = g.n, g.m
+    dev = torch.device("cuda", local)
+    rp_d = torch.from_numpy(g.row_ptr).to(dev)
+    col_d = torch.from_numpy(g.col).to(dev)
+    h = kt.load(rp_d, col_d)
+    h.set_kernel(kt.KERNEL_BALANCED if args.kernel == "balanced" else kt.KERNEL_EDGE)
+    mask = torch.empty(m, dtype=torch.uint8, device=dev)
+    sup = torch.empty(m, dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        h.run(args.K, out=(mask, sup))
+
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        step()
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    sup_ms, sup_launches, bytes_alg, launches, st = 0.0, 0, 0, 0, None
+    with ClockSampler(local) as clk:
+        wall0 = time.perf_counter()
+        for i in range(args.steps):
+            flush.fill_(i)
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+            st = h.stats()
+            launches += st.kernel_launches
+            sup_ms += sum(st.ms_support_per_round)
+            sup_launches += st.support_launches
+            bytes_alg += sum(algorithmic_bytes(n, lv, mw, tr) for lv, mw, tr in
+                             zip(st.live_per_round, st.merge_work_per_round,
+                                 st.triangles_per_round))
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    tot_ms = sum(step_ms)
+    if pg:
+        t = torch.tensor([tot_ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        tot_ms = float(t.item())
+        pg.barrier()
+    torch.cuda.synchronize()
+    value = world * m * args.steps / (tot_ms / 1000.0) / 1e6
+
+    # ---- e2e through the C ABI with pinned host buffers
+    rp_h = torch.from_numpy(g.row_ptr).pin_memory()
+    col_h = torch.from_numpy(g.col).pin_memory()
+    mask_h = torch.empty(m, dtype=torch.uint8).pin_memory()
+    sup_h = torch.empty(m, dtype=torch.int32).pin_memory()
+    st_ptr = kt._stream_ptr()
+
+    def e2e_step():
+        hh = ctypes_load(lib, rp_h, col_h, n, m, st_ptr)
+        rc = lib.ktruss_run(hh, args.K, mask_h.data_ptr(), sup_h.data_ptr(), kt.HOST, st_ptr)
+        if rc != 0:
+            raise kt.KtrussError(rc, "ktruss_run")
+        lib.ktruss_free(hh)
+
+    for _ in range(2):
+        e2e_step()
+    e2e_times = []
+    for i in range(max(3, min(args.steps, 5))):
+        flush.fill_(i)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_step()
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_s = sum(e2e_times) / len(e2e_times)
+    if pg:
+        t = torch.tensor([e2e_s], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * m / e2e_s / 1e6
+
+    if rank != 0:
+        if pg:
+            pg.destroy_process_group()
+        return
+
+    peak, peak_kind = peaks()
+    sup_avg_ms = sup_ms / max(sup_launches, 1)
+    bytes_per_launch = bytes_alg / max(sup_launches, 1)
+    achieved = bytes_per_launch / (sup_avg_ms / 1000.0) / 1e9 if sup_avg_ms > 0 else None
+    tr = traffic_record()
+    roofline = {
+        "bound": "hbm", "achieved": round(achieved, 1) if achieved else None, "peak": peak,
+        "unit": "GB/s", "frac": round(achieved / peak, 4) if achieved else None,
+        "traffic": (int(tr["dram_bytes_per_launch"]) if tr else None),
+        "peak_kind": f"{peak_kind} (HBM copy)",
+        "kernel": "support step (support_short_kernel + support_long_kernel)",
+        "support_ms_per_launch": round(sup_avg_ms, 4),
+        "alg_bytes_per_launch": int(bytes_per_launch),
+    }
+    if tr:
+        roofline["dram_frac"] = round(tr["dram_bytes_per_launch"] / (sup_avg_ms / 1e3) / 1e9 / peak, 4)
+    out = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tot_ms / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC[args.workload] + f", K={args.K}", "K": args.K,
+                   "n": n, "m": m, "rounds": st.rounds, "kernel": args.kernel,
+                   "parallelism": f"replicas{world}", "l2": "flushed between steps (512 MiB write)"},
+        "e2e": {"value": round(e2e_value, 2), "unit": UNIT,
+                "h2d_bytes_per_step": 4 * (n + 1) + 4 * m, "d2h_bytes_per_step": 5 * m},
+        "gpu_launches": launches,
+        "roofline": roofline,
+        "clocks": clk.summary(),
+        "wall_s_timed": round(wall, 3),
+    }
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(out), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
+def ctypes_load(lib, rp_h, col_h, n, m, stream_ptr):
+    import ctypes
+    hh = ctypes.c_void_p(0)
+    rc = lib.ktruss_load_csr(ctypes.byref(hh), n, m, rp_h.data_ptr(), col_h.data_ptr(), 0,
+                             stream_ptr)
+    if rc != 0:
+        import paper_2009_07929_gb300 as kt
+        raise kt.KtrussError(rc, "ktruss_load_csr")
+    return hh
+
+
+if __name__ == "__main__":
+    main()

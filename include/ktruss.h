@@ -1,0 +1,151 @@
+/*
+ * ktruss.h: C ABI of the GB300 (sm_103a) K-truss library, libktruss.so.
+ *
+ * Method: fine-grained Eager K-truss (M. Blanco, T. M. Low, K. Kim, "Exploration
+ * of Fine-Grained Parallelism for Load Balancing Eager K-truss on GPU and CPU",
+ * HPEC 2019).  The K-truss of an undirected graph is its largest subgraph in
+ * which every edge lies in at least K-2 triangles of that subgraph (Sec. I).
+ * It is reached by Alg. 1: compute the support of every live edge, remove every
+ * edge whose support is below K-2, repeat until a round removes nothing.
+ * Supports are computed per edge task (Alg. 3): edge (i, kappa) intersects the
+ * part of row i after kappa with row kappa, and every common column w credits
+ * the three edges (i,kappa), (i,w), (kappa,w) (the eager rule of Sec. II-B).
+ *
+ * Graph format (Sec. II-B, Sec. III-D): strictly upper-triangular CSR.
+ *   row_ptr  int32[n+1], row_ptr[0] = 0, non-decreasing, row_ptr[n] = m
+ *   col      int32[m],   row_ptr[i] <= p < row_ptr[i+1] => i < col[p] < n,
+ *                        columns strictly increasing within a row
+ * Edge e is CSR slot e; every per-edge output is indexed by that slot.
+ * Limits: 0 <= n < 2^31, 0 <= m < 2^31.
+ *
+ * Memory kinds: KTRUSS_HOST means ordinary (pageable or pinned) host memory,
+ * KTRUSS_DEVICE means device memory of the current CUDA device.  Device-side
+ * work is issued on `cuda_stream` (a cudaStream_t; NULL = the legacy default
+ * stream).  Every call returns after the work it issued has completed, so
+ * outputs may be read, and inputs freed, as soon as it returns.
+ *
+ * Errors: every int-returning call returns KTRUSS_OK (0) or a negative code;
+ * no C++ exception crosses this boundary.  ktruss_strerror() names a code, and
+ * ktruss_last_cuda_error() gives the CUDA error behind the last KTRUSS_ECUDA
+ * of the calling thread.
+ *
+ * Threads: a graph handle may be used by one call at a time; a call that finds
+ * the handle in use returns KTRUSS_EBUSY.  Distinct handles are independent.
+ */
+#ifndef KTRUSS_H
+#define KTRUSS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define KTRUSS_OK 0
+#define KTRUSS_EINVAL (-1)   /* bad argument or malformed CSR */
+#define KTRUSS_ENOMEM (-2)   /* device or host allocation failed */
+#define KTRUSS_ECUDA (-3)    /* a CUDA runtime call failed */
+#define KTRUSS_ETIMEOUT (-4) /* a bounded device wait gave up */
+#define KTRUSS_EBUSY (-5)    /* handle in use by another call */
+
+#define KTRUSS_HOST 0
+#define KTRUSS_DEVICE 1
+
+/* Support kernels selectable with KTRUSS_OPT_SUPPORT_KERNEL. */
+#define KTRUSS_KERNEL_BALANCED 0 /* work-prefix balancer + staged warp intersection (default) */
+#define KTRUSS_KERNEL_EDGE 1     /* one thread per edge, two-pointer merge (Alg. 3 task as-is) */
+
+/* Option keys for ktruss_set_option. */
+#define KTRUSS_OPT_SUPPORT_KERNEL 1 /* KTRUSS_KERNEL_* */
+#define KTRUSS_OPT_TIMING 2         /* 1 = record per-phase CUDA events (default 1) */
+
+typedef struct ktruss_graph ktruss_graph; /* opaque, library-owned */
+
+/* Statistics of the last ktruss_run on a handle (Alg. 1 bookkeeping). */
+typedef struct {
+    int32_t rounds;            /* executions of the support step (Alg. 1 Step 1) */
+    int64_t edges_in;          /* m */
+    int64_t edges_out;         /* edges in the K-truss */
+    int64_t triangles_out;     /* triangles of the K-truss */
+    int32_t per_round_len;     /* = rounds */
+    const int64_t *removed_per_round;   /* [rounds] edges removed by each round */
+    const int64_t *live_per_round;      /* [rounds] live edges entering each round */
+    const int64_t *triangles_per_round; /* [rounds] triangles found by each support step */
+    const float *ms_support_per_round;  /* [rounds] support kernel time (timing on) */
+    const int64_t *merge_work_per_round; /* [rounds] sum over live edges of the lengths of
+                                            the two lists each edge task intersects (the
+                                            tail of row i and row kappa); 0 with the
+                                            thread-per-edge kernel */
+    float ms_total;            /* whole run, device time on the stream (timing on) */
+    float ms_support;          /* sum of support steps */
+    float ms_balance;          /* sum of work-estimate / scan / partition steps */
+    float ms_prune_compact;    /* sum of prune + compaction steps */
+    float ms_finalize;         /* final scatter of outputs to input edge order */
+    int32_t support_launches;  /* support-kernel launches issued */
+    int32_t kernel_launches;   /* all kernels of this library issued by the run */
+} ktruss_stats_t;
+
+/*
+ * Copies a strictly upper-triangular CSR graph into a new library-owned handle
+ * on the current CUDA device (Sec. II-B input; Sec. III-D layout).
+ *   out        receives the handle (set to NULL on error)
+ *   n, m       vertex and edge counts
+ *   row_ptr    int32[n+1], col int32[m], in memory of kind mem_kind
+ *   cuda_stream stream for the copies and the validation kernel
+ * The caller keeps ownership of row_ptr/col and may free them on return.
+ * The whole CSR contract is validated on the device before the handle is
+ * returned.  Returns KTRUSS_EINVAL for n < 0, m < 0, m >= 2^31, NULL arrays
+ * (col may be NULL when m == 0), a bad mem_kind, row_ptr[0] != 0,
+ * row_ptr[n] != m, a decreasing row_ptr, a column <= its row or >= n, or
+ * columns not strictly increasing in a row; KTRUSS_ENOMEM, KTRUSS_ECUDA.
+ */
+int ktruss_load_csr(ktruss_graph **out, int32_t n, int64_t m, const int32_t *row_ptr,
+                    const int32_t *col, int mem_kind, void *cuda_stream);
+
+/*
+ * Computes the K-truss of the loaded graph by Alg. 1 with fine-grained support
+ * tasks (Alg. 3) and writes, per input edge slot e:
+ *   mask_out[e]    = 1 if e is in the K-truss, else 0          (uint8[m])
+ *   support_out[e] = number of triangles of the K-truss on e,
+ *                    0 for removed edges                       (int32[m]; may be NULL)
+ * Outputs are caller-owned, of kind mem_kind.  The loaded graph is not
+ * modified, so several K may be run on one handle.  Rounds, removals and
+ * timings are available from ktruss_stats until the next run or free.
+ * K = 2 keeps every edge and returns triangle counts.
+ * Returns KTRUSS_EINVAL for K < 2 or a NULL mask_out with m > 0,
+ * KTRUSS_ENOMEM, KTRUSS_ECUDA, KTRUSS_ETIMEOUT, KTRUSS_EBUSY.
+ */
+int ktruss_run(ktruss_graph *g, int32_t K, uint8_t *mask_out, int32_t *support_out, int mem_kind,
+               void *cuda_stream);
+
+/*
+ * Copies the statistics of the last ktruss_run into *out.  The per-round
+ * arrays point into the handle and stay valid until the next run or free.
+ * Returns KTRUSS_EINVAL for NULL arguments or a handle never run.
+ */
+int ktruss_stats(const ktruss_graph *g, ktruss_stats_t *out);
+
+/* Sets a KTRUSS_OPT_* option on a handle.  KTRUSS_EINVAL for an unknown key
+ * or value. */
+int ktruss_set_option(ktruss_graph *g, int32_t key, int64_t value);
+
+/* Vertex and edge counts of a loaded handle.  KTRUSS_EINVAL for NULL. */
+int ktruss_graph_size(const ktruss_graph *g, int32_t *n, int64_t *m);
+
+/* Releases a handle and all device memory it owns (NULL is a no-op). */
+void ktruss_free(ktruss_graph *g);
+
+/* Static string naming a KTRUSS_* code. */
+const char *ktruss_strerror(int code);
+
+/* The cudaError_t behind the calling thread's last KTRUSS_ECUDA (0 if none). */
+int ktruss_last_cuda_error(void);
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int ktruss_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KTRUSS_H */

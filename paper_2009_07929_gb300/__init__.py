@@ -1,0 +1,252 @@
+"""GB300-native fine-grained Eager K-truss.
+
+Python binding of ``libktruss.so`` (C ABI in ``include/ktruss.h``).  This module
+only marshals arguments: every step of the K-truss computation runs in the
+library's CUDA kernels.  PyTorch provides device memory and the current stream.
+There is no CPU fallback: if the library cannot be built or loaded, every call
+raises.
+
+    >>> import paper_2009_07929_gb300 as kt
+    >>> g = kt.load(row_ptr, col)          # int32 CSR (torch cuda/cpu or numpy)
+    >>> mask, support = g.run(3)           # uint8 / int32 cuda tensors
+    >>> g.stats()["rounds"]
+
+Method: M. Blanco, T. M. Low, K. Kim, "Exploration of Fine-Grained Parallelism
+for Load Balancing Eager K-truss on GPU and CPU", HPEC 2019 (Alg. 1 peeling,
+Alg. 3 edge tasks, eager credit rule of Sec. II-B).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _build
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBUSY = 0, -1, -2, -3, -4, -5
+HOST, DEVICE = 0, 1
+KERNEL_BALANCED, KERNEL_EDGE = 0, 1
+OPT_SUPPORT_KERNEL, OPT_TIMING = 1, 2
+
+_lib = None
+
+
+class KtrussError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        msg = _lib.ktruss_strerror(code).decode() if _lib is not None else str(code)
+        if code == ECUDA and _lib is not None:
+            msg += f" (cudaError {_lib.ktruss_last_cuda_error()})"
+        super().__init__(f"{what}: {msg} [{code}]" if what else f"{msg} [{code}]")
+        self.code = code
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [
+        ("rounds", ctypes.c_int32),
+        ("edges_in", ctypes.c_int64),
+        ("edges_out", ctypes.c_int64),
+        ("triangles_out", ctypes.c_int64),
+        ("per_round_len", ctypes.c_int32),
+        ("removed_per_round", ctypes.POINTER(ctypes.c_int64)),
+        ("live_per_round", ctypes.POINTER(ctypes.c_int64)),
+        ("triangles_per_round", ctypes.POINTER(ctypes.c_int64)),
+        ("ms_support_per_round", ctypes.POINTER(ctypes.c_float)),
+        ("merge_work_per_round", ctypes.POINTER(ctypes.c_int64)),
+        ("ms_total", ctypes.c_float),
+        ("ms_support", ctypes.c_float),
+        ("ms_balance", ctypes.c_float),
+        ("ms_prune_compact", ctypes.c_float),
+        ("ms_finalize", ctypes.c_float),
+        ("support_launches", ctypes.c_int32),
+        ("kernel_launches", ctypes.c_int32),
+    ]
+
+
+def build(force: bool = False) -> str:
+    """Compiles libktruss.so for sm_103a (in-tree) and returns its path."""
+    return _build.build(force=force)
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """The loaded libktruss (built first if needed)."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        L.ktruss_load_csr.argtypes = [ctypes.POINTER(vp), i32, i64, vp, vp, ctypes.c_int, vp]
+        L.ktruss_run.argtypes = [vp, i32, vp, vp, ctypes.c_int, vp]
+        L.ktruss_stats.argtypes = [vp, ctypes.POINTER(_Stats)]
+        L.ktruss_set_option.argtypes = [vp, i32, i64]
+        L.ktruss_graph_size.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i64)]
+        L.ktruss_free.argtypes = [vp]
+        L.ktruss_free.restype = None
+        L.ktruss_strerror.argtypes = [ctypes.c_int]
+        L.ktruss_strerror.restype = ctypes.c_char_p
+        for f in (L.ktruss_load_csr, L.ktruss_run, L.ktruss_stats, L.ktruss_set_option,
+                  L.ktruss_graph_size, L.ktruss_last_cuda_error, L.ktruss_version):
+            f.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, what: str):
+    if rc != OK:
+        raise KtrussError(rc, what)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream=None) -> int:
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _as_i32(a):
+    """Returns (pointer, kind, keepalive, length) for an int32 1-D array."""
+    if isinstance(a, np.ndarray):
+        arr = np.ascontiguousarray(a, dtype=np.int32)
+        return arr.ctypes.data if arr.size else None, HOST, arr, arr.shape[0]
+    torch = _torch()
+    if isinstance(a, torch.Tensor):
+        t = a.contiguous()
+        if t.dtype != torch.int32:
+            t = t.to(torch.int32)
+        kind = DEVICE if t.is_cuda else HOST
+        return (t.data_ptr() if t.numel() else None), kind, t, t.shape[0]
+    arr = np.ascontiguousarray(np.asarray(a), dtype=np.int32)
+    return arr.ctypes.data if arr.size else None, HOST, arr, arr.shape[0]
+
+
+@dataclass
+class Stats:
+    rounds: int
+    edges_in: int
+    edges_out: int
+    triangles_out: int
+    removed_per_round: list
+    live_per_round: list
+    triangles_per_round: list
+    ms_support_per_round: list
+    merge_work_per_round: list
+    ms_total: float
+    ms_support: float
+    ms_balance: float
+    ms_prune_compact: float
+    ms_finalize: float
+    support_launches: int
+    kernel_launches: int
+
+    def __getitem__(self, k):
+        return getattr(self, k)
+
+
+class Graph:
+    """A CSR graph resident on the current CUDA device (ktruss_load_csr)."""
+
+    def __init__(self, handle: int, n: int, m: int):
+        self._h = ctypes.c_void_p(handle)
+        self.n, self.m = n, m
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().ktruss_free(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def set_option(self, key: int, value: int):
+        _check(lib().ktruss_set_option(self._h, key, value), "ktruss_set_option")
+
+    def set_kernel(self, kernel: int):
+        self.set_option(OPT_SUPPORT_KERNEL, kernel)
+
+    def run(self, K: int, support: bool = True, out=None, stream=None):
+        """K-truss on the device (ktruss_run, device outputs on the current
+        torch stream).  Returns (mask uint8[m], support int32[m] or None)."""
+        torch = _torch()
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if out is not None:
+            mask, sup = out
+        else:
+            mask = torch.empty(max(self.m, 1), dtype=torch.uint8, device=dev)[: self.m]
+            sup = (torch.empty(max(self.m, 1), dtype=torch.int32, device=dev)[: self.m]
+                   if support else None)
+        rc = lib().ktruss_run(self._h, K, mask.data_ptr() if self.m else None,
+                              sup.data_ptr() if (sup is not None and self.m) else None, DEVICE,
+                              _stream_ptr(stream))
+        _check(rc, "ktruss_run")
+        return mask, sup
+
+    def run_host(self, K: int, support: bool = True, mask_out=None, support_out=None,
+                 stream=None):
+        """K-truss with host output buffers (numpy, pageable or pinned torch)."""
+        if mask_out is None:
+            mask_out = np.zeros(self.m, dtype=np.uint8)
+        if support_out is None and support:
+            support_out = np.zeros(self.m, dtype=np.int32)
+
+        def ptr(a):
+            if a is None or self.m == 0:
+                return None
+            return a.ctypes.data if isinstance(a, np.ndarray) else a.data_ptr()
+
+        rc = lib().ktruss_run(self._h, K, ptr(mask_out), ptr(support_out), HOST,
+                              _stream_ptr(stream))
+        _check(rc, "ktruss_run")
+        return mask_out, support_out
+
+    def stats(self) -> Stats:
+        st = _Stats()
+        _check(lib().ktruss_stats(self._h, ctypes.byref(st)), "ktruss_stats")
+        r = st.per_round_len
+
+        def arr(p, typ=int):
+            return [typ(p[i]) for i in range(r)] if r else []
+
+        return Stats(st.rounds, st.edges_in, st.edges_out, st.triangles_out,
+                     arr(st.removed_per_round), arr(st.live_per_round),
+                     arr(st.triangles_per_round), arr(st.ms_support_per_round, float),
+                     arr(st.merge_work_per_round),
+                     st.ms_total, st.ms_support, st.ms_balance, st.ms_prune_compact,
+                     st.ms_finalize, st.support_launches, st.kernel_launches)
+
+
+def load(row_ptr, col, stream=None) -> Graph:
+    """Copies an upper-triangular int32 CSR (torch cuda/cpu tensors or numpy
+    arrays; both of the same kind) into a new graph handle (ktruss_load_csr)."""
+    rp_p, rp_kind, rp_keep, rp_len = _as_i32(row_ptr)
+    c_p, c_kind, c_keep, m = _as_i32(col)
+    if m > 0 and rp_kind != c_kind:
+        raise ValueError("row_ptr and col must both be host or both be device arrays")
+    n = rp_len - 1
+    if n < 0:
+        raise KtrussError(EINVAL, "ktruss_load_csr")
+    h = ctypes.c_void_p(0)
+    rc = lib().ktruss_load_csr(ctypes.byref(h), n, m, rp_p, c_p, rp_kind, _stream_ptr(stream))
+    _check(rc, "ktruss_load_csr")
+    return Graph(h.value, n, m)
+
+
+def ktruss(row_ptr, col, K: int, kernel: int = KERNEL_BALANCED):
+    """One-shot helper: load, run on the device, return (mask, support, stats)."""
+    g = load(row_ptr, col)
+    g.set_kernel(kernel)
+    mask, sup = g.run(K)
+    st = g.stats()
+    g.close()
+    return mask, sup, st

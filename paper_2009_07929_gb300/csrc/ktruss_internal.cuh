@@ -1,0 +1,103 @@
+// Internal interfaces of libktruss: kernel launchers shared by the C ABI
+// runtime (capi.cu) and the kernel translation units.  Not installed.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace kt {
+
+// Live graph of one peel round: strictly upper-triangular CSR plus, per slot,
+// the input edge id it came from (eid == nullptr means the identity, which is
+// the case before the first compaction).
+struct Live {
+    const int32_t *rp;   // [n+1]
+    const int32_t *col;  // [m]
+    const int32_t *eid;  // [m] or nullptr
+    int32_t n;
+    int32_t m;
+};
+
+// Device-side counters of one round, written by kernels, read once per round
+// by the host through a pinned mirror.
+struct RoundCounters {
+    unsigned long long triangles;  // triangles found by the support step
+    unsigned long long merge_work; // sum over live edges of tail + row-kappa lengths
+    int32_t kept;                  // edges with support >= K-2
+    int32_t error;                 // nonzero: a kernel detected an inconsistency
+};
+
+// Device error bits in RoundCounters::error during a run.
+constexpr int32_t kDevErrTimeout = 1;   // a bounded wait gave up
+constexpr int32_t kDevErrInternal = 2;  // an internal consistency check failed
+
+constexpr int kWarp = 32;
+
+// ---- validation (validate.cu) ----------------------------------------------
+// Sets *err to a nonzero bit mask if (rp, col) violates the upper-triangular
+// CSR contract.  *err must be zero on entry.
+cudaError_t launch_validate(const int32_t *rp, const int32_t *col, int32_t n, int64_t m,
+                            int32_t *err, cudaStream_t s);
+
+// ---- support step (support_edge.cu, support_balanced.cu) -------------------
+// S[0..m) must be zero on entry; adds every live edge's support into S and the
+// number of triangles found into cnt->triangles.
+cudaError_t launch_support_edge(const Live &g, int32_t *S, RoundCounters *cnt, cudaStream_t s);
+
+// Scratch owned by the handle for the balanced support kernel.
+// One device allocation carved into: the int64 work prefix [m+1], tile sums
+// and offsets of its scan, the chunk plan, the chunk boundary table, the
+// long-row task table and the scheduler counters.
+struct BalancedScratch {
+    void *base = nullptr;
+    int64_t cap_m = 0;      // capacity in edges
+    int64_t cap_tasks = 0;  // long-row task capacity
+    int32_t cap_n = 0;
+};
+
+// Bytes of device scratch BalancedScratch needs for a graph of n vertices and
+// m edges (used for allocation at load time).
+size_t balanced_scratch_bytes(int32_t n, int64_t m);
+cudaError_t balanced_scratch_alloc(BalancedScratch *bs, int32_t n, int64_t m);
+void balanced_scratch_free(BalancedScratch *bs);
+
+// Balanced support step: work estimate + int64 scan + partition + staged
+// warp-cooperative intersection.  Adds supports into S (zero on entry).
+// Kernel launches issued are added to *launches.  When ev is given, ev[1] is
+// recorded between the balance kernels and the support kernels.
+cudaError_t launch_support_balanced(const Live &g, int32_t *S, RoundCounters *cnt,
+                                    BalancedScratch *bs, cudaStream_t s, int *launches,
+                                    cudaEvent_t *ev);
+
+// ---- prune + compaction + finalize (compact.cu) ---------------------------
+// Tile geometry of the compaction kernels.
+constexpr int kCompactThreads = 256;
+constexpr int kCompactItemsPerThread = 16;
+constexpr int kCompactTile = kCompactThreads * kCompactItemsPerThread;
+
+inline int32_t compact_tiles(int32_t m) { return (m + kCompactTile - 1) / kCompactTile; }
+
+// Counts edges with S >= thr per tile into tile_count[tiles], then scans the
+// tile counts into tile_off[tiles] and writes the total into cnt->kept.
+cudaError_t launch_prune_count(const int32_t *S, int32_t m, int32_t thr, int32_t *tile_count,
+                               int32_t *tile_off, RoundCounters *cnt, cudaStream_t s,
+                               int *launches);
+
+// Scatters kept edges (S >= thr) of `in` into (col_out, eid_out) in order,
+// writes the exclusive kept-prefix of every slot into pos[m_in] (pos[m] =
+// total), writes removed edges' final outputs (mask 0, support 0 at their
+// input edge id) and builds rp_out[i] = pos[rp_in[i]] (cnt->kept for
+// rp_in[i] == m).
+cudaError_t launch_compact(const Live &in, const int32_t *S, int32_t thr, const int32_t *tile_off,
+                           const RoundCounters *cnt, int32_t *pos, int32_t *rp_out,
+                           int32_t *col_out, int32_t *eid_out, uint8_t *mask_out,
+                           int32_t *support_out, cudaStream_t s, int *launches);
+
+// Final outputs of the surviving edges: mask 1 and support S at their input id.
+cudaError_t launch_finalize(const Live &g, const int32_t *S, uint8_t *mask_out,
+                            int32_t *support_out, cudaStream_t s, int *launches);
+
+// Fills eid[e] = e.
+cudaError_t launch_iota(int32_t *eid, int32_t m, cudaStream_t s);
+
+}  // namespace kt

@@ -1,0 +1,59 @@
+"""The C ABI library builds for sm_103a, loads, and exports every function
+declared in include/ktruss.h (no GPU needed: no compute call is made)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2009_07929_gb300 as kt
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "ktruss.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ktruss_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for f in ("ktruss_load_csr", "ktruss_run", "ktruss_stats", "ktruss_free", "ktruss_strerror"):
+        assert f in names
+
+
+def test_library_exports_every_declared_symbol():
+    L = kt.lib()
+    for name in declared_functions():
+        assert hasattr(L, name), name
+
+
+def test_error_strings_and_version_without_gpu():
+    L = kt.lib()
+    assert L.ktruss_version() >= 100
+    for code in (kt.OK, kt.EINVAL, kt.ENOMEM, kt.ECUDA, kt.ETIMEOUT, kt.EBUSY):
+        assert L.ktruss_strerror(code)
+    assert L.ktruss_strerror(-99) == b"unknown error"
+
+
+def test_argument_checks_before_any_cuda_call():
+    L = kt.lib()
+    h = ctypes.c_void_p(0)
+    # NULL out-pointer, negative sizes, NULL arrays and bad kinds are rejected on the host
+    assert L.ktruss_load_csr(None, 1, 0, None, None, kt.HOST, None) == kt.EINVAL
+    assert L.ktruss_load_csr(ctypes.byref(h), -1, 0, None, None, kt.HOST, None) == kt.EINVAL
+    assert L.ktruss_load_csr(ctypes.byref(h), 3, -1, None, None, kt.HOST, None) == kt.EINVAL
+    assert L.ktruss_load_csr(ctypes.byref(h), 3, 1 << 31, None, None, kt.HOST, None) == kt.EINVAL
+    rp = (ctypes.c_int32 * 2)(0, 0)
+    assert L.ktruss_load_csr(ctypes.byref(h), 1, 0, rp, None, 7, None) == kt.EINVAL
+    assert L.ktruss_run(None, 3, None, None, kt.DEVICE, None) == kt.EINVAL
+    assert L.ktruss_stats(None, None) == kt.EINVAL
+    assert L.ktruss_set_option(None, kt.OPT_TIMING, 1) == kt.EINVAL
+    L.ktruss_free(None)
+
+
+def test_build_is_for_sm_103a():
+    from paper_2009_07929_gb300 import _build
+    assert "arch=compute_103a,code=sm_103a" in " ".join(_build.ARCH)
+    assert os.path.exists(kt.library_path())

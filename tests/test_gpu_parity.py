@@ -1,0 +1,340 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+All arithmetic is integer, so masks, supports and per-round statistics must be
+identical (tolerance 0).  Small and mid-size graphs are compared element by
+element with a live oracle run; the full-size R-MAT workloads are compared
+against stored oracle digests and, where no digest exists, on sampled edges
+the oracle computes one at a time plus size-independent properties.
+"""
+import hashlib
+import json
+import os
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+KERNELS = [0, 1]  # balanced, thread-per-edge
+
+
+@pytest.fixture(scope="module")
+def kt():
+    import torch
+    import paper_2009_07929_gb300 as kt
+    kt.lib()
+    torch.cuda.init()
+    return kt
+
+
+def gpu_run(kt, g, K, kernel=0, host=False):
+    import torch
+    if host:
+        h = kt.load(g.row_ptr, g.col)
+    else:
+        h = kt.load(torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col).cuda())
+    h.set_kernel(kernel)
+    if host:
+        mask, sup = h.run_host(K)
+    else:
+        m_t, s_t = h.run(K)
+        torch.cuda.current_stream().synchronize()
+        mask, sup = m_t.cpu().numpy(), s_t.cpu().numpy()
+    st = h.stats()
+    h.close()
+    return mask, sup, st
+
+
+def assert_parity(kt, g, K, kernel=0, host=False):
+    r = oracle.ktruss(g.row_ptr, g.col, K)
+    mask, sup, st = gpu_run(kt, g, K, kernel, host)
+    assert np.array_equal(mask, r.mask), f"mask differs (K={K}, kernel={kernel})"
+    assert np.array_equal(sup, r.support), f"support differs (K={K}, kernel={kernel})"
+    assert st.rounds == r.rounds
+    assert st.removed_per_round == r.removed_per_round
+    assert st.triangles_out == r.triangles
+    assert st.edges_out == int(r.mask.sum())
+    return r, st
+
+
+# ---------------------------------------------------------------- config 1
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("seed", range(10))
+def test_er2000_all_seeds(kt, seed, kernel):
+    g = gg.workload("er2000", seed)
+    for K in (3, 4, 5):
+        assert_parity(kt, g, K, kernel)
+
+
+# --------------------------------------------------------------- edge cases
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_degenerate_graphs(kt, kernel):
+    cases = [gg.empty(0), gg.empty(1), gg.empty(17), gg.from_edges(2, [(0, 1)]), gg.star(50),
+             gg.triangle_strip(4), gg.triangle_strip(101), gg.complete(3)]
+    for g in cases:
+        for K in (2, 3, 4, 5):
+            assert_parity(kt, g, K, kernel)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_complete_graphs(kt, kernel):
+    for n in (4, 5, 17, 33, 64, 130):
+        g = gg.complete(n)
+        r, st = assert_parity(kt, g, n, kernel)
+        assert st.rounds == 1 and r.mask.all()
+        assert_parity(kt, g, n + 1, kernel)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_book_graph_support_above_uint16(kt, kernel):
+    g = gg.book(70000)
+    r, _ = assert_parity(kt, g, 3, kernel)
+    assert r.support[0] == 70000
+    assert_parity(kt, g, 4, kernel)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_row_longer_than_any_stage(kt, kernel):
+    # vertex 0 adjacent to 1..L, plus a path and chords among its neighbours,
+    # so row 0 is far longer than a shared-memory stage and carries triangles
+    L = 20000
+    edges = [(0, j) for j in range(1, L + 1)]
+    edges += [(j, j + 1) for j in range(1, L)] + [(j, j + 7) for j in range(1, L - 7, 3)]
+    g = gg.from_edges(L + 1, edges)
+    for K in (3, 4, 5):
+        assert_parity(kt, g, K, kernel)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_random_small_graphs(kt, kernel):
+    for s in range(60):
+        g = gg.gnp_small(5 + s % 36, (0.1, 0.3, 0.6, 0.9)[s % 4], seed=1000 + s)
+        for K in (2, 3, 4, 6):
+            assert_parity(kt, g, K, kernel)
+
+
+def deep_cascade_graphs(count=6):
+    """Seeded search over small random graphs keeping those whose peeling runs
+    the most bulk rounds (the oracle decides)."""
+    best = []
+    for s in range(400):
+        g = gg.gnp_small(30, 0.25, seed=5000 + s)
+        for K in (4, 5):
+            r = oracle.ktruss(g.row_ptr, g.col, K)
+            best.append((r.rounds, s, K))
+    best.sort(reverse=True)
+    return [(gg.gnp_small(30, 0.25, seed=5000 + s), K, rounds) for rounds, s, K in best[:count]]
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_deep_cascades(kt, kernel):
+    for g, K, rounds in deep_cascade_graphs():
+        assert rounds >= 3
+        assert_parity(kt, g, K, kernel)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_small_rmat_with_long_rows(kt, kernel):
+    for scale, seed in ((12, 0), (14, 1), (16, 2)):
+        g = gg.rmat(scale, 16, seed)
+        assert np.diff(g.row_ptr).max() > 4096 or scale < 16
+        for K in (3, 4, 7, 12):
+            assert_parity(kt, g, K, kernel)
+
+
+def test_rmat_with_cliques_kmax(kt):
+    g = gg.rmat(14, 8, seed=3, n_cliques=8, clique_lo=20, clique_hi=60)
+    tr = oracle.truss_decomposition(g.row_ptr, g.col)
+    kmax = int(tr.max())
+    for K in (3, kmax - 1, kmax, kmax + 1):
+        assert_parity(kt, g, K)
+
+
+def test_relabel_variant_same_truss(kt):
+    g = gg.rmat(13, 16, 5)
+    h = gg.rmat(13, 16, 5, relabel=True)
+    rel = gg.relabel_map(g.n, g.row_ptr, g.col)
+    new_e = np.sort(rel[g.edges()], axis=1)
+    key_h = h.edges()[:, 0] * g.n + h.edges()[:, 1]
+    idx = np.searchsorted(key_h, new_e[:, 0] * g.n + new_e[:, 1])
+    for K in (3, 5, 9):
+        mg, sg, _ = gpu_run(kt, g, K)
+        mh, sh, _ = gpu_run(kt, h, K)
+        assert np.array_equal(mg, mh[idx]) and np.array_equal(sg, sh[idx])
+
+
+def test_host_kind_buffers_match_device_kind(kt):
+    g = gg.rmat(14, 16, 7)
+    for K in (3, 6):
+        assert_parity(kt, g, K, host=True)
+
+
+def test_several_K_on_one_handle(kt):
+    import torch
+    g = gg.rmat(14, 16, 8)
+    h = kt.load(torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col).cuda())
+    prev = None
+    for K in (9, 3, 5, 3, 12):
+        m_t, s_t = h.run(K)
+        torch.cuda.synchronize()
+        r = oracle.ktruss(g.row_ptr, g.col, K)
+        assert np.array_equal(m_t.cpu().numpy(), r.mask)
+        assert np.array_equal(s_t.cpu().numpy(), r.support)
+        assert h.stats().rounds == r.rounds
+    h.close()
+
+
+def test_support_optional(kt):
+    import torch
+    g = gg.er(2000, 16000, 3)
+    h = kt.load(torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col).cuda())
+    mask, sup = h.run(3, support=False)
+    torch.cuda.synchronize()
+    assert sup is None
+    assert np.array_equal(mask.cpu().numpy(), oracle.ktruss(g.row_ptr, g.col, 3).mask)
+    h.close()
+
+
+# ---------------------------------------------------------------- errors
+
+def test_malformed_csr_rejected_on_device(kt):
+    import torch
+    bad = [
+        (np.array([0, 1], np.int32), np.array([0], np.int32)),
+        (np.array([0, 2, 2], np.int32), np.array([1, 1], np.int32)),
+        (np.array([0, 1, 1], np.int32), np.array([5], np.int32)),
+        (np.array([0, 2, 1, 2], np.int32), np.array([1, 2], np.int32)),
+        (np.array([1, 1], np.int32), np.zeros(1, np.int32)[:0]),
+        (np.array([0, 0, 3], np.int32), np.array([1, 2, 3], np.int32)),
+    ]
+    for rp, c in bad:
+        for dev in (False, True):
+            a = torch.from_numpy(rp).cuda() if dev else rp
+            b = torch.from_numpy(c).cuda() if dev else c
+            with pytest.raises(kt.KtrussError) as ei:
+                kt.load(a, b)
+            assert ei.value.code == kt.EINVAL
+
+
+def test_k_below_two_rejected(kt):
+    import torch
+    g = gg.complete(5)
+    h = kt.load(torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col).cuda())
+    with pytest.raises(kt.KtrussError) as ei:
+        h.run(1)
+    assert ei.value.code == kt.EINVAL
+    h.close()
+
+
+def test_injected_allocation_failure(kt, monkeypatch):
+    g = gg.complete(6)
+    for budget in ("0", "3", "12"):
+        monkeypatch.setenv("KTRUSS_TEST_FAIL_ALLOC", budget)
+        with pytest.raises(kt.KtrussError) as ei:
+            kt.load(g.row_ptr, g.col)
+        assert ei.value.code == kt.ENOMEM
+    monkeypatch.delenv("KTRUSS_TEST_FAIL_ALLOC")
+    assert_parity(kt, g, 6)
+
+
+# -------------------------------------------- full-size workloads (digests)
+
+def sha(a) -> str:
+    return hashlib.sha256(a.tobytes()).hexdigest()
+
+
+def golden_cases(name):
+    p = os.path.join(GOLDEN, f"{name}.json")
+    if not os.path.exists(p):
+        return []
+    with open(p) as f:
+        return json.load(f)["cases"]
+
+
+def graph_digest(g) -> str:
+    h = hashlib.sha256()
+    h.update(np.ascontiguousarray(g.row_ptr, dtype="<i4").tobytes())
+    h.update(np.ascontiguousarray(g.col, dtype="<i4").tobytes())
+    return h.hexdigest()
+
+
+@pytest.mark.parametrize("name", ["rmat20", "rmat20r", "rmat23c"])
+def test_full_size_against_oracle_digests(kt, name):
+    cases = golden_cases(name)
+    if not cases:
+        pytest.skip(f"no stored oracle digests for {name}")
+    import torch
+    by_seed = {}
+    for c in cases:
+        by_seed.setdefault(c["seed"], []).append(c)
+    for seed, cs in sorted(by_seed.items()):
+        g = gg.workload(name, seed)
+        assert graph_digest(g) == cs[0]["graph_sha256"], "generator output changed"
+        h = kt.load(torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col).cuda())
+        for c in cs:
+            m_t, s_t = h.run(c["K"])
+            torch.cuda.synchronize()
+            st = h.stats()
+            mask = m_t.cpu().numpy()
+            sup = np.ascontiguousarray(s_t.cpu().numpy(), dtype="<i4")
+            assert st.rounds == c["rounds"], c
+            assert st.removed_per_round == c["removed_per_round"], c
+            assert st.edges_out == c["edges_out"] and st.triangles_out == c["triangles_out"]
+            assert int(sup.astype(np.int64).sum()) == c["support_sum"]
+            assert sha(mask) == c["mask_sha256"] and sha(sup) == c["support_sha256"]
+        h.close()
+
+
+def test_rmat23_cliques_k3_sampled_and_kmax_sweep(kt):
+    """Config 3 at full size: K=3 checked on sampled edges against per-edge
+    oracle supports (for K=3 the kept edges are exactly those in a triangle and
+    keep their full-graph support); then K rises to the largest non-empty truss,
+    checking size-independent properties at every K and sampled supports inside
+    the truss for a few K."""
+    import torch
+    g = gg.cached_workload("rmat23c", 0)
+    h = kt.load(torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col).cuda())
+    rng = np.random.default_rng(0)
+    m_t, s_t = h.run(3)
+    torch.cuda.synchronize()
+    mask3, sup3 = m_t.cpu().numpy(), s_t.cpu().numpy()
+    st = h.stats()
+    assert st.rounds <= 2
+    q = np.unique(np.concatenate([rng.integers(0, g.m, 4000), np.arange(2000),
+                                  np.flatnonzero(np.diff(g.row_ptr) > 0)[:500]]))
+    q = q[q < g.m]
+    full = oracle.edge_support(g.row_ptr, g.col, q)
+    assert np.array_equal(sup3[q], full)
+    assert np.array_equal(mask3[q], (full >= 1).astype(np.uint8))
+    assert int(sup3.astype(np.int64).sum()) == 3 * st.triangles_out
+    prev = mask3
+    K = 4
+    kmax = 3
+    while True:
+        m_t, s_t = h.run(K)
+        torch.cuda.synchronize()
+        mask, sup = m_t.cpu().numpy(), s_t.cpu().numpy()
+        st = h.stats()
+        if not mask.any():
+            break
+        kmax = K
+        assert (sup[mask == 1] >= K - 2).all() and (sup[mask == 0] == 0).all()
+        assert not np.any((mask == 1) & (prev == 0))
+        assert int(sup.astype(np.int64).sum()) == 3 * st.triangles_out
+        if K in (6, 20, 100, 199) or mask.sum() < 50000:
+            kept = np.flatnonzero(mask)
+            qs = kept if kept.size <= 3000 else rng.choice(kept, 3000, replace=False)
+            assert np.array_equal(sup[qs], oracle.edge_support(g.row_ptr, g.col, qs, keep=mask))
+        prev = mask
+        K += 1 if K < 20 or K > 190 else 10
+        if K > 400:
+            break
+    # a 200-clique was planted, so the 200-truss is non-empty
+    assert kmax >= 200
+    h.close()
