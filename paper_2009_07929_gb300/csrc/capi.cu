@@ -17,7 +17,7 @@
 #include <new>
 #include <vector>
 
-#include "../../include/ktruss.h"
+#include "ktruss.h"
 #include "ktruss_internal.cuh"
 
 namespace {

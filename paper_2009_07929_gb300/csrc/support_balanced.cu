@@ -21,12 +21,14 @@
 //    across CTAs.
 //  * intersection: a persistent kernel takes chunks dynamically.  Consecutive
 //    short staged rows (<= kCap slots in total) are loaded into one shared-
-//    memory hash table keyed by (row, column) -> slot; warps take segments
-//    dynamically, stream the probe list with coalesced loads and probe the
-//    table.  A staged row longer than kCap is loaded piece by piece (in column
-//    order); each segment keeps a cursor that advances through its probe list
-//    piece by piece, so every probe is still read once.  Credits to staged
-//    slots are gathered in shared memory and flushed once per stage or piece.
+//    memory hash table (one region per row, column -> slot); the probes of a
+//    batch of segments form one flat item space that the warps split evenly,
+//    each lane mapping its item to its segment, so short and long segments
+//    keep every lane busy.  A staged row longer than kCap is loaded piece by
+//    piece (in column order); per piece each segment contributes the run of
+//    its probes below the piece's last column, found by binary search, so
+//    every probe is still read once.  Credits to staged slots are gathered in
+//    shared memory and flushed once per stage or piece.
 //
 // All credits are integer additions, so the result does not depend on the
 // order in which CTAs, warps or the counting sort place the work.
@@ -38,11 +40,13 @@ namespace kt {
 namespace {
 
 // ----------------------------------------------------------- configuration
-constexpr int kThreads = 512;           // threads per support CTA
+constexpr int kThreads = 1024;          // threads per support CTA (one CTA per SM)
 constexpr int kCap = 4096;              // staged slots per stage or piece
-constexpr int kTable = 2 * kCap;        // hash entries (load factor <= 1/2)
+constexpr int kTable = 4 * kCap;        // hash entries (load factor <= 1/4)
 constexpr int kStageRows = 256;         // staged rows per stage
-constexpr int kSegBatch = 512;          // segments per long-row batch
+constexpr int kWarps = kThreads / 32;
+constexpr int kBatch = kThreads;        // segments per batch (one per thread)
+constexpr int kUnroll = 4;              // 32-item windows in flight per warp
 constexpr long long kChunkMin = 65536;  // items per chunk (minimum)
 constexpr int kChunksPerCta = 16;       // target chunks per resident CTA
 constexpr int kMaxChunks = 1 << 17;     // chunk table capacity
@@ -120,64 +124,52 @@ struct RowWalk {
 };
 
 // ------------------------------------------------------------ hash table
-// Buckets of 4 int32 keys (one 16-byte shared load per probe), a parallel
-// array of 16-bit local slots, load factor <= 1/2.  key_row disambiguates
-// equal columns of different staged rows.
-__device__ __forceinline__ uint32_t bucket_of(int32_t key_row, int32_t w, uint32_t mask) {
-    uint32_t h = uint32_t(w) * 0x9E3779B1u + uint32_t(key_row) * 0x7FEB352Du;
-    h ^= h >> 15;
-    h *= 0x846CA68Bu;
-    h ^= h >> 13;
-    return h & mask;
+// Every staged row gets its own power-of-two region of the shared table made
+// of buckets of 4 int32 keys (one 16-byte shared load per probe), with a
+// parallel array of 16-bit local slots.  A region has at least 2 buckets and
+// is at most a quarter full, so a probe rarely needs a second bucket.  Entries of a bucket fill in order (an insert tries
+// the next entry only when the previous one is taken), so a bucket whose last
+// key is free ends a search.
+constexpr uint32_t kHashMul = 0x9E3779B1u;  // Fibonacci hashing: top bits of w * 2^32/phi
+
+// log2 of the bucket count of the region of a row of length len (4 entries
+// per bucket, at least 4 entries per key).
+__device__ __forceinline__ int region_lb(int32_t len) {
+    int lb = 1;
+    while ((1 << lb) < len) ++lb;
+    return lb;
 }
 
-__device__ __forceinline__ void table_insert(int32_t *keys, uint16_t *slots, uint32_t mask,
-                                             int32_t key_row, int32_t w, int32_t s) {
-    uint32_t b = bucket_of(key_row, w, mask);
+__device__ __forceinline__ void table_insert(int32_t *keys, uint16_t *slots, int32_t bbase,
+                                             int lb, int32_t w, int32_t s) {
+    const uint32_t bm = (1u << lb) - 1u;
+    uint32_t b = (uint32_t(w) * kHashMul) >> (32 - lb);
     for (;;) {
+        const int32_t at = 4 * (bbase + int32_t(b));
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            if (atomicCAS(keys + 4 * b + j, kEmpty, w) == kEmpty) {
-                slots[4 * b + j] = uint16_t(s);
+            if (atomicCAS(keys + at + j, kEmpty, w) == kEmpty) {
+                slots[at + j] = uint16_t(s);
                 return;
             }
         }
-        b = (b + 1) & mask;
+        b = (b + 1) & bm;
     }
 }
 
-// Local slot of column w in the staged slots [lo, hi) of key_row, or -1.
+// Local slot of column w in the region (bbase, lb), or -1.
 __device__ __forceinline__ int32_t table_find(const int32_t *keys, const uint16_t *slots,
-                                              uint32_t mask, int32_t key_row, int32_t w,
-                                              int32_t lo, int32_t hi) {
-    uint32_t b = bucket_of(key_row, w, mask);
+                                              int32_t bbase, int lb, int32_t w) {
+    const uint32_t bm = (1u << lb) - 1u;
+    uint32_t b = (uint32_t(w) * kHashMul) >> (32 - lb);
     for (;;) {
-        const int4 k = reinterpret_cast<const int4 *>(keys)[b];
-        if (k.x == w) {
-            const int32_t s = slots[4 * b + 0];
-            if (s >= lo && s < hi) return s;
-        }
-        if (k.y == w) {
-            const int32_t s = slots[4 * b + 1];
-            if (s >= lo && s < hi) return s;
-        }
-        if (k.z == w) {
-            const int32_t s = slots[4 * b + 2];
-            if (s >= lo && s < hi) return s;
-        }
-        if (k.w == w) {
-            const int32_t s = slots[4 * b + 3];
-            if (s >= lo && s < hi) return s;
-        }
-        if (k.x == kEmpty || k.y == kEmpty || k.z == kEmpty || k.w == kEmpty) return -1;
-        b = (b + 1) & mask;
+        const int32_t at = bbase + int32_t(b);
+        const int4 k = reinterpret_cast<const int4 *>(keys)[at];
+        const int j = k.x == w ? 0 : k.y == w ? 1 : k.z == w ? 2 : k.w == w ? 3 : -1;
+        if (j >= 0) return slots[4 * at + j];
+        if (k.w == kEmpty) return -1;
+        b = (b + 1) & bm;
     }
-}
-
-__device__ __forceinline__ int table_size_for(int32_t len) {
-    int t = 64;
-    while (t < 2 * len) t <<= 1;
-    return t;
 }
 
 // ------------------------------------------------------- generic tile scan
@@ -283,40 +275,44 @@ scan_apply_kernel(Load ld, Store st, int64_t count, const V *__restrict__ tile_o
 
 // --------------------------------------------------------- balance kernels
 // Per live edge: staged row, probe start and item count; per staged row: the
-// number of segments; per round: the merge work sum(t + d).
+// number of segments; per round: the merge work sum(t + d).  Counts of equal
+// staged rows within a warp are aggregated into one atomic.
 __global__ void __launch_bounds__(kEdgeThreads)
 classify_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, int32_t n,
                 int32_t m, int32_t *__restrict__ ekey, int32_t *__restrict__ epst,
                 int32_t *__restrict__ eitems, int32_t *__restrict__ rcount,
                 unsigned long long *__restrict__ merge_work) {
     __shared__ long long part[kEdgeThreads / 32];
+    const int lane = threadIdx.x & 31;
     const int64_t e0 = (int64_t(blockIdx.x) * kEdgeThreads + threadIdx.x) * kEdgesPerThread;
     long long merge = 0;
-    if (e0 < m) {
-        RowWalk rw;
-        rw.start(rp, n, int32_t(e0));
-        const int32_t e1 = int32_t(min(int64_t(m), e0 + kEdgesPerThread));
-        for (int32_t e = int32_t(e0); e < e1; ++e) {
-            rw.advance(rp, n, e);
+    RowWalk rw{0, 0, 0};
+    if (e0 < m) rw.start(rp, n, int32_t(e0));
+#pragma unroll 1
+    for (int j = 0; j < kEdgesPerThread; ++j) {
+        const int64_t e = e0 + j;
+        int32_t key = -1;
+        if (e < m) {
+            rw.advance(rp, n, int32_t(e));
             const int32_t kappa = __ldg(col + e);
             const int32_t kb = __ldg(rp + kappa);
             const int32_t d = __ldg(rp + kappa + 1) - kb;
-            const int32_t t = rw.rend - e - 1;
+            const int32_t t = rw.rend - int32_t(e) - 1;
             merge += (long long)t + d;
             const int32_t items = min(t, d);
-            int32_t key = -1;
             if (items > 0) {
                 const bool stage_kappa = t < d;
                 key = stage_kappa ? kappa : rw.row;
-                epst[e] = stage_kappa ? e + 1 : kb;
-                atomicAdd(rcount + key, 1);
+                epst[e] = stage_kappa ? int32_t(e) + 1 : kb;
             }
             ekey[e] = key;
             eitems[e] = items;
         }
+        const uint32_t peers = __match_any_sync(0xffffffffu, key);
+        if (key >= 0 && lane == __ffs(peers) - 1) atomicAdd(rcount + key, __popc(peers));
     }
     merge = warp_sum_ll(merge);
-    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = merge;
+    if (lane == 0) part[threadIdx.x >> 5] = merge;
     __syncthreads();
     if (threadIdx.x == 0) {
         long long t = 0;
@@ -355,20 +351,28 @@ __global__ void active_rows_kernel(const int32_t *__restrict__ rcount,
     if (r == 0) aseg[tot->b] = tot->a;
 }
 
-// Counting-sort scatter of the segments by staged row (consumes rcount).
+// Counting-sort scatter of the segments by staged row (consumes rcount);
+// also records each segment's active-row rank.
 __global__ void scatter_kernel(const int32_t *__restrict__ ekey, const int32_t *__restrict__ epst,
                                const int32_t *__restrict__ eitems, int32_t m,
-                               const int32_t *__restrict__ rstart, int32_t *__restrict__ rcount,
+                               const int32_t *__restrict__ rstart,
+                               const int32_t *__restrict__ arank, int32_t *__restrict__ rcount,
                                int32_t *__restrict__ seg, int32_t *__restrict__ pst,
-                               int32_t *__restrict__ sitems) {
+                               int32_t *__restrict__ sitems, int32_t *__restrict__ sact) {
+    const int lane = threadIdx.x & 31;
     const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (e >= m) return;
-    const int32_t key = ekey[e];
+    const int32_t key = e < m ? ekey[e] : -1;
+    const uint32_t peers = __match_any_sync(0xffffffffu, key);
     if (key < 0) return;
-    const int32_t pos = rstart[key] + atomicSub(rcount + key, 1) - 1;
+    const int leader = __ffs(peers) - 1;
+    int32_t old = 0;
+    if (lane == leader) old = atomicSub(rcount + key, __popc(peers));
+    old = __shfl_sync(peers, old, leader);
+    const int32_t pos = rstart[key] + old - 1 - __popc(peers & ((1u << lane) - 1u));
     seg[pos] = int32_t(e);
     pst[pos] = epst[e];
     sitems[pos] = eitems[e];
+    sact[pos] = arank[key];
 }
 
 struct ItemLoad {
@@ -424,31 +428,31 @@ __global__ void partition_kernel(const long long *__restrict__ wp, const int32_t
 }
 
 // ------------------------------------------------------------ support kernel
-struct StageDesc {
-    int32_t gbase[kStageRows];     // global slot of each staged row's first element
-    int32_t loc[kStageRows + 1];   // local slot offsets (prefix of row lengths)
-    int32_t segb[kStageRows + 1];  // first segment position of each staged row
-};
-struct LongDesc {
-    int32_t cur[kSegBatch];    // next probe position of each segment
-    int32_t end[kSegBatch];    // end of the segment's probes in this chunk
-    int32_t own[kSegBatch];    // hits counted for the segment's owner edge
-    int32_t owner[kSegBatch];  // owner edge slot
-};
+// Shared memory of one support CTA.
 struct SupportSmem {
-    int32_t keys[kTable];
-    uint16_t slots[kTable];
-    int32_t cnt[kCap];
-    union {
-        StageDesc st;
-        LongDesc lg;
-    } u;
-    int32_t ctl[32];
+    int32_t keys[kTable];             // hash keys (columns), kEmpty when free
+    uint16_t slots[kTable];           // local staged slot of each key
+    int32_t cnt[kCap];                // credits to staged slots
+    int32_t gbase[kStageRows];        // stage: global slot of each row's first element
+    int32_t loc[kStageRows + 1];      // stage: local slot offsets of the rows
+    int32_t segb[kStageRows + 1];     // stage: first segment position of each row
+    int32_t tbase[kStageRows + 1];    // stage: first bucket of each row's region
+    int32_t tlb[kStageRows];          // stage: log2 bucket count of each row's region
+    int32_t cur[kBatch];              // batch: next probe position of segment j
+    int32_t end[kBatch];              // batch: end of segment j's probes in the chunk
+    int32_t owner[kBatch];            // batch: owner edge slot of segment j
+    int32_t hit[kBatch];              // batch: hits credited to segment j's owner
+    int32_t rstart[kBatch + 1];       // runs: batch-local item offset of run r
+    int32_t rpos[kBatch];             // runs: probe position of run r's first item
+    int32_t rkey[kBatch];             // runs: staged (local) row the run probes
+    int32_t rseg[kBatch];             // runs: segment of run r
+    int32_t wtmp[64];
+    int32_t ctl[64];
 };
 
 struct SupportArgs {
     const int32_t *rp, *col;
-    const int32_t *seg, *pst;
+    const int32_t *seg, *pst, *sact;
     const long long *wp;
     const int32_t *arow, *aseg;
     const ChunkPlan *plan;
@@ -458,69 +462,181 @@ struct SupportArgs {
     unsigned long long *tri;
 };
 
-// Probes the staged table with col[x], x in [x0, x1), lanes striding by 32
-// (four loads in flight per lane); returns this lane's hits.
-__device__ __forceinline__ int32_t probe_range(const SupportArgs &A, SupportSmem &sm,
-                                               uint32_t mask, int32_t key_row, int32_t qlo,
-                                               int32_t qhi, int32_t x0, int32_t x1, int lane) {
-    int32_t own = 0;
-    int32_t x = x0 + lane;
-    for (; x + 96 < x1; x += 128) {
-        const int32_t w0 = __ldg(A.col + x), w1 = __ldg(A.col + x + 32);
-        const int32_t w2 = __ldg(A.col + x + 64), w3 = __ldg(A.col + x + 96);
-        const int32_t q0 = table_find(sm.keys, sm.slots, mask, key_row, w0, qlo, qhi);
-        const int32_t q1 = table_find(sm.keys, sm.slots, mask, key_row, w1, qlo, qhi);
-        const int32_t q2 = table_find(sm.keys, sm.slots, mask, key_row, w2, qlo, qhi);
-        const int32_t q3 = table_find(sm.keys, sm.slots, mask, key_row, w3, qlo, qhi);
-        if (q0 >= 0) { atomicAdd(&sm.cnt[q0], 1); atomicAdd(A.S + x, 1); ++own; }
-        if (q1 >= 0) { atomicAdd(&sm.cnt[q1], 1); atomicAdd(A.S + x + 32, 1); ++own; }
-        if (q2 >= 0) { atomicAdd(&sm.cnt[q2], 1); atomicAdd(A.S + x + 64, 1); ++own; }
-        if (q3 >= 0) { atomicAdd(&sm.cnt[q3], 1); atomicAdd(A.S + x + 96, 1); ++own; }
+// Exclusive block-wide prefix of v (kThreads threads); *total = sum.
+__device__ __forceinline__ int32_t block_excl_scan(int32_t v, int32_t *wtmp, int32_t &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t incl = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int32_t u = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += u;
     }
-    for (; x < x1; x += 32) {
-        const int32_t w = __ldg(A.col + x);
-        const int32_t q = table_find(sm.keys, sm.slots, mask, key_row, w, qlo, qhi);
-        if (q >= 0) { atomicAdd(&sm.cnt[q], 1); atomicAdd(A.S + x, 1); ++own; }
+    if (lane == 31) wtmp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int32_t x = lane < kWarps ? wtmp[lane] : 0;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int32_t u = __shfl_up_sync(0xffffffffu, x, d);
+            if (lane >= d) x += u;
+        }
+        if (lane < kWarps) wtmp[32 + lane] = x;
     }
-    return own;
+    __syncthreads();
+    const int32_t before = warp > 0 ? wtmp[32 + warp - 1] : 0;
+    total = wtmp[32 + kWarps - 1];
+    __syncthreads();
+    return before + incl - v;
 }
 
-__device__ __forceinline__ void clear_table(SupportSmem &sm, int tsize, int32_t len, int tid) {
-    for (int k = tid; k < tsize / 4; k += kThreads)
+// Builds the run list from per-thread (len, pos, key, seg) proposals: runs of
+// positive length in thread order.  Returns (runs, items) through the refs.
+__device__ __forceinline__ void build_runs(SupportSmem &sm, int32_t len, int32_t pos, int32_t key,
+                                           int32_t j, int32_t &nruns, int32_t &items) {
+    const int32_t flag = len > 0 ? 1 : 0;
+    const int32_t ridx = block_excl_scan(flag, sm.wtmp, nruns);
+    const int32_t roff = block_excl_scan(len > 0 ? len : 0, sm.wtmp, items);
+    if (flag) {
+        sm.rstart[ridx] = roff;
+        sm.rpos[ridx] = pos;
+        sm.rkey[ridx] = key;
+        sm.rseg[ridx] = j;
+    }
+    if (threadIdx.x == 0) sm.rstart[nruns] = items;
+    __syncthreads();
+}
+
+// Flattened probing of the runs of a batch.  The batch's items are split
+// evenly over the warps.  Where a warp's next 32 items lie inside one run, the
+// run's parameters are warp-uniform and a tight loop streams its windows
+// (kUnroll loads in flight per lane), counting the owner's hits in a register.
+// A window that crosses run boundaries maps each lane to its run with a
+// bitmask of the run starts inside the window.  single = true: the staged
+// rows are one piece whose region is (0, piece_lb).
+__device__ __forceinline__ void probe_runs(const SupportArgs &A, SupportSmem &sm, int32_t nruns,
+                                           int32_t items, bool single, int piece_lb) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int32_t per = ((items + kWarps - 1) / kWarps + 31) & ~31;
+    const int32_t w0 = warp * per;
+    const int32_t w1 = min(items, w0 + per);
+    if (w0 >= w1) return;
+    int32_t E = last_le(sm.rstart, 0, nruns - 1, w0);
+    int32_t pos = w0;
+    while (pos < w1) {
+        while (E + 1 < nruns && sm.rstart[E + 1] <= pos) ++E;
+        const int32_t rend = min(w1, E + 1 < nruns ? sm.rstart[E + 1] : items);
+        if (rend - pos >= 32) {
+            // ---- whole windows of run E
+            const int32_t nwin = (rend - pos) >> 5;
+            const int32_t xb = sm.rpos[E] + (pos - sm.rstart[E]) + lane;
+            const int32_t key = single ? 0 : sm.rkey[E];
+            const int32_t bb = single ? 0 : sm.tbase[key];
+            const int lb = single ? piece_lb : sm.tlb[key];
+            int32_t own = 0;
+            int32_t i = 0;
+            for (; i + kUnroll <= nwin; i += kUnroll) {
+                int32_t wv[kUnroll];
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u) wv[u] = __ldg(A.col + xb + 32 * (i + u));
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u) {
+                    const int32_t q = table_find(sm.keys, sm.slots, bb, lb, wv[u]);
+                    if (q >= 0) {
+                        atomicAdd(&sm.cnt[q], 1);
+                        atomicAdd(A.S + xb + 32 * (i + u), 1);
+                        ++own;
+                    }
+                }
+            }
+            for (; i < nwin; ++i) {
+                const int32_t q = table_find(sm.keys, sm.slots, bb, lb, __ldg(A.col + xb + 32 * i));
+                if (q >= 0) {
+                    atomicAdd(&sm.cnt[q], 1);
+                    atomicAdd(A.S + xb + 32 * i, 1);
+                    ++own;
+                }
+            }
+            own = __reduce_add_sync(0xffffffffu, own);
+            if (lane == 0 && own) atomicAdd(&sm.hit[sm.rseg[E]], own);
+            pos += nwin * 32;
+        } else {
+            // ---- one window crossing run boundaries
+            int32_t r = E;
+            if (E + 1 < nruns && sm.rstart[E + 1] < pos + 32) {
+                const int32_t j = E + 1 + lane;
+                const int32_t s = j < nruns ? sm.rstart[j] : kIntMax;
+                const int32_t rel = s - pos;
+                const uint32_t bits = __reduce_or_sync(0xffffffffu, rel < 32 ? (1u << rel) : 0u);
+                r = E + __popc(bits & (0xffffffffu >> (31 - lane)));
+            }
+            const int32_t item = pos + lane;
+            if (item < w1) {
+                const int32_t x = sm.rpos[r] + (item - sm.rstart[r]);
+                const int32_t key = single ? 0 : sm.rkey[r];
+                const int32_t bb = single ? 0 : sm.tbase[key];
+                const int lb = single ? piece_lb : sm.tlb[key];
+                const int32_t q = table_find(sm.keys, sm.slots, bb, lb, __ldg(A.col + x));
+                if (q >= 0) {
+                    atomicAdd(&sm.cnt[q], 1);
+                    atomicAdd(A.S + x, 1);
+                    atomicAdd(&sm.hit[sm.rseg[r]], 1);
+                }
+            }
+            E = __shfl_sync(0xffffffffu, r, 31);
+            pos += 32;
+        }
+    }
+}
+
+__device__ __forceinline__ void clear_table(SupportSmem &sm, int32_t buckets, int32_t len, int tid) {
+    for (int k = tid; k < buckets; k += kThreads)
         reinterpret_cast<int4 *>(sm.keys)[k] = make_int4(kEmpty, kEmpty, kEmpty, kEmpty);
     for (int k = tid; k < len; k += kThreads) sm.cnt[k] = 0;
 }
 
+// Adds the owner credits of a batch to S and to the triangle count.
+__device__ __forceinline__ void flush_owners(const SupportArgs &A, SupportSmem &sm, int32_t nb,
+                                             unsigned long long &tri) {
+    const int j = threadIdx.x;
+    if (j < nb) {
+        const int32_t v = sm.hit[j];
+        if (v) {
+            atomicAdd(A.S + sm.owner[j], v);
+            tri += v;
+        }
+    }
+}
+
 // The segments [s0, s1) of chunk [iA, iB) whose staged row (rbase, L) is
-// longer than kCap: piece by piece, with a cursor per segment.
+// longer than kCap: the row is staged piece by piece in column order; per
+// piece each segment contributes the run of its probes below the piece's end.
 __device__ void long_row(const SupportArgs &A, SupportSmem &sm, int32_t rbase, int32_t L,
                          int32_t s0, int32_t s1, long long iA, long long iB,
                          unsigned long long &tri) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int32_t npieces = (L + kCap - 1) / kCap;
-    for (int32_t sb = s0; sb < s1; sb += kSegBatch) {
-        const int32_t nb = min(kSegBatch, s1 - sb);
+    for (int32_t sb = s0; sb < s1; sb += kBatch) {
+        const int32_t nb = min(kBatch, s1 - sb);
         int32_t minv = kIntMax;
-        for (int j = tid; j < nb; j += kThreads) {
-            const int32_t pos = sb + j;
+        if (tid < nb) {
+            const int32_t pos = sb + tid;
             const long long base = __ldg(A.wp + pos);
             const int32_t ka = int32_t(max(iA, base) - base);
             const int32_t kb = int32_t(min(iB, __ldg(A.wp + pos + 1)) - base);
             const int32_t p0 = __ldg(A.pst + pos);
-            sm.u.lg.cur[j] = p0 + ka;
-            sm.u.lg.end[j] = p0 + max(ka, kb);
-            sm.u.lg.own[j] = 0;
-            sm.u.lg.owner[j] = __ldg(A.seg + pos);
-            if (kb > ka) minv = min(minv, __ldg(A.col + p0 + ka));
+            sm.cur[tid] = p0 + ka;
+            sm.end[tid] = p0 + max(ka, kb);
+            sm.owner[tid] = __ldg(A.seg + pos);
+            sm.hit[tid] = 0;
+            if (kb > ka) minv = __ldg(A.col + p0 + ka);
         }
         minv = __reduce_min_sync(0xffffffffu, minv);
         if (lane == 0) sm.ctl[16 + warp] = minv;
         __syncthreads();
         if (tid == 0) {
             int32_t mv = kIntMax;
-            for (int k = 0; k < kThreads / 32; ++k) mv = min(mv, sm.ctl[16 + k]);
-            // the last piece starting at a column <= mv holds the smallest probe
-            int32_t lo = 0, hi = npieces - 1;
+            for (int k = 0; k < kWarps; ++k) mv = min(mv, sm.ctl[16 + k]);
+            int32_t lo = 0, hi = npieces - 1;  // last piece starting at a column <= mv
             while (lo < hi) {
                 const int32_t mid = (lo + hi + 1) >> 1;
                 if (__ldg(A.col + rbase + mid * kCap) <= mv) lo = mid; else hi = mid - 1;
@@ -533,110 +649,116 @@ __device__ void long_row(const SupportArgs &A, SupportSmem &sm, int32_t rbase, i
             const int32_t ps = rbase + p * kCap;
             const int32_t plen = min(kCap, L - p * kCap);
             const int32_t vhi = (p + 1 < npieces) ? __ldg(A.col + ps + plen) : kIntMax;
-            const int tsize = table_size_for(plen);
-            const uint32_t mask = uint32_t(tsize / 4 - 1);
-            clear_table(sm, tsize, plen, tid);
-            if (tid == 0) sm.ctl[1] = 0;
-            __syncthreads();
-            for (int k = tid; k < plen; k += kThreads)
-                table_insert(sm.keys, sm.slots, mask, 0, __ldg(A.col + ps + k), k);
-            __syncthreads();
-            for (;;) {
-                int32_t j = 0;
-                if (lane == 0) j = atomicAdd(&sm.ctl[1], 1);
-                j = __shfl_sync(0xffffffffu, j, 0);
-                if (j >= nb) break;
-                int32_t k = sm.u.lg.cur[j];
-                const int32_t ke = sm.u.lg.end[j];
-                if (k >= ke) continue;
-                int32_t own = 0;
-                for (;;) {
-                    const int32_t x = k + lane;
-                    const int32_t w = x < ke ? __ldg(A.col + x) : kIntMax;
-                    const bool in = w < vhi;
-                    if (in) {
-                        const int32_t q = table_find(sm.keys, sm.slots, mask, 0, w, 0, plen);
-                        if (q >= 0) {
-                            atomicAdd(&sm.cnt[q], 1);
-                            atomicAdd(A.S + x, 1);
-                            ++own;
+            // run of segment tid: its probes below vhi (binary search)
+            int32_t k = 0, cnt_in = 0, left = 0;
+            if (tid < nb) {
+                // galloping search for the first probe >= vhi in [cur, end)
+                k = sm.cur[tid];
+                const int32_t ke = sm.end[tid];
+                int32_t lo = k, hi = ke;
+                if (k < ke && __ldg(A.col + k) < vhi) {
+                    lo = k + 1;
+                    for (int32_t step = 1;; step <<= 1) {
+                        const int32_t t = k + step;
+                        if (t >= ke) break;
+                        if (__ldg(A.col + t) >= vhi) {
+                            hi = t;
+                            break;
                         }
+                        lo = t + 1;
                     }
-                    const int32_t nin = __popc(__ballot_sync(0xffffffffu, in));
-                    k += nin;
-                    if (nin < 32) break;
+                    while (lo < hi) {
+                        const int32_t mid = (lo + hi) >> 1;
+                        if (__ldg(A.col + mid) < vhi) lo = mid + 1; else hi = mid;
+                    }
+                } else {
+                    hi = k;
+                    lo = k;
                 }
-                own = __reduce_add_sync(0xffffffffu, own);
-                if (lane == 0) {
-                    sm.u.lg.cur[j] = k;
-                    sm.u.lg.own[j] += own;
+                cnt_in = lo - k;
+                left = ke - lo;
+            }
+            int32_t nruns, items;
+            build_runs(sm, cnt_in, k, 0, tid, nruns, items);
+            if (items > 0) {
+                const int lb = region_lb(plen);
+                clear_table(sm, 1 << lb, plen, tid);
+                __syncthreads();
+                for (int q = tid; q < plen; q += kThreads)
+                    table_insert(sm.keys, sm.slots, 0, lb, __ldg(A.col + ps + q), q);
+                __syncthreads();
+                probe_runs(A, sm, nruns, items, true, lb);
+                __syncthreads();
+                for (int q = tid; q < plen; q += kThreads) {
+                    const int32_t v = sm.cnt[q];
+                    if (v) atomicAdd(A.S + ps + q, v);
                 }
+                if (tid < nb) sm.cur[tid] = k + cnt_in;
             }
-            __syncthreads();
-            for (int k = tid; k < plen; k += kThreads) {
-                const int32_t v = sm.cnt[k];
-                if (v) atomicAdd(A.S + ps + k, v);
-            }
-            int32_t left = 0;
-            for (int j = tid; j < nb; j += kThreads) left |= sm.u.lg.cur[j] < sm.u.lg.end[j];
-            if (!__syncthreads_or(left)) break;  // every cursor exhausted
+            if (!__syncthreads_or(left > 0)) break;  // every segment exhausted
         }
-        __syncthreads();
-        for (int j = tid; j < nb; j += kThreads) {
-            const int32_t v = sm.u.lg.own[j];
-            if (v) {
-                atomicAdd(A.S + sm.u.lg.owner[j], v);
-                tri += v;
-            }
-        }
+        flush_owners(A, sm, nb, tri);
         __syncthreads();
     }
 }
 
 // Forms a stage of consecutive short active rows starting at active row a
-// (warp 0): rows a .. a+nr-1 with total length <= kCap and nr <= kStageRows.
+// (warp 0): rows a .. a+nr-1 with total length <= kCap, total region size
+// <= kTable / 4 buckets and nr <= kStageRows.
 __device__ void form_stage(const SupportArgs &A, SupportSmem &sm, int32_t a, int32_t ab) {
     const int lane = threadIdx.x & 31;
-    int32_t acc = 0, nr = 0;
+    constexpr int32_t kBuckets = kTable / 4;
+    int32_t acc = 0, accb = 0, nr = 0;
     for (;;) {
         const int32_t ai = a + nr + lane;
-        int32_t len = -1, gb = 0, sgb = 0;
+        int32_t len = -1, gb = 0, sgb = 0, lb = 1;
         if (ai <= ab && nr + lane < kStageRows) {
             const int32_t rr = __ldg(A.arow + ai);
             gb = __ldg(A.rp + rr);
             len = __ldg(A.rp + rr + 1) - gb;
             sgb = __ldg(A.aseg + ai);
             if (len > kCap) len = -1;
+            else lb = region_lb(len);
         }
-        // inclusive prefix of lengths, saturating above kCap (ineligible rows
-        // count as kCap + 1 so that every later lane fails too)
+        // inclusive prefixes of lengths and region sizes, saturating (an
+        // ineligible row counts as too large, so every later lane fails too)
         int32_t incl = len < 0 ? kCap + 1 : len;
+        int32_t inclb = len < 0 ? kBuckets + 1 : (1 << lb);
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
             const int32_t u = __shfl_up_sync(0xffffffffu, incl, d);
-            if (lane >= d) incl = min(incl + u, kCap + 1);
+            const int32_t ub = __shfl_up_sync(0xffffffffu, inclb, d);
+            if (lane >= d) {
+                incl = min(incl + u, kCap + 1);
+                inclb = min(inclb + ub, kBuckets + 1);
+            }
         }
-        const bool ok = len >= 0 && acc + incl <= kCap;
+        const bool ok = len >= 0 && acc + incl <= kCap && accb + inclb <= kBuckets;
         const uint32_t okm = __ballot_sync(0xffffffffu, ok);
         const int tk = okm == 0xffffffffu ? 32 : __ffs(~okm) - 1;  // ok is a lane prefix
         if (lane < tk) {
-            sm.u.st.gbase[nr + lane] = gb;
-            sm.u.st.loc[nr + lane] = acc + incl - len;
-            sm.u.st.segb[nr + lane] = sgb;
+            sm.gbase[nr + lane] = gb;
+            sm.loc[nr + lane] = acc + incl - len;
+            sm.segb[nr + lane] = sgb;
+            sm.tbase[nr + lane] = accb + inclb - (1 << lb);
+            sm.tlb[nr + lane] = lb;
         }
-        if (tk > 0) acc += __shfl_sync(0xffffffffu, incl, tk - 1);
+        if (tk > 0) {
+            acc += __shfl_sync(0xffffffffu, incl, tk - 1);
+            accb += __shfl_sync(0xffffffffu, inclb, tk - 1);
+        }
         nr += tk;
         if (tk < 32) break;
     }
     if (lane == 0) {
-        sm.u.st.loc[nr] = acc;
-        sm.u.st.segb[nr] = __ldg(A.aseg + a + nr);
+        sm.loc[nr] = acc;
+        sm.tbase[nr] = accb;
+        sm.segb[nr] = __ldg(A.aseg + a + nr);
         sm.ctl[3] = nr;
-        sm.ctl[1] = 0;
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 3)
+__global__ void __launch_bounds__(kThreads, 1)
 support_kernel(SupportArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SupportSmem &sm = *reinterpret_cast<SupportSmem *>(smem_raw);
@@ -667,47 +789,47 @@ support_kernel(SupportArgs A) {
                 ++a;
                 continue;
             }
+            // ------------------------------------- stage of short staged rows
             if (warp == 0) form_stage(A, sm, a, ab);
             __syncthreads();
             const int32_t nr = sm.ctl[3];
-            const int32_t slen = sm.u.st.loc[nr];
-            const int tsize = table_size_for(slen);
-            const uint32_t mask = uint32_t(tsize / 4 - 1);
-            clear_table(sm, tsize, slen, tid);
+            const int32_t slen = sm.loc[nr];
+            clear_table(sm, sm.tbase[nr], slen, tid);
             __syncthreads();
             for (int k = tid; k < slen; k += kThreads) {
-                const int32_t lr = last_le(sm.u.st.loc, 0, nr - 1, k);
-                const int32_t g = sm.u.st.gbase[lr] + (k - sm.u.st.loc[lr]);
-                table_insert(sm.keys, sm.slots, mask, lr, __ldg(A.col + g), k);
+                const int32_t lr = last_le(sm.loc, 0, nr - 1, k);
+                const int32_t g = sm.gbase[lr] + (k - sm.loc[lr]);
+                table_insert(sm.keys, sm.slots, sm.tbase[lr], sm.tlb[lr], __ldg(A.col + g), k);
             }
             __syncthreads();
-            const int32_t sLo = max(pa, sm.u.st.segb[0]);
-            const int32_t sHi = min(pb + 1, sm.u.st.segb[nr]);
-            for (;;) {
-                int32_t pos = 0;
-                if (lane == 0) pos = sLo + atomicAdd(&sm.ctl[1], 1);
-                pos = __shfl_sync(0xffffffffu, pos, 0);
-                if (pos >= sHi) break;
-                const long long base = __ldg(A.wp + pos);
-                const int32_t ka = int32_t(max(iA, base) - base);
-                const int32_t kb = int32_t(min(iB, __ldg(A.wp + pos + 1)) - base);
-                if (ka >= kb) continue;
-                const int32_t lr = last_le(sm.u.st.segb, 0, nr - 1, pos);
-                const int32_t p0 = __ldg(A.pst + pos);
-                int32_t own = probe_range(A, sm, mask, lr, sm.u.st.loc[lr], sm.u.st.loc[lr + 1],
-                                          p0 + ka, p0 + kb, lane);
-                own = __reduce_add_sync(0xffffffffu, own);
-                if (lane == 0 && own) {
-                    atomicAdd(A.S + __ldg(A.seg + pos), own);
-                    tri += own;
+            const int32_t sLo = max(pa, sm.segb[0]);
+            const int32_t sHi = min(pb + 1, sm.segb[nr]);
+            for (int32_t sb = sLo; sb < sHi; sb += kBatch) {
+                const int32_t nb = min(kBatch, sHi - sb);
+                int32_t len = 0, pos0 = 0, key = 0;
+                if (tid < nb) {
+                    const int32_t pos = sb + tid;
+                    const long long base = __ldg(A.wp + pos);
+                    const int32_t ka = int32_t(max(iA, base) - base);
+                    const int32_t kb = int32_t(min(iB, __ldg(A.wp + pos + 1)) - base);
+                    len = kb - ka;
+                    pos0 = __ldg(A.pst + pos) + ka;
+                    key = __ldg(A.sact + pos) - a;
+                    sm.owner[tid] = __ldg(A.seg + pos);
+                    sm.hit[tid] = 0;
                 }
+                int32_t nruns, items;
+                build_runs(sm, len, pos0, key, tid, nruns, items);
+                if (items > 0) probe_runs(A, sm, nruns, items, false, 0);
+                __syncthreads();
+                flush_owners(A, sm, nb, tri);
+                __syncthreads();
             }
-            __syncthreads();
             for (int k = tid; k < slen; k += kThreads) {
                 const int32_t v = sm.cnt[k];
                 if (v) {
-                    const int32_t lr = last_le(sm.u.st.loc, 0, nr - 1, k);
-                    atomicAdd(A.S + sm.u.st.gbase[lr] + (k - sm.u.st.loc[lr]), v);
+                    const int32_t lr = last_le(sm.loc, 0, nr - 1, k);
+                    atomicAdd(A.S + sm.gbase[lr] + (k - sm.loc[lr]), v);
                 }
             }
             __syncthreads();
@@ -739,7 +861,7 @@ cudaError_t configure_once() {
 size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Carve {
-    int32_t *ekey, *epst, *eitems, *seg, *pst, *sitems;
+    int32_t *ekey, *epst, *eitems, *seg, *pst, *sitems, *sact;
     long long *wp;
     int32_t *rcount, *rstart, *arank, *arow, *aseg;
     Pair *rtile_sum, *rtile_off, *rtot;
@@ -766,6 +888,7 @@ size_t carve(void *base, int32_t n, int64_t m, Carve *c) {
     c->seg = reinterpret_cast<int32_t *>(take(size_t(m + 1) * 4));
     c->pst = reinterpret_cast<int32_t *>(take(size_t(m + 1) * 4));
     c->sitems = reinterpret_cast<int32_t *>(take(size_t(m + 1) * 4));
+    c->sact = reinterpret_cast<int32_t *>(take(size_t(m + 1) * 4));
     c->wp = reinterpret_cast<long long *>(take(size_t(m + 2) * 8));
     c->rcount = reinterpret_cast<int32_t *>(take(size_t(n + 1) * 4));
     c->rstart = reinterpret_cast<int32_t *>(take(size_t(n + 1) * 4));
@@ -839,7 +962,8 @@ cudaError_t launch_support_balanced(const Live &g, int32_t *S, RoundCounters *cn
     active_rows_kernel<<<int((rows + 255) / 256), 256, 0, s>>>(c.rcount, c.rstart, c.arank,
                                                                c.rtot, n, c.arow, c.aseg);
     scatter_kernel<<<(m + 255) / 256, 256, 0, s>>>(c.ekey, c.epst, c.eitems, m, c.rstart,
-                                                   c.rcount, c.seg, c.pst, c.sitems);
+                                                   c.arank, c.rcount, c.seg, c.pst, c.sitems,
+                                                   c.sact);
     // item scan over the segments (at most m of them; entries past nseg are 0)
     const int32_t itiles = int32_t((int64_t(m) + kScanTile - 1) / kScanTile);
     ItemLoad il{c.sitems, c.rtot};
@@ -857,8 +981,8 @@ cudaError_t launch_support_balanced(const Live &g, int32_t *S, RoundCounters *cn
         e = cudaEventRecord(ev[1], s);
         if (e != cudaSuccess) return e;
     }
-    SupportArgs A{g.rp, g.col, c.seg, c.pst, c.wp, c.arow, c.aseg, c.plan, c.bound, c.sched, S,
-                  &cnt->triangles};
+    SupportArgs A{g.rp, g.col, c.seg, c.pst, c.sact, c.wp, c.arow, c.aseg, c.plan, c.bound,
+                  c.sched, S, &cnt->triangles};
     support_kernel<<<g_support_blocks, kThreads, sizeof(SupportSmem), s>>>(A);
     *launches += 1;
     return cudaGetLastError();
