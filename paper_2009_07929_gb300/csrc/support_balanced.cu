@@ -40,13 +40,30 @@ namespace kt {
 namespace {
 
 // ----------------------------------------------------------- configuration
-constexpr int kThreads = 1024;          // threads per support CTA (one CTA per SM)
-constexpr int kCap = 4096;              // staged slots per stage or piece
+#ifndef KT_SUPPORT_THREADS
+#define KT_SUPPORT_THREADS 1024
+#endif
+#ifndef KT_SUPPORT_CAP
+#define KT_SUPPORT_CAP 8192
+#endif
+#ifndef KT_SUPPORT_UNROLL
+#define KT_SUPPORT_UNROLL 4
+#endif
+#ifndef KT_SUPPORT_MIN_CTAS
+#define KT_SUPPORT_MIN_CTAS 1
+#endif
+constexpr int kThreads = KT_SUPPORT_THREADS;  // threads per support CTA
+constexpr int kCap = KT_SUPPORT_CAP;          // staged slots per stage or piece
 constexpr int kTable = 4 * kCap;        // hash entries (load factor <= 1/4)
 constexpr int kStageRows = 256;         // staged rows per stage
 constexpr int kWarps = kThreads / 32;
 constexpr int kBatch = kThreads;        // segments per batch (one per thread)
-constexpr int kUnroll = 4;              // 32-item windows in flight per warp
+constexpr int kUnroll = KT_SUPPORT_UNROLL;  // 32-item windows in flight per warp
+#ifndef KT_SUPPORT_GRAIN
+#define KT_SUPPORT_GRAIN 0
+#endif
+// Items a warp takes from a batch at a time; 0 = an even static split.
+constexpr int kGrain = KT_SUPPORT_GRAIN;
 constexpr long long kChunkMin = 65536;  // items per chunk (minimum)
 constexpr int kChunksPerCta = 16;       // target chunks per resident CTA
 constexpr int kMaxChunks = 1 << 17;     // chunk table capacity
@@ -57,7 +74,6 @@ constexpr int kScanTile = kScanThreads * kScanPer;
 constexpr int kEdgeThreads = 256;
 constexpr int kEdgesPerThread = 16;
 
-constexpr int32_t kEmpty = -1;
 constexpr int32_t kIntMax = 0x7fffffff;
 
 // sched[] words
@@ -124,50 +140,68 @@ struct RowWalk {
 };
 
 // ------------------------------------------------------------ hash table
-// Every staged row gets its own power-of-two region of the shared table made
-// of buckets of 4 int32 keys (one 16-byte shared load per probe), with a
-// parallel array of 16-bit local slots.  A region has at least 2 buckets and
-// is at most a quarter full, so a probe rarely needs a second bucket.  Entries of a bucket fill in order (an insert tries
-// the next entry only when the previous one is taken), so a bucket whose last
-// key is free ends a search.
-constexpr uint32_t kHashMul = 0x9E3779B1u;  // Fibonacci hashing: top bits of w * 2^32/phi
+// Every staged row gets its own power-of-two region of the shared table.  A
+// bucket holds 4 entries: a 32-bit word of four 8-bit fingerprints (0 = free)
+// and four 16-bit local slots; the staged columns themselves sit in a plain
+// array (vals) indexed by local slot.  A probe loads one fingerprint word,
+// compares its four bytes at once and reads a slot and a column only for a
+// fingerprint match, so a miss costs a single 4-byte shared load.  Entries of
+// a bucket fill in order, so a bucket whose last fingerprint is free ends a
+// search.  A region has at least 2 buckets and at most one key per 4 entries.
+constexpr uint32_t kHashMul = 0x9E3779B1u;  // Fibonacci hashing: top bits select the bucket
+constexpr uint32_t kFpMul = 0x85EBCA6Bu;    // independent multiplier for the fingerprint
 
-// log2 of the bucket count of the region of a row of length len (4 entries
-// per bucket, at least 4 entries per key).
+// log2 of the bucket count of the region of a row of length len.
 __device__ __forceinline__ int region_lb(int32_t len) {
     int lb = 1;
     while ((1 << lb) < len) ++lb;
     return lb;
 }
 
-__device__ __forceinline__ void table_insert(int32_t *keys, uint16_t *slots, int32_t bbase,
-                                             int lb, int32_t w, int32_t s) {
+// Fingerprint in [1, 255] (never 0, which marks a free entry).
+__device__ __forceinline__ uint32_t fingerprint(int32_t w) {
+    return ((uint32_t(w) * kFpMul) >> 24) | 1u;
+}
+
+__device__ __forceinline__ void table_insert(uint32_t *fpw, uint16_t *slots, int32_t bbase, int lb,
+                                             int32_t w, int32_t s) {
     const uint32_t bm = (1u << lb) - 1u;
+    const uint32_t fp = fingerprint(w);
     uint32_t b = (uint32_t(w) * kHashMul) >> (32 - lb);
     for (;;) {
-        const int32_t at = 4 * (bbase + int32_t(b));
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            if (atomicCAS(keys + at + j, kEmpty, w) == kEmpty) {
-                slots[at + j] = uint16_t(s);
+        const int32_t at = bbase + int32_t(b);
+        uint32_t old = fpw[at];
+        while ((old >> 24) == 0) {  // bucket not full: take its first free entry
+            const int j = old == 0 ? 0 : (old >> 16) ? 3 : (old >> 8) ? 2 : 1;
+            const uint32_t prev = atomicCAS(fpw + at, old, old | (fp << (8 * j)));
+            if (prev == old) {
+                slots[4 * at + j] = uint16_t(s);
                 return;
             }
+            old = prev;
         }
         b = (b + 1) & bm;
     }
 }
 
 // Local slot of column w in the region (bbase, lb), or -1.
-__device__ __forceinline__ int32_t table_find(const int32_t *keys, const uint16_t *slots,
-                                              int32_t bbase, int lb, int32_t w) {
+__device__ __forceinline__ int32_t table_find(const uint32_t *fpw, const uint16_t *slots,
+                                              const int32_t *vals, int32_t bbase, int lb,
+                                              int32_t w) {
     const uint32_t bm = (1u << lb) - 1u;
+    const uint32_t fp4 = fingerprint(w) * 0x01010101u;
     uint32_t b = (uint32_t(w) * kHashMul) >> (32 - lb);
     for (;;) {
         const int32_t at = bbase + int32_t(b);
-        const int4 k = reinterpret_cast<const int4 *>(keys)[at];
-        const int j = k.x == w ? 0 : k.y == w ? 1 : k.z == w ? 2 : k.w == w ? 3 : -1;
-        if (j >= 0) return slots[4 * at + j];
-        if (k.w == kEmpty) return -1;
+        const uint32_t word = fpw[at];
+        uint32_t mm = __vcmpeq4(word, fp4);
+        while (mm) {
+            const int j = (__ffs(mm) - 1) >> 3;
+            const int32_t sl = slots[4 * at + j];
+            if (vals[sl] == w) return sl;
+            mm &= ~(0xFFu << (8 * j));
+        }
+        if ((word >> 24) == 0) return -1;
         b = (b + 1) & bm;
     }
 }
@@ -430,8 +464,9 @@ __global__ void partition_kernel(const long long *__restrict__ wp, const int32_t
 // ------------------------------------------------------------ support kernel
 // Shared memory of one support CTA.
 struct SupportSmem {
-    int32_t keys[kTable];             // hash keys (columns), kEmpty when free
-    uint16_t slots[kTable];           // local staged slot of each key
+    uint32_t fpw[kTable / 4];         // fingerprint word of each bucket
+    uint16_t slots[kTable];           // local staged slot of each entry
+    int32_t vals[kCap];               // staged columns by local slot
     int32_t cnt[kCap];                // credits to staged slots
     int32_t gbase[kStageRows];        // stage: global slot of each row's first element
     int32_t loc[kStageRows + 1];      // stage: local slot offsets of the rows
@@ -449,6 +484,7 @@ struct SupportSmem {
     int32_t wtmp[64];
     int32_t ctl[64];
 };
+static_assert(sizeof(SupportSmem) <= 227 * 1024, "support CTA exceeds shared memory");
 
 struct SupportArgs {
     const int32_t *rp, *col;
@@ -502,80 +538,100 @@ __device__ __forceinline__ void build_runs(SupportSmem &sm, int32_t len, int32_t
         sm.rkey[ridx] = key;
         sm.rseg[ridx] = j;
     }
-    if (threadIdx.x == 0) sm.rstart[nruns] = items;
+    if (threadIdx.x == 0) {
+        sm.rstart[nruns] = items;
+        sm.ctl[4] = 0;
+    }
     __syncthreads();
 }
 
-// Flattened probing of the runs of a batch.  The batch's items are split
-// evenly over the warps.  Where a warp's next 32 items lie inside one run, the
-// run's parameters are warp-uniform and a tight loop streams its windows
-// (kUnroll loads in flight per lane), counting the owner's hits in a register.
-// A window that crosses run boundaries maps each lane to its run with a
-// bitmask of the run starts inside the window.  single = true: the staged
-// rows are one piece whose region is (0, piece_lb).
-__device__ __forceinline__ void probe_runs(const SupportArgs &A, SupportSmem &sm, int32_t nruns,
-                                           int32_t items, bool single, int piece_lb) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int32_t per = ((items + kWarps - 1) / kWarps + 31) & ~31;
-    const int32_t w0 = warp * per;
-    const int32_t w1 = min(items, w0 + per);
-    if (w0 >= w1) return;
-    int32_t E = last_le(sm.rstart, 0, nruns - 1, w0);
-    int32_t pos = w0;
-    while (pos < w1) {
-        while (E + 1 < nruns && sm.rstart[E + 1] <= pos) ++E;
-        const int32_t rend = min(w1, E + 1 < nruns ? sm.rstart[E + 1] : items);
-        if (rend - pos >= 32) {
-            // ---- whole windows of run E
-            const int32_t nwin = (rend - pos) >> 5;
-            const int32_t xb = sm.rpos[E] + (pos - sm.rstart[E]) + lane;
+// Probes of the items [p, pe) of a batch's flat item space (p in run E).
+// Where the next 32 items lie inside one run, the run's parameters are
+// warp-uniform and a tight loop streams its windows (kUnroll loads in flight
+// per lane), counting the owner's hits in a register; a window that crosses
+// run boundaries maps each lane to its run with a bitmask of the run starts
+// inside the window.  single = true: one staged piece, region (0, piece_lb).
+__device__ __forceinline__ void probe_range(const SupportArgs &A, SupportSmem &sm, int32_t nruns,
+                                            int32_t items, int32_t E, int32_t p, int32_t pe,
+                                            bool single, int piece_lb) {
+    const int lane = threadIdx.x & 31;
+    while (p < pe) {
+        while (E + 1 < nruns && sm.rstart[E + 1] <= p) ++E;
+        const int32_t rend = min(pe, E + 1 < nruns ? sm.rstart[E + 1] : items);
+        if (rend - p >= 32) {
+            // ---- whole windows of run E: warp-uniform parameters
+            const int32_t nwin = (rend - p) >> 5;
             const int32_t key = single ? 0 : sm.rkey[E];
             const int32_t bb = single ? 0 : sm.tbase[key];
             const int lb = single ? piece_lb : sm.tlb[key];
+            const uint32_t bm = (1u << lb) - 1u;
+            const int sh = 32 - lb;
+            const int32_t *__restrict__ src = A.col + sm.rpos[E] + (p - sm.rstart[E]) + lane;
+            int32_t *__restrict__ dst = A.S + (src - A.col);
             int32_t own = 0;
             int32_t i = 0;
             for (; i + kUnroll <= nwin; i += kUnroll) {
                 int32_t wv[kUnroll];
 #pragma unroll
-                for (int u = 0; u < kUnroll; ++u) wv[u] = __ldg(A.col + xb + 32 * (i + u));
+                for (int u = 0; u < kUnroll; ++u) wv[u] = __ldg(src + 32 * (i + u));
 #pragma unroll
                 for (int u = 0; u < kUnroll; ++u) {
-                    const int32_t q = table_find(sm.keys, sm.slots, bb, lb, wv[u]);
-                    if (q >= 0) {
-                        atomicAdd(&sm.cnt[q], 1);
-                        atomicAdd(A.S + xb + 32 * (i + u), 1);
-                        ++own;
+                    const int32_t w = wv[u];
+                    const uint32_t fp4 = fingerprint(w) * 0x01010101u;
+                    uint32_t b = (uint32_t(w) * kHashMul) >> sh;
+                    for (;;) {
+                        const int32_t at = bb + int32_t(b);
+                        const uint32_t word = sm.fpw[at];
+                        uint32_t mm = __vcmpeq4(word, fp4);
+                        int32_t q = -1;
+                        while (mm) {
+                            const int j = (__ffs(mm) - 1) >> 3;
+                            const int32_t sl = sm.slots[4 * at + j];
+                            if (sm.vals[sl] == w) {
+                                q = sl;
+                                break;
+                            }
+                            mm &= ~(0xFFu << (8 * j));
+                        }
+                        if (q >= 0) {
+                            atomicAdd(&sm.cnt[q], 1);
+                            atomicAdd(dst + 32 * (i + u), 1);
+                            ++own;
+                            break;
+                        }
+                        if ((word >> 24) == 0) break;
+                        b = (b + 1) & bm;
                     }
                 }
             }
             for (; i < nwin; ++i) {
-                const int32_t q = table_find(sm.keys, sm.slots, bb, lb, __ldg(A.col + xb + 32 * i));
+                const int32_t q = table_find(sm.fpw, sm.slots, sm.vals, bb, lb, __ldg(src + 32 * i));
                 if (q >= 0) {
                     atomicAdd(&sm.cnt[q], 1);
-                    atomicAdd(A.S + xb + 32 * i, 1);
+                    atomicAdd(dst + 32 * i, 1);
                     ++own;
                 }
             }
             own = __reduce_add_sync(0xffffffffu, own);
             if (lane == 0 && own) atomicAdd(&sm.hit[sm.rseg[E]], own);
-            pos += nwin * 32;
+            p += nwin * 32;
         } else {
             // ---- one window crossing run boundaries
             int32_t r = E;
-            if (E + 1 < nruns && sm.rstart[E + 1] < pos + 32) {
+            if (E + 1 < nruns && sm.rstart[E + 1] < p + 32) {
                 const int32_t j = E + 1 + lane;
                 const int32_t s = j < nruns ? sm.rstart[j] : kIntMax;
-                const int32_t rel = s - pos;
+                const int32_t rel = s - p;
                 const uint32_t bits = __reduce_or_sync(0xffffffffu, rel < 32 ? (1u << rel) : 0u);
                 r = E + __popc(bits & (0xffffffffu >> (31 - lane)));
             }
-            const int32_t item = pos + lane;
-            if (item < w1) {
+            const int32_t item = p + lane;
+            if (item < pe) {
                 const int32_t x = sm.rpos[r] + (item - sm.rstart[r]);
                 const int32_t key = single ? 0 : sm.rkey[r];
                 const int32_t bb = single ? 0 : sm.tbase[key];
                 const int lb = single ? piece_lb : sm.tlb[key];
-                const int32_t q = table_find(sm.keys, sm.slots, bb, lb, __ldg(A.col + x));
+                const int32_t q = table_find(sm.fpw, sm.slots, sm.vals, bb, lb, __ldg(A.col + x));
                 if (q >= 0) {
                     atomicAdd(&sm.cnt[q], 1);
                     atomicAdd(A.S + x, 1);
@@ -583,14 +639,38 @@ __device__ __forceinline__ void probe_runs(const SupportArgs &A, SupportSmem &sm
                 }
             }
             E = __shfl_sync(0xffffffffu, r, 31);
-            pos += 32;
+            p += 32;
+        }
+    }
+}
+
+// Probing of all runs of a batch: an even split of the items over the warps
+// (kGrain == 0), or grains of kGrain items taken from a shared counter
+// (sm.ctl[4], zero on entry) until the batch is exhausted.
+__device__ __forceinline__ void probe_runs(const SupportArgs &A, SupportSmem &sm, int32_t nruns,
+                                           int32_t items, bool single, int piece_lb) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if constexpr (kGrain == 0) {
+        const int32_t per = ((items + kWarps - 1) / kWarps + 31) & ~31;
+        const int32_t w0 = warp * per;
+        const int32_t w1 = min(items, w0 + per);
+        if (w0 < w1)
+            probe_range(A, sm, nruns, items, last_le(sm.rstart, 0, nruns - 1, w0), w0, w1,
+                        single, piece_lb);
+    } else {
+        for (;;) {
+            int32_t g = 0;
+            if (lane == 0) g = atomicAdd(&sm.ctl[4], kGrain);
+            g = __shfl_sync(0xffffffffu, g, 0);
+            if (g >= items) break;
+            const int32_t E = last_le(sm.rstart, 0, nruns - 1, g);
+            probe_range(A, sm, nruns, items, E, g, min(items, g + kGrain), single, piece_lb);
         }
     }
 }
 
 __device__ __forceinline__ void clear_table(SupportSmem &sm, int32_t buckets, int32_t len, int tid) {
-    for (int k = tid; k < buckets; k += kThreads)
-        reinterpret_cast<int4 *>(sm.keys)[k] = make_int4(kEmpty, kEmpty, kEmpty, kEmpty);
+    for (int k = tid; k < buckets; k += kThreads) sm.fpw[k] = 0u;
     for (int k = tid; k < len; k += kThreads) sm.cnt[k] = 0;
 }
 
@@ -684,8 +764,11 @@ __device__ void long_row(const SupportArgs &A, SupportSmem &sm, int32_t rbase, i
                 const int lb = region_lb(plen);
                 clear_table(sm, 1 << lb, plen, tid);
                 __syncthreads();
-                for (int q = tid; q < plen; q += kThreads)
-                    table_insert(sm.keys, sm.slots, 0, lb, __ldg(A.col + ps + q), q);
+                for (int q = tid; q < plen; q += kThreads) {
+                    const int32_t w = __ldg(A.col + ps + q);
+                    sm.vals[q] = w;
+                    table_insert(sm.fpw, sm.slots, 0, lb, w, q);
+                }
                 __syncthreads();
                 probe_runs(A, sm, nruns, items, true, lb);
                 __syncthreads();
@@ -758,7 +841,7 @@ __device__ void form_stage(const SupportArgs &A, SupportSmem &sm, int32_t a, int
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, KT_SUPPORT_MIN_CTAS)
 support_kernel(SupportArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SupportSmem &sm = *reinterpret_cast<SupportSmem *>(smem_raw);
@@ -799,7 +882,9 @@ support_kernel(SupportArgs A) {
             for (int k = tid; k < slen; k += kThreads) {
                 const int32_t lr = last_le(sm.loc, 0, nr - 1, k);
                 const int32_t g = sm.gbase[lr] + (k - sm.loc[lr]);
-                table_insert(sm.keys, sm.slots, sm.tbase[lr], sm.tlb[lr], __ldg(A.col + g), k);
+                const int32_t w = __ldg(A.col + g);
+                sm.vals[k] = w;
+                table_insert(sm.fpw, sm.slots, sm.tbase[lr], sm.tlb[lr], w, k);
             }
             __syncthreads();
             const int32_t sLo = max(pa, sm.segb[0]);
