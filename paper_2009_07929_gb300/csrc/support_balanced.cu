@@ -59,6 +59,7 @@ constexpr int kStageRows = 256;         // staged rows per stage
 constexpr int kWarps = kThreads / 32;
 constexpr int kBatch = kThreads;        // segments per batch (one per thread)
 constexpr int kUnroll = KT_SUPPORT_UNROLL;  // 32-item windows in flight per warp
+constexpr int kMixUnroll = 2;           // run-crossing windows in flight per warp
 #ifndef KT_SUPPORT_GRAIN
 #define KT_SUPPORT_GRAIN 0
 #endif
@@ -163,6 +164,17 @@ __device__ __forceinline__ uint32_t fingerprint(int32_t w) {
     return ((uint32_t(w) * kFpMul) >> 24) | 1u;
 }
 
+// Bit 7 of byte j is set exactly where byte j of word equals the fingerprint
+// replicated in fp4: a byte of x = word ^ fp4 is zero iff neither its low 7
+// bits (which would carry into bit 7 when 0x7F is added) nor its bit 7 is
+// set.  The addition never carries across bytes, so no other byte is flagged;
+// in particular a free entry (byte 0) never matches, since fingerprints are
+// never 0.
+__device__ __forceinline__ uint32_t match_bytes(uint32_t word, uint32_t fp4) {
+    const uint32_t x = word ^ fp4;
+    return ~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x | 0x7F7F7F7Fu);
+}
+
 __device__ __forceinline__ void table_insert(uint32_t *fpw, uint16_t *slots, int32_t bbase, int lb,
                                              int32_t w, int32_t s) {
     const uint32_t bm = (1u << lb) - 1u;
@@ -194,12 +206,9 @@ __device__ __forceinline__ int32_t table_find(const uint32_t *fpw, const uint16_
     for (;;) {
         const int32_t at = bbase + int32_t(b);
         const uint32_t word = fpw[at];
-        uint32_t mm = __vcmpeq4(word, fp4);
-        while (mm) {
-            const int j = (__ffs(mm) - 1) >> 3;
-            const int32_t sl = slots[4 * at + j];
+        for (uint32_t mm = match_bytes(word, fp4); mm; mm &= mm - 1u) {
+            const int32_t sl = slots[4 * at + ((__ffs(mm) - 1) >> 3)];
             if (vals[sl] == w) return sl;
-            mm &= ~(0xFFu << (8 * j));
         }
         if ((word >> 24) == 0) return -1;
         b = (b + 1) & bm;
@@ -582,16 +591,13 @@ __device__ __forceinline__ void probe_range(const SupportArgs &A, SupportSmem &s
                     for (;;) {
                         const int32_t at = bb + int32_t(b);
                         const uint32_t word = sm.fpw[at];
-                        uint32_t mm = __vcmpeq4(word, fp4);
                         int32_t q = -1;
-                        while (mm) {
-                            const int j = (__ffs(mm) - 1) >> 3;
-                            const int32_t sl = sm.slots[4 * at + j];
+                        for (uint32_t mm = match_bytes(word, fp4); mm; mm &= mm - 1u) {
+                            const int32_t sl = sm.slots[4 * at + ((__ffs(mm) - 1) >> 3)];
                             if (sm.vals[sl] == w) {
                                 q = sl;
                                 break;
                             }
-                            mm &= ~(0xFFu << (8 * j));
                         }
                         if (q >= 0) {
                             atomicAdd(&sm.cnt[q], 1);
@@ -616,30 +622,47 @@ __device__ __forceinline__ void probe_range(const SupportArgs &A, SupportSmem &s
             if (lane == 0 && own) atomicAdd(&sm.hit[sm.rseg[E]], own);
             p += nwin * 32;
         } else {
-            // ---- one window crossing run boundaries
-            int32_t r = E;
-            if (E + 1 < nruns && sm.rstart[E + 1] < p + 32) {
+            // ---- windows crossing run boundaries: map lanes to runs with a
+            // bitmask of the run starts in each window; up to kMixUnroll such
+            // windows have their loads in flight together
+            int32_t x[kMixUnroll], rr[kMixUnroll], wv[kMixUnroll];
+            bool ok[kMixUnroll];
+#pragma unroll
+            for (int u = 0; u < kMixUnroll; ++u) ok[u] = false;
+#pragma unroll
+            for (int u = 0; u < kMixUnroll; ++u) {
+                if (u > 0) {
+                    if (p >= pe) break;
+                    while (E + 1 < nruns && sm.rstart[E + 1] <= p) ++E;
+                    if (!(E + 1 < nruns && sm.rstart[E + 1] < p + 32)) break;
+                }
                 const int32_t j = E + 1 + lane;
-                const int32_t s = j < nruns ? sm.rstart[j] : kIntMax;
-                const int32_t rel = s - p;
+                const int32_t s0 = j < nruns ? sm.rstart[j] : kIntMax;
+                const int32_t rel = s0 - p;
                 const uint32_t bits = __reduce_or_sync(0xffffffffu, rel < 32 ? (1u << rel) : 0u);
-                r = E + __popc(bits & (0xffffffffu >> (31 - lane)));
+                const int32_t r = E + __popc(bits & (0xffffffffu >> (31 - lane)));
+                const int32_t item = p + lane;
+                ok[u] = item < pe;
+                rr[u] = r;
+                x[u] = sm.rpos[r] + (item - sm.rstart[r]);
+                E = __shfl_sync(0xffffffffu, r, 31);
+                p += 32;
             }
-            const int32_t item = p + lane;
-            if (item < pe) {
-                const int32_t x = sm.rpos[r] + (item - sm.rstart[r]);
-                const int32_t key = single ? 0 : sm.rkey[r];
+#pragma unroll
+            for (int u = 0; u < kMixUnroll; ++u) wv[u] = ok[u] ? __ldg(A.col + x[u]) : 0;
+#pragma unroll
+            for (int u = 0; u < kMixUnroll; ++u) {
+                if (!ok[u]) continue;
+                const int32_t key = single ? 0 : sm.rkey[rr[u]];
                 const int32_t bb = single ? 0 : sm.tbase[key];
                 const int lb = single ? piece_lb : sm.tlb[key];
-                const int32_t q = table_find(sm.fpw, sm.slots, sm.vals, bb, lb, __ldg(A.col + x));
+                const int32_t q = table_find(sm.fpw, sm.slots, sm.vals, bb, lb, wv[u]);
                 if (q >= 0) {
                     atomicAdd(&sm.cnt[q], 1);
-                    atomicAdd(A.S + x, 1);
-                    atomicAdd(&sm.hit[sm.rseg[r]], 1);
+                    atomicAdd(A.S + x[u], 1);
+                    atomicAdd(&sm.hit[sm.rseg[rr[u]]], 1);
                 }
             }
-            E = __shfl_sync(0xffffffffu, r, 31);
-            p += 32;
         }
     }
 }
