@@ -144,6 +144,35 @@ int ktruss_last_cuda_error(void);
 /* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
 int ktruss_version(void);
 
+/*
+ * Support of every edge of a graph that stays in the caller's device memory,
+ * computed without allocating any memory.  The paper has no counterpart: this
+ * entry point exists for callers that may not call cudaMalloc or any other
+ * allocating routine on their path (code running inside someone else's memory
+ * pool or arena, code that must not grow the device footprint after start-up,
+ * embedded users with a fixed memory budget).
+ *
+ * Computes what the first support step of ktruss_run computes: support_out[e]
+ * = number of triangles of the whole graph on edge e (so it equals the
+ * support_out of ktruss_run with K = 2), plus the triangle count.
+ *   n, m          vertex and edge count; at most 524288 each
+ *   row_ptr, col  strictly upper-triangular CSR in DEVICE memory (caller-owned)
+ *   support_out   int32[m] in DEVICE memory (caller-owned), overwritten
+ *   triangles_out host int64, may be NULL
+ *   cuda_stream   stream for all work; the call returns when it has finished
+ * Working memory is one fixed 32 MiB device array inside the library, held by
+ * every GPU that loads the library until the process exits.  All calls share
+ * it and it keeps the last call's contents; calls whose work overlaps on the
+ * GPU (other streams or host threads) race on it and must not be issued.  The
+ * first call on a device looks up the array's device address with that device
+ * current; make that first call before any stream capture.
+ * Returns KTRUSS_EINVAL for n or m out of range (including above 524288),
+ * NULL pointers or a malformed CSR (checked on the device first);
+ * KTRUSS_ECUDA for a failed CUDA call.
+ */
+int ktruss_support_noalloc(int32_t n, int64_t m, const int32_t *row_ptr, const int32_t *col,
+                           int32_t *support_out, int64_t *triangles_out, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -87,6 +87,8 @@ def lib():
         L.ktruss_graph_size.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i64)]
         L.ktruss_free.argtypes = [vp]
         L.ktruss_free.restype = None
+        L.ktruss_support_noalloc.argtypes = [i32, i64, vp, vp, vp, vp, vp]
+        L.ktruss_support_noalloc.restype = ctypes.c_int
         L.ktruss_strerror.argtypes = [ctypes.c_int]
         L.ktruss_strerror.restype = ctypes.c_char_p
         for f in (L.ktruss_load_csr, L.ktruss_run, L.ktruss_stats, L.ktruss_set_option,
@@ -240,6 +242,30 @@ def load(row_ptr, col, stream=None) -> Graph:
     rc = lib().ktruss_load_csr(ctypes.byref(h), n, m, rp_p, c_p, rp_kind, _stream_ptr(stream))
     _check(rc, "ktruss_load_csr")
     return Graph(h.value, n, m)
+
+
+NOALLOC_MAX_VERTICES = 1 << 19
+NOALLOC_MAX_EDGES = 1 << 19
+
+
+def support_noalloc(row_ptr, col, support_out=None, stream=None):
+    """ktruss_support_noalloc: support of every edge of a device-resident CSR,
+    computed by the library without allocating (its working memory is a fixed
+    32 MiB array inside the library).  For callers that may not allocate on
+    their path.  row_ptr/col: int32 cuda tensors; support_out: an int32 cuda
+    tensor of m entries (allocated here when None, which the caller can avoid
+    by passing one).  Returns (support_out, triangles)."""
+    torch = _torch()
+    n = row_ptr.shape[0] - 1
+    m = col.shape[0]
+    if support_out is None:
+        support_out = torch.empty(max(m, 1), dtype=torch.int32, device=row_ptr.device)[:m]
+    tri = ctypes.c_int64(0)
+    rc = lib().ktruss_support_noalloc(n, m, row_ptr.data_ptr(), col.data_ptr() if m else None,
+                                      support_out.data_ptr() if m else None,
+                                      ctypes.addressof(tri), _stream_ptr(stream))
+    _check(rc, "ktruss_support_noalloc")
+    return support_out, tri.value
 
 
 def ktruss(row_ptr, col, K: int, kernel: int = KERNEL_BALANCED):
