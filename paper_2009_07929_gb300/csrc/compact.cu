@@ -141,11 +141,6 @@ __global__ void finalize_kernel(const int32_t *__restrict__ eid, const int32_t *
     if (support_out) support_out[id] = S[e];
 }
 
-__global__ void iota_kernel(int32_t *__restrict__ eid, int32_t m) {
-    const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (e < m) eid[e] = int32_t(e);
-}
-
 }  // namespace
 
 cudaError_t launch_prune_count(const int32_t *S, int32_t m, int32_t thr, int32_t *tile_count,
@@ -183,12 +178,6 @@ cudaError_t launch_finalize(const Live &g, const int32_t *S, uint8_t *mask_out,
     if (g.m == 0) return cudaSuccess;
     finalize_kernel<<<(g.m + 255) / 256, 256, 0, s>>>(g.eid, S, g.m, mask_out, support_out);
     ++*launches;
-    return cudaGetLastError();
-}
-
-cudaError_t launch_iota(int32_t *eid, int32_t m, cudaStream_t s) {
-    if (m == 0) return cudaSuccess;
-    iota_kernel<<<(m + 255) / 256, 256, 0, s>>>(eid, m);
     return cudaGetLastError();
 }
 

@@ -97,7 +97,4 @@ cudaError_t launch_compact(const Live &in, const int32_t *S, int32_t thr, const 
 cudaError_t launch_finalize(const Live &g, const int32_t *S, uint8_t *mask_out,
                             int32_t *support_out, cudaStream_t s, int *launches);
 
-// Fills eid[e] = e.
-cudaError_t launch_iota(int32_t *eid, int32_t m, cudaStream_t s);
-
 }  // namespace kt

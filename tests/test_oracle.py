@@ -315,3 +315,52 @@ def test_planted_mistake_is_caught(name):
                 caught = True
                 break
         assert caught, f"mutant {name} passed every pin"
+
+
+# ------------------------------------------- closed forms of the checkers
+
+@pytest.mark.parametrize("n", [3, 4, 7, 15])
+def test_checkers_on_complete_graph(n):
+    g = gg.complete(n)
+    assert (oracle.truss_decomposition(g.row_ptr, g.col) == n).all()
+    assert oracle.triangles(g.row_ptr, g.col) == n * (n - 1) * (n - 2) // 6
+    assert (oracle.edge_support(g.row_ptr, g.col, np.arange(g.m)) == n - 2).all()
+
+
+def test_checkers_on_book_star_strip():
+    b = gg.book(6)
+    assert (oracle.truss_decomposition(b.row_ptr, b.col) == 3).all()
+    assert oracle.triangles(b.row_ptr, b.col) == 6
+    s = gg.star(9)
+    assert (oracle.truss_decomposition(s.row_ptr, s.col) == 2).all()
+    assert oracle.triangles(s.row_ptr, s.col) == 0
+    t = gg.triangle_strip(10)
+    assert oracle.triangles(t.row_ptr, t.col) == 8
+    assert (oracle.truss_decomposition(t.row_ptr, t.col) == 3).all()
+    # a kept-edge mask removes exactly the triangles that lose an edge
+    keep = np.ones(t.m, np.uint8)
+    keep[0] = 0  # edge (0,1) is in one triangle
+    assert oracle.triangles(t.row_ptr, t.col, keep) == 7
+
+
+def test_tail_start_reading():
+    """Reading of Alg. 3: its first update intersects the whole a12 with row
+    kappa, the other two only the tail a12(j+1:).  Both give the same matches
+    because row kappa holds only columns > kappa.  An oracle whose merge starts
+    at the edge itself (not after it) must therefore agree exactly."""
+    src = open(os.path.join(os.path.dirname(oracle.__file__), "oracle.c")).read()
+    old = "int64_t x = a + 1, xe"
+    assert old in src
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "variant.c")
+        so = os.path.join(d, "variant.so")
+        with open(c, "w") as f:
+            f.write(src.replace(old, "int64_t x = lstart[i], xe", 1))
+        subprocess.check_call(["gcc", "-O1", "-shared", "-fPIC", "-o", so, c])
+        lib = _load_mutant(so)
+        for s in range(40):
+            g = gg.gnp_small(10 + s % 25, 0.45, seed=700 + s)
+            for K in (2, 3, 4, 5):
+                a, b = run(g, K), _mutant_run(lib, g, K)
+                assert np.array_equal(a.mask, b.mask) and np.array_equal(a.support, b.support)
+                assert a.rounds == b.rounds
