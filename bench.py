@@ -17,7 +17,8 @@ support, prune, compaction, convergence test, final outputs) of that graph.
 Between timed steps L2 is flushed by writing a buffer larger than L2.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload rmat20|rmat20r|rmat23c|er2000] [--K 3] [--kernel balanced|edge]
+                  [--workload rmat20|rmat20r|rmat23c|er2000] [--K 3]
+                  [--kernel balanced|edge|coarse]
 """
 from __future__ import annotations
 
@@ -214,8 +215,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rmat20", choices=sorted(WORKLOAD_DESC))
     ap.add_argument("--K", type=int, default=3)
-    ap.add_argument("--kernel", default="balanced", choices=["balanced", "edge"])
+    ap.add_argument("--kernel", default="balanced", choices=["balanced", "edge", "coarse"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-kmax", action="store_true", help="skip the K_max sweep timing")
     ap.add_argument("--ref-scale", type=int, default=CPU_SAMPLE_SCALE,
                     help="R-MAT scale of the oracle sample timed by --impl reference")
     args = ap.parse_args()
@@ -245,7 +247,8 @@ def main():
     rp_d = torch.from_numpy(g.row_ptr).to(dev)
     col_d = torch.from_numpy(g.col).to(dev)
     h = kt.load(rp_d, col_d)
-    h.set_kernel(kt.KERNEL_BALANCED if args.kernel == "balanced" else kt.KERNEL_EDGE)
+    h.set_kernel({"balanced": kt.KERNEL_BALANCED, "edge": kt.KERNEL_EDGE,
+                  "coarse": kt.KERNEL_COARSE}[args.kernel])
     mask = torch.empty(m, dtype=torch.uint8, device=dev)
     sup = torch.empty(m, dtype=torch.int32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
@@ -313,6 +316,20 @@ def main():
     e2e_s = max_over_ranks(sum(e2e_times) / len(e2e_times), dev)
     e2e_value = world * m / e2e_s / 1e6
 
+    # ---- K_max sweep (truss decomposition) of the same graph, for context
+    kmax, dec_ms = None, None
+    if not args.no_kmax:
+        h.decompose()
+        torch.cuda.synchronize()
+        d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.fill_(7)
+        d0.record(stream)
+        _, kmax = h.decompose()
+        d1.record(stream)
+        torch.cuda.synchronize()
+        dec_ms = d0.elapsed_time(d1)
+        dec_steps = h.stats().rounds
+
     if rank != 0:
         if pg:
             pg.destroy_process_group()
@@ -353,6 +370,10 @@ def main():
         "clocks": clk.summary(),
         "wall_s_timed": round(wall, 3),
     }
+    if kmax is not None:
+        out["kmax_sweep"] = {"kmax": kmax, "ms": round(dec_ms, 3), "support_steps": dec_steps,
+                             "Medges_per_s": round(m / (dec_ms / 1e3) / 1e6, 2),
+                             "what": "ktruss_decompose: K = 3 .. K_max, each K from the previous truss"}
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline()
     print(json.dumps(out), flush=True)

@@ -54,6 +54,7 @@ extern "C" {
 /* Support kernels selectable with KTRUSS_OPT_SUPPORT_KERNEL. */
 #define KTRUSS_KERNEL_BALANCED 0 /* work-prefix balancer + staged warp intersection (default) */
 #define KTRUSS_KERNEL_EDGE 1     /* one thread per edge, two-pointer merge (Alg. 3 task as-is) */
+#define KTRUSS_KERNEL_COARSE 2   /* one thread per row (coarse-grained Alg. 2), for comparison */
 
 /* Option keys for ktruss_set_option. */
 #define KTRUSS_OPT_SUPPORT_KERNEL 1 /* KTRUSS_KERNEL_* */
@@ -119,7 +120,24 @@ int ktruss_run(ktruss_graph *g, int32_t K, uint8_t *mask_out, int32_t *support_o
                void *cuda_stream);
 
 /*
- * Copies the statistics of the last ktruss_run into *out.  The per-round
+ * Truss decomposition of the loaded graph: trussness_out[e] = the largest K
+ * such that edge e is in the K-truss (2 for an edge in no triangle), and
+ * *kmax_out = the largest K whose K-truss is not empty (0 for a graph with no
+ * edge).  Runs Alg. 1 for K = 3, 4, ... in turn, each K starting from the
+ * (K-1)-truss, which contains it (the K-trusses are nested, Sec. I); an edge
+ * removed while peeling for K gets trussness K-1.  Between two values of K the
+ * supports of the converged truss are reused instead of recomputed.
+ *   trussness_out int32[m], kind mem_kind (caller-owned); kmax_out host, may be NULL
+ * ktruss_stats afterwards reports the support steps executed (rounds) with
+ * their live edges and triangles; edges_out and triangles_out are 0.
+ * Returns KTRUSS_EINVAL for a NULL output with m > 0 or a bad mem_kind;
+ * KTRUSS_ENOMEM, KTRUSS_ECUDA, KTRUSS_ETIMEOUT, KTRUSS_EBUSY.
+ */
+int ktruss_decompose(ktruss_graph *g, int32_t *trussness_out, int32_t *kmax_out, int mem_kind,
+                     void *cuda_stream);
+
+/*
+ * Copies the statistics of the last ktruss_run or ktruss_decompose into *out.  The per-round
  * arrays point into the handle and stay valid until the next run or free.
  * Returns KTRUSS_EINVAL for NULL arguments or a handle never run.
  */

@@ -27,7 +27,7 @@ from . import _build
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBUSY = 0, -1, -2, -3, -4, -5
 HOST, DEVICE = 0, 1
-KERNEL_BALANCED, KERNEL_EDGE = 0, 1
+KERNEL_BALANCED, KERNEL_EDGE, KERNEL_COARSE = 0, 1, 2
 OPT_SUPPORT_KERNEL, OPT_TIMING = 1, 2
 
 _lib = None
@@ -82,6 +82,8 @@ def lib():
         vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
         L.ktruss_load_csr.argtypes = [ctypes.POINTER(vp), i32, i64, vp, vp, ctypes.c_int, vp]
         L.ktruss_run.argtypes = [vp, i32, vp, vp, ctypes.c_int, vp]
+        L.ktruss_decompose.argtypes = [vp, vp, vp, ctypes.c_int, vp]
+        L.ktruss_decompose.restype = ctypes.c_int
         L.ktruss_stats.argtypes = [vp, ctypes.POINTER(_Stats)]
         L.ktruss_set_option.argtypes = [vp, i32, i64]
         L.ktruss_graph_size.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i64)]
@@ -211,6 +213,19 @@ class Graph:
                               _stream_ptr(stream))
         _check(rc, "ktruss_run")
         return mask_out, support_out
+
+    def decompose(self, out=None, stream=None):
+        """Truss decomposition (ktruss_decompose) on the device: returns
+        (trussness int32[m] cuda tensor, K_max)."""
+        torch = _torch()
+        dev = torch.device("cuda", torch.cuda.current_device())
+        tr = out if out is not None else torch.empty(max(self.m, 1), dtype=torch.int32,
+                                                     device=dev)[: self.m]
+        kmax = ctypes.c_int32(0)
+        rc = lib().ktruss_decompose(self._h, tr.data_ptr() if self.m else None,
+                                    ctypes.addressof(kmax), DEVICE, _stream_ptr(stream))
+        _check(rc, "ktruss_decompose")
+        return tr, kmax.value
 
     def stats(self) -> Stats:
         st = _Stats()

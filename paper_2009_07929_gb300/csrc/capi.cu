@@ -228,7 +228,9 @@ int ktruss_set_option(ktruss_graph *g, int32_t key, int64_t value) {
     if (!g) return KTRUSS_EINVAL;
     switch (key) {
         case KTRUSS_OPT_SUPPORT_KERNEL:
-            if (value != KTRUSS_KERNEL_BALANCED && value != KTRUSS_KERNEL_EDGE) return KTRUSS_EINVAL;
+            if (value != KTRUSS_KERNEL_BALANCED && value != KTRUSS_KERNEL_EDGE &&
+                value != KTRUSS_KERNEL_COARSE)
+                return KTRUSS_EINVAL;
             g->support_kernel = int(value);
             return KTRUSS_OK;
         case KTRUSS_OPT_TIMING:
@@ -295,9 +297,12 @@ int ktruss_run(ktruss_graph *g, int32_t K, uint8_t *mask_out, int32_t *support_o
         KT_CK(cudaMemsetAsync(g->S, 0, size_t(cur.m) * 4, s));
         KT_CK(cudaMemsetAsync(g->cnt, 0, sizeof(kt::RoundCounters), s));
         if (timing) KT_CK(cudaEventRecord(g->events[base + 0], s));
-        if (g->support_kernel == KTRUSS_KERNEL_EDGE) {
+        if (g->support_kernel == KTRUSS_KERNEL_EDGE || g->support_kernel == KTRUSS_KERNEL_COARSE) {
             if (timing) KT_CK(cudaEventRecord(g->events[base + 1], s));
-            KT_CK(kt::launch_support_edge(cur, g->S, g->cnt, s));
+            if (g->support_kernel == KTRUSS_KERNEL_EDGE)
+                KT_CK(kt::launch_support_edge(cur, g->S, g->cnt, s));
+            else
+                KT_CK(kt::launch_support_coarse(cur, g->S, g->cnt, s));
             ++launches;
             ++support_launches;
         } else {
@@ -385,6 +390,113 @@ int ktruss_run(ktruss_graph *g, int32_t K, uint8_t *mask_out, int32_t *support_o
     g->st.ms_balance = ms_balance;
     g->st.ms_prune_compact = ms_prune;
     g->st.ms_finalize = ms_final;
+    g->st.support_launches = support_launches;
+    g->st.kernel_launches = launches;
+    g->has_stats = true;
+    return KTRUSS_OK;
+}
+
+int ktruss_decompose(ktruss_graph *g, int32_t *trussness_out, int32_t *kmax_out, int mem_kind,
+                     void *cuda_stream) {
+    if (!g || (g->m > 0 && !trussness_out)) return KTRUSS_EINVAL;
+    if (mem_kind != KTRUSS_HOST && mem_kind != KTRUSS_DEVICE) return KTRUSS_EINVAL;
+    BusyGuard guard(g);
+    if (!guard.ok) return KTRUSS_EBUSY;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const int32_t n = g->n;
+    const int32_t m = int32_t(g->m);
+    g->has_stats = false;
+    g->removed.clear();
+    g->live.clear();
+    g->tris.clear();
+    g->merge.clear();
+    g->ms_sup.clear();
+    int32_t *tr_d = trussness_out;
+    if (mem_kind == KTRUSS_HOST && m > 0) {
+        if (!g->d_mask) {
+            Allocator al;
+            KT_CK(al.alloc((void **)&g->d_mask, size_t(m)));
+            g->owned.push_back(g->d_mask);
+            KT_CK(al.alloc((void **)&g->d_sup, size_t(m) * 4));
+            g->owned.push_back(g->d_sup);
+        }
+        tr_d = g->d_sup;
+    }
+    const bool timing = g->timing != 0;
+    if (timing) {
+        KT_CK(ensure_events(g, 2));
+        KT_CK(cudaEventRecord(g->events[0], s));
+    }
+    int launches = 0, support_launches = 0, rounds = 0;
+    kt::Live cur{g->rp0, g->col0, nullptr, n, m};
+    int buf = 0;
+    int32_t K = 3;          // the whole graph is the 2-truss
+    bool have_s = false;    // S holds the supports of the current live graph
+    while (cur.m > 0) {
+        if (!have_s) {
+            ++rounds;
+            KT_CK(cudaMemsetAsync(g->S, 0, size_t(cur.m) * 4, s));
+            KT_CK(cudaMemsetAsync(g->cnt, 0, sizeof(kt::RoundCounters), s));
+            if (g->support_kernel == KTRUSS_KERNEL_EDGE) {
+                KT_CK(kt::launch_support_edge(cur, g->S, g->cnt, s));
+                ++launches;
+            } else if (g->support_kernel == KTRUSS_KERNEL_COARSE) {
+                KT_CK(kt::launch_support_coarse(cur, g->S, g->cnt, s));
+                ++launches;
+            } else {
+                int l = 0;
+                KT_CK(kt::launch_support_balanced(cur, g->S, g->cnt, &g->bs, s, &l, nullptr));
+                launches += l;
+            }
+            ++support_launches;
+        }
+        KT_CK(kt::launch_prune_count(g->S, cur.m, K - 2, g->tile_count, g->tile_off, g->cnt, s,
+                                     &launches));
+        KT_CK(cudaMemcpyAsync(g->cnt_host, g->cnt, sizeof(kt::RoundCounters),
+                              cudaMemcpyDeviceToHost, s));
+        KT_CK(cudaStreamSynchronize(s));
+        const kt::RoundCounters c = *g->cnt_host;
+        if (c.error) return (c.error & kt::kDevErrTimeout) ? KTRUSS_ETIMEOUT : KTRUSS_ECUDA;
+        const int32_t kept = c.kept;
+        if (!have_s) {
+            g->live.push_back(cur.m);
+            g->tris.push_back(int64_t(c.triangles));
+            g->merge.push_back(int64_t(c.merge_work));
+            g->removed.push_back(int64_t(cur.m) - kept);
+            g->ms_sup.push_back(0.f);
+        } else if (!g->removed.empty()) {
+            g->removed.back() += int64_t(cur.m) - kept;
+        }
+        if (kept == cur.m) {
+            // cur is the (non-empty) K-truss: the (K+1)-truss lies inside it,
+            // and its supports are already in S
+            ++K;
+            have_s = true;
+            continue;
+        }
+        const int nb = buf;
+        KT_CK(kt::launch_compact(cur, g->S, K - 2, g->tile_off, g->cnt, g->pos, g->rp[nb],
+                                 g->col[nb], g->eid[nb], nullptr, nullptr, s, &launches, tr_d,
+                                 K - 1));
+        cur = kt::Live{g->rp[nb], g->col[nb], g->eid[nb], n, kept};
+        buf ^= 1;
+        have_s = false;
+    }
+    if (timing) KT_CK(cudaEventRecord(g->events[1], s));
+    if (mem_kind == KTRUSS_HOST && m > 0)
+        KT_CK(cudaMemcpyAsync(trussness_out, tr_d, size_t(m) * 4, cudaMemcpyDeviceToHost, s));
+    KT_CK(cudaStreamSynchronize(s));
+    if (kmax_out) *kmax_out = m == 0 ? 0 : K - 1;
+    g->st = ktruss_stats_t{};
+    g->st.rounds = rounds;
+    g->st.edges_in = g->m;
+    g->st.per_round_len = rounds;
+    g->st.removed_per_round = g->removed.data();
+    g->st.live_per_round = g->live.data();
+    g->st.triangles_per_round = g->tris.data();
+    g->st.ms_support_per_round = g->ms_sup.data();
+    g->st.merge_work_per_round = g->merge.data();
+    g->st.ms_total = timing ? elapsed(g->events[0], g->events[1]) : 0.f;
     g->st.support_launches = support_launches;
     g->st.kernel_launches = launches;
     g->has_stats = true;

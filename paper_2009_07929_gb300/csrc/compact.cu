@@ -85,7 +85,8 @@ compact_kernel(const int32_t *__restrict__ col, const int32_t *__restrict__ eid,
                const int32_t *__restrict__ S, int32_t m, int32_t thr,
                const int32_t *__restrict__ tile_off, int32_t *__restrict__ pos,
                int32_t *__restrict__ col_out, int32_t *__restrict__ eid_out,
-               uint8_t *__restrict__ mask_out, int32_t *__restrict__ support_out) {
+               uint8_t *__restrict__ mask_out, int32_t *__restrict__ support_out,
+               int32_t *__restrict__ level_out, int32_t level) {
     __shared__ int32_t warp_tot[kWarpsPerTile];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t base = int64_t(blockIdx.x) * kCompactTile + int64_t(w) * kWarpSpan + lane;
@@ -114,8 +115,9 @@ compact_kernel(const int32_t *__restrict__ col, const int32_t *__restrict__ eid,
                 col_out[p] = __ldg(col + e);
                 eid_out[p] = id;
             } else {
-                mask_out[id] = 0;
+                if (mask_out) mask_out[id] = 0;
                 if (support_out) support_out[id] = 0;
+                if (level_out) level_out[id] = level;
             }
         }
         run += __popc(ballots[j]);
@@ -159,12 +161,13 @@ cudaError_t launch_prune_count(const int32_t *S, int32_t m, int32_t thr, int32_t
 cudaError_t launch_compact(const Live &in, const int32_t *S, int32_t thr, const int32_t *tile_off,
                            const RoundCounters *cnt, int32_t *pos, int32_t *rp_out,
                            int32_t *col_out, int32_t *eid_out, uint8_t *mask_out,
-                           int32_t *support_out, cudaStream_t s, int *launches) {
+                           int32_t *support_out, cudaStream_t s, int *launches,
+                           int32_t *level_out, int32_t level) {
     const int32_t tiles = compact_tiles(in.m);
     if (tiles > 0) {
         compact_kernel<<<tiles, kCompactThreads, 0, s>>>(in.col, in.eid, S, in.m, thr, tile_off,
                                                          pos, col_out, eid_out, mask_out,
-                                                         support_out);
+                                                         support_out, level_out, level);
         ++*launches;
     }
     const int64_t rows = int64_t(in.n) + 1;

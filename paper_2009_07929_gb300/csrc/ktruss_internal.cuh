@@ -44,6 +44,9 @@ cudaError_t launch_validate(const int32_t *rp, const int32_t *col, int32_t n, in
 // number of triangles found into cnt->triangles.
 cudaError_t launch_support_edge(const Live &g, int32_t *S, RoundCounters *cnt, cudaStream_t s);
 
+// Coarse-grained support step (Alg. 2): one thread per row.
+cudaError_t launch_support_coarse(const Live &g, int32_t *S, RoundCounters *cnt, cudaStream_t s);
+
 // Scratch owned by the handle for the balanced support kernel.
 // One device allocation carved into: the int64 work prefix [m+1], tile sums
 // and offsets of its scan, the chunk plan, the chunk boundary table, the
@@ -87,11 +90,13 @@ cudaError_t launch_prune_count(const int32_t *S, int32_t m, int32_t thr, int32_t
 // writes the exclusive kept-prefix of every slot into pos[m_in] (pos[m] =
 // total), writes removed edges' final outputs (mask 0, support 0 at their
 // input edge id) and builds rp_out[i] = pos[rp_in[i]] (cnt->kept for
-// rp_in[i] == m).
+// rp_in[i] == m).  mask_out / support_out may be null; when level_out is not
+// null, removed edges also get level_out[id] = level (trussness).
 cudaError_t launch_compact(const Live &in, const int32_t *S, int32_t thr, const int32_t *tile_off,
                            const RoundCounters *cnt, int32_t *pos, int32_t *rp_out,
                            int32_t *col_out, int32_t *eid_out, uint8_t *mask_out,
-                           int32_t *support_out, cudaStream_t s, int *launches);
+                           int32_t *support_out, cudaStream_t s, int *launches,
+                           int32_t *level_out = nullptr, int32_t level = 0);
 
 // Final outputs of the surviving edges: mask 1 and support S at their input id.
 cudaError_t launch_finalize(const Live &g, const int32_t *S, uint8_t *mask_out,

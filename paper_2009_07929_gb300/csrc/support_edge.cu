@@ -3,7 +3,8 @@
 // a two-pointer merge of row i after e with row kappa, and every common column
 // credits the three edges of that triangle (eager rule, Sec. II-B).  This is
 // the simple, unbalanced baseline; the balanced kernel lives in
-// support_balanced.cu.
+// support_balanced.cu.  The coarse-grained kernel (Alg. 2, one thread per row)
+// is here too, to measure the paper's fine/coarse comparison on this GPU.
 #include "ktruss_internal.cuh"
 
 namespace kt {
@@ -52,7 +53,55 @@ support_edge_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ 
     if ((threadIdx.x & 31) == 0 && tot) atomicAdd(tri, (unsigned long long)tot);
 }
 
+// Coarse-grained support step (Alg. 2): one thread per row i applies both
+// update rules of the row partition, i.e. for every nonzero kappa of a12 it
+// intersects the rest of a12 with row kappa of A22 and credits each triangle
+// to (i,kappa), (i,w) and (kappa,w).  All edge tasks of a row run one after
+// another in the same thread, which is the load imbalance Sec. III-A describes.
+__global__ void __launch_bounds__(256)
+support_coarse_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, int32_t n,
+                      int32_t *__restrict__ S, unsigned long long *__restrict__ tri) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    long long found = 0;
+    if (i < n) {
+        const int32_t rb = __ldg(rp + i), re = __ldg(rp + i + 1);
+        for (int32_t e = rb; e < re; ++e) {
+            const int32_t kappa = __ldg(col + e);
+            int32_t x = e + 1, y = __ldg(rp + kappa);
+            const int32_t ye = __ldg(rp + kappa + 1);
+            int32_t own = 0;
+            while (x < re && y < ye) {
+                const int32_t a = __ldg(col + x), b = __ldg(col + y);
+                if (a == b) {
+                    atomicAdd(S + x, 1);
+                    atomicAdd(S + y, 1);
+                    ++own;
+                    ++x;
+                    ++y;
+                } else if (a < b) {
+                    ++x;
+                } else {
+                    ++y;
+                }
+            }
+            if (own) atomicAdd(S + e, own);
+            found += own;
+        }
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) found += __shfl_down_sync(0xffffffffu, found, d);
+    if ((threadIdx.x & 31) == 0 && found) atomicAdd(tri, (unsigned long long)found);
+}
+
 }  // namespace
+
+cudaError_t launch_support_coarse(const Live &g, int32_t *S, RoundCounters *cnt, cudaStream_t s) {
+    if (g.m == 0) return cudaSuccess;
+    const int threads = 256;
+    const int blocks = (g.n + threads - 1) / threads;
+    support_coarse_kernel<<<blocks, threads, 0, s>>>(g.rp, g.col, g.n, S, &cnt->triangles);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_support_edge(const Live &g, int32_t *S, RoundCounters *cnt, cudaStream_t s) {
     if (g.m == 0) return cudaSuccess;

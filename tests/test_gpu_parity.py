@@ -19,7 +19,7 @@ import oracle
 pytestmark = pytest.mark.gpu
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
-KERNELS = [0, 1]  # balanced, thread-per-edge
+KERNELS = [0, 1, 2]  # balanced, thread-per-edge, coarse (thread-per-row)
 
 
 @pytest.fixture(scope="module")
@@ -201,6 +201,31 @@ def test_support_optional(kt):
     h.close()
 
 
+# ------------------------------------------------ truss decomposition
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_decomposition_matches_oracle(kt, kernel):
+    import torch
+    graphs = [gg.complete(9), gg.book(20), gg.star(10), gg.triangle_strip(30), gg.empty(5),
+              gg.er(2000, 16000, 1), gg.rmat(12, 16, 0),
+              gg.rmat(14, 8, seed=3, n_cliques=8, clique_lo=20, clique_hi=60)]
+    for g in graphs:
+        h = kt.load(torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col).cuda())
+        h.set_kernel(kernel)
+        tr, kmax = h.decompose()
+        torch.cuda.synchronize()
+        got = tr.cpu().numpy()
+        want = oracle.truss_decomposition(g.row_ptr, g.col)
+        assert np.array_equal(got, want)
+        assert kmax == (int(want.max()) if g.m else 0)
+        # the K-truss of ktruss_run is {e : trussness >= K}
+        for K in {3, max(3, kmax), max(3, kmax + 1)}:
+            m_t, _ = h.run(K)
+            torch.cuda.synchronize()
+            assert np.array_equal(m_t.cpu().numpy(), (got >= K).astype(np.uint8))
+        h.close()
+
+
 # ---------------------------------------------------------------- errors
 
 def test_malformed_csr_rejected_on_device(kt):
@@ -300,6 +325,9 @@ def test_rmat23_cliques_k3_sampled_and_kmax_sweep(kt):
     import torch
     g = gg.cached_workload("rmat23c", 0)
     h = kt.load(torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col).cuda())
+    tr_t, kmax_dec = h.decompose()
+    torch.cuda.synchronize()
+    tr = tr_t.cpu().numpy()
     rng = np.random.default_rng(0)
     m_t, s_t = h.run(3)
     torch.cuda.synchronize()
@@ -324,6 +352,7 @@ def test_rmat23_cliques_k3_sampled_and_kmax_sweep(kt):
         if not mask.any():
             break
         kmax = K
+        assert np.array_equal(mask, (tr >= K).astype(np.uint8))
         assert (sup[mask == 1] >= K - 2).all() and (sup[mask == 0] == 0).all()
         assert not np.any((mask == 1) & (prev == 0))
         assert int(sup.astype(np.int64).sum()) == 3 * st.triangles_out
@@ -337,4 +366,6 @@ def test_rmat23_cliques_k3_sampled_and_kmax_sweep(kt):
             break
     # a 200-clique was planted, so the 200-truss is non-empty
     assert kmax >= 200
+    assert kmax_dec >= kmax and not (tr > kmax_dec).any()
+    assert np.array_equal(mask3, (tr >= 3).astype(np.uint8))
     h.close()
