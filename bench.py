@@ -18,7 +18,7 @@ Between timed steps L2 is flushed by writing a buffer larger than L2.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload rmat20|rmat20r|rmat23c|er2000] [--K 3]
-                  [--kernel balanced|edge|coarse]
+                  [--kernel auto|balanced|edge|coarse]
 """
 from __future__ import annotations
 
@@ -174,6 +174,60 @@ def cpu_baseline(seconds_cap=30.0, scale=CPU_SAMPLE_SCALE):
                       f"{el:.1f} s on {os.cpu_count()} host cores (1 used)"}
 
 
+def measure_batched(kt, gg, count, m_hi, seed=0):
+    """Batched graphs/s against the plain path on the batching workload
+    (graphgen.batch_config: sizes log-uniform in [1e3, m_hi] edges, half G(n,m)
+    with degree 8..64, half R-MAT scale 10..17, K uniform in 3..12).  Plain:
+    every graph preloaded into its own handle, then one ktruss_run per graph.
+    Batched: the block-diagonal batch preloaded into one handle, then one
+    ktruss_run_batch.  Both timed with CUDA events, graphs resident in HBM."""
+    import torch
+    batch = gg.batch_config(count, seed=seed, m_lo=1e3, m_hi=m_hi)
+    graphs = [b[0] for b in batch]
+    Ks = [b[1] for b in batch]
+    edges = sum(g.m for g in graphs)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    # plain
+    handles = [kt.load(torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col).to(dev))
+               for g in graphs]
+    outs = [(torch.empty(max(g.m, 1), dtype=torch.uint8, device=dev)[:g.m],
+             torch.empty(max(g.m, 1), dtype=torch.int32, device=dev)[:g.m]) for g in graphs]
+    for h, K, o in zip(handles, Ks, outs):
+        h.run(K, out=o)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for h, K, o in zip(handles, Ks, outs):
+        h.run(K, out=o)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = e0.elapsed_time(e1)
+    for h in handles:
+        h.close()
+    # batched
+    vo, rp, col, eo = kt.concat_graphs(graphs)
+    hb = kt.load_batch(vertex_offsets=vo, row_ptr=torch.from_numpy(rp).to(dev),
+                       col=torch.from_numpy(col).to(dev))
+    mb = torch.empty(max(int(eo[-1]), 1), dtype=torch.uint8, device=dev)[:int(eo[-1])]
+    sb = torch.empty(max(int(eo[-1]), 1), dtype=torch.int32, device=dev)[:int(eo[-1])]
+    hb.run_batch(Ks, out=(mb, sb))
+    torch.cuda.synchronize()
+    e0.record(stream)
+    _, _, rounds = hb.run_batch(Ks, out=(mb, sb))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    batch_ms = e0.elapsed_time(e1)
+    brounds = hb.stats().rounds
+    hb.close()
+    return {"graphs": count, "edges": int(edges), "m_range": [1000, int(m_hi)],
+            "graphs_per_s": round(count / (batch_ms / 1e3), 1),
+            "plain_graphs_per_s": round(count / (plain_ms / 1e3), 1),
+            "speedup": round(plain_ms / batch_ms, 2), "batch_ms": round(batch_ms, 3),
+            "plain_ms": round(plain_ms, 3), "batch_rounds": int(brounds),
+            "max_graph_rounds": int(max(rounds)) if len(rounds) else 0}
+
+
 def run_reference(args, world, rank):
     """Reference arm: the CPU oracle as it stands, on a bounded sample."""
     if rank != 0:
@@ -215,9 +269,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rmat20", choices=sorted(WORKLOAD_DESC))
     ap.add_argument("--K", type=int, default=3)
-    ap.add_argument("--kernel", default="balanced", choices=["balanced", "edge", "coarse"])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "balanced", "edge", "coarse"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-kmax", action="store_true", help="skip the K_max sweep timing")
+    ap.add_argument("--batch-graphs", type=int, default=4096,
+                    help="graphs of the batched-vs-plain measurement (0 = skip)")
+    ap.add_argument("--batch-mmax", type=float, default=1e5,
+                    help="largest graph size (edges) of that batch; the full batching "
+                         "workload uses 2e6")
     ap.add_argument("--ref-scale", type=int, default=CPU_SAMPLE_SCALE,
                     help="R-MAT scale of the oracle sample timed by --impl reference")
     args = ap.parse_args()
@@ -248,7 +307,7 @@ def main():
     col_d = torch.from_numpy(g.col).to(dev)
     h = kt.load(rp_d, col_d)
     h.set_kernel({"balanced": kt.KERNEL_BALANCED, "edge": kt.KERNEL_EDGE,
-                  "coarse": kt.KERNEL_COARSE}[args.kernel])
+                  "coarse": kt.KERNEL_COARSE, "auto": kt.KERNEL_AUTO}[args.kernel])
     mask = torch.empty(m, dtype=torch.uint8, device=dev)
     sup = torch.empty(m, dtype=torch.int32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
@@ -374,6 +433,8 @@ def main():
         out["kmax_sweep"] = {"kmax": kmax, "ms": round(dec_ms, 3), "support_steps": dec_steps,
                              "Medges_per_s": round(m / (dec_ms / 1e3) / 1e6, 2),
                              "what": "ktruss_decompose: K = 3 .. K_max, each K from the previous truss"}
+    if args.batch_graphs > 0:
+        out["batched"] = measure_batched(kt, gg, args.batch_graphs, args.batch_mmax)
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline()
     print(json.dumps(out), flush=True)

@@ -248,3 +248,38 @@ def cached_workload(name: str, seed: int = 0, cache_dir: str | None = None) -> C
         np.save(base + "_rp.npy", g.row_ptr)
         np.save(base + "_col.npy", g.col)
         return g
+
+
+# ------------------------------------------------------------- batches
+
+def _unit(key: int, i: int) -> float:
+    """Uniform double in [0, 1) from draw i of stream key (top 53 bits)."""
+    return (rand_u64(key, i) >> 11) * (1.0 / 9007199254740992.0)
+
+
+def batch_config(count: int, seed: int = 0, m_lo: float = 1e3, m_hi: float = 2e6,
+                 k_lo: int = 3, k_hi: int = 12):
+    """The batching workload: `count` graphs with target sizes log-uniform in
+    [m_lo, m_hi] edges.  Even-numbered graphs are G(n, m) with an average
+    degree d uniform in [8, 64] and n = max(ceil(2m/d), ceil(2 sqrt(m)) + 1)
+    (so that the density stays at most 1/2); odd-numbered graphs are R-MAT
+    with scale clamp(ceil(log2(m/16)), 10, 17) and edge factor 16 (their size
+    is what that scale gives).  Each graph has a K drawn uniformly from
+    [k_lo, k_hi].  Returns a list of (CSR, K)."""
+    import math
+    key = stream_key(5, seed, count)
+    out = []
+    for g in range(count):
+        u = _unit(key, 4 * g)
+        mt = int(round(math.exp(math.log(m_lo) + u * (math.log(m_hi) - math.log(m_lo)))))
+        K = k_lo + int(_unit(key, 4 * g + 1) * (k_hi - k_lo + 1))
+        sub_seed = rand_u64(key, 4 * g + 2) & 0x7FFFFFFF
+        if g % 2 == 0:
+            d = 8.0 + _unit(key, 4 * g + 3) * 56.0
+            n = max(int(math.ceil(2 * mt / d)), int(math.ceil(2 * math.sqrt(mt))) + 1)
+            csr = er(n, mt, sub_seed)
+        else:
+            scale = min(17, max(10, int(math.ceil(math.log2(max(mt, 1) / 16.0)))))
+            csr = rmat(scale, 16, sub_seed)
+        out.append((csr, K))
+    return out

@@ -52,9 +52,10 @@ extern "C" {
 #define KTRUSS_DEVICE 1
 
 /* Support kernels selectable with KTRUSS_OPT_SUPPORT_KERNEL. */
-#define KTRUSS_KERNEL_BALANCED 0 /* work-prefix balancer + staged warp intersection (default) */
+#define KTRUSS_KERNEL_BALANCED 0 /* work-prefix balancer + staged warp intersection */
 #define KTRUSS_KERNEL_EDGE 1     /* one thread per edge, two-pointer merge (Alg. 3 task as-is) */
 #define KTRUSS_KERNEL_COARSE 2   /* one thread per row (coarse-grained Alg. 2), for comparison */
+#define KTRUSS_KERNEL_AUTO 3     /* default: per round, EDGE below 131072 live edges, else BALANCED */
 
 /* Option keys for ktruss_set_option. */
 #define KTRUSS_OPT_SUPPORT_KERNEL 1 /* KTRUSS_KERNEL_* */
@@ -118,6 +119,45 @@ int ktruss_load_csr(ktruss_graph **out, int32_t n, int64_t m, const int32_t *row
  */
 int ktruss_run(ktruss_graph *g, int32_t K, uint8_t *mask_out, int32_t *support_out, int mem_kind,
                void *cuda_stream);
+
+/*
+ * Loads a batch of graphs to be peeled together (batched K-truss; the paper
+ * peels one graph at a time).  The batch is one block-diagonal strictly
+ * upper-triangular CSR over n vertices and m edges, in the format of
+ * ktruss_load_csr with global vertex ids: graph k owns the vertices
+ * [vertex_offsets[k], vertex_offsets[k+1]) and every edge must join two
+ * vertices of the same graph.
+ *   num_graphs       G >= 1
+ *   vertex_offsets   int32[G+1] in HOST memory, vertex_offsets[0] = 0,
+ *                    non-decreasing, vertex_offsets[G] = n (empty graphs allowed)
+ *   n, m, row_ptr, col, mem_kind, cuda_stream: as for ktruss_load_csr
+ * The handle also accepts ktruss_run (one K for all graphs), ktruss_decompose
+ * and ktruss_stats.  Returns KTRUSS_EINVAL for bad offsets, a malformed CSR or
+ * an edge joining two graphs; KTRUSS_ENOMEM, KTRUSS_ECUDA.
+ */
+int ktruss_load_batch(ktruss_graph **out, int32_t num_graphs, const int32_t *vertex_offsets,
+                      int32_t n, int64_t m, const int32_t *row_ptr, const int32_t *col,
+                      int mem_kind, void *cuda_stream);
+
+/* Number of graphs of a batch handle (0 for a handle from ktruss_load_csr). */
+int ktruss_batch_size(const ktruss_graph *g, int32_t *num_graphs);
+
+/*
+ * K-truss of every graph of a batch, graph k with its own K[k] (host int32[G],
+ * each >= 2).  All graphs are peeled in the same bulk rounds: each round runs
+ * one support step over every unfinished graph, prunes each graph with its own
+ * threshold K[k] - 2, and lets the graphs whose round removed nothing leave the
+ * live set with their final outputs.  Every graph gets exactly the outputs and
+ * the number of rounds of its own ktruss_run.
+ *   mask_out, support_out  as for ktruss_run, indexed by batch edge slot
+ *   rounds_out             host int32[G] (may be NULL): support steps of each
+ *                          graph, as ktruss_stats reports for a single run
+ * ktruss_stats reports the batch's rounds.  Returns KTRUSS_EINVAL for a
+ * handle that is not a batch, a NULL K, a K[k] < 2 or a bad mem_kind;
+ * KTRUSS_ENOMEM, KTRUSS_ECUDA, KTRUSS_ETIMEOUT, KTRUSS_EBUSY.
+ */
+int ktruss_run_batch(ktruss_graph *g, const int32_t *K, uint8_t *mask_out, int32_t *support_out,
+                     int32_t *rounds_out, int mem_kind, void *cuda_stream);
 
 /*
  * Truss decomposition of the loaded graph: trussness_out[e] = the largest K

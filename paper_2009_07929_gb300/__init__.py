@@ -27,7 +27,7 @@ from . import _build
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBUSY = 0, -1, -2, -3, -4, -5
 HOST, DEVICE = 0, 1
-KERNEL_BALANCED, KERNEL_EDGE, KERNEL_COARSE = 0, 1, 2
+KERNEL_BALANCED, KERNEL_EDGE, KERNEL_COARSE, KERNEL_AUTO = 0, 1, 2, 3
 OPT_SUPPORT_KERNEL, OPT_TIMING = 1, 2
 
 _lib = None
@@ -83,6 +83,13 @@ def lib():
         L.ktruss_load_csr.argtypes = [ctypes.POINTER(vp), i32, i64, vp, vp, ctypes.c_int, vp]
         L.ktruss_run.argtypes = [vp, i32, vp, vp, ctypes.c_int, vp]
         L.ktruss_decompose.argtypes = [vp, vp, vp, ctypes.c_int, vp]
+        L.ktruss_load_batch.argtypes = [ctypes.POINTER(vp), i32, vp, i32, i64, vp, vp,
+                                        ctypes.c_int, vp]
+        L.ktruss_load_batch.restype = ctypes.c_int
+        L.ktruss_run_batch.argtypes = [vp, vp, vp, vp, vp, ctypes.c_int, vp]
+        L.ktruss_run_batch.restype = ctypes.c_int
+        L.ktruss_batch_size.argtypes = [vp, ctypes.POINTER(i32)]
+        L.ktruss_batch_size.restype = ctypes.c_int
         L.ktruss_decompose.restype = ctypes.c_int
         L.ktruss_stats.argtypes = [vp, ctypes.POINTER(_Stats)]
         L.ktruss_set_option.argtypes = [vp, i32, i64]
@@ -227,6 +234,28 @@ class Graph:
         _check(rc, "ktruss_decompose")
         return tr, kmax.value
 
+    def run_batch(self, K, support: bool = True, out=None, stream=None):
+        """Batched K-truss (ktruss_run_batch), graph k with K[k]; device
+        outputs on the current torch stream.  Returns (mask, support, rounds)
+        with rounds a numpy int32[G]."""
+        torch = _torch()
+        G = ctypes.c_int32(0)
+        _check(lib().ktruss_batch_size(self._h, ctypes.byref(G)), "ktruss_batch_size")
+        Ks = np.ascontiguousarray(np.broadcast_to(np.asarray(K, dtype=np.int32), (G.value,)))
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if out is not None:
+            mask, sup = out
+        else:
+            mask = torch.empty(max(self.m, 1), dtype=torch.uint8, device=dev)[: self.m]
+            sup = (torch.empty(max(self.m, 1), dtype=torch.int32, device=dev)[: self.m]
+                   if support else None)
+        rounds = np.zeros(G.value, dtype=np.int32)
+        rc = lib().ktruss_run_batch(self._h, Ks.ctypes.data, mask.data_ptr() if self.m else None,
+                                    sup.data_ptr() if (sup is not None and self.m) else None,
+                                    rounds.ctypes.data, DEVICE, _stream_ptr(stream))
+        _check(rc, "ktruss_run_batch")
+        return mask, sup, rounds
+
     def stats(self) -> Stats:
         st = _Stats()
         _check(lib().ktruss_stats(self._h, ctypes.byref(st)), "ktruss_stats")
@@ -259,6 +288,44 @@ def load(row_ptr, col, stream=None) -> Graph:
     return Graph(h.value, n, m)
 
 
+def concat_graphs(graphs):
+    """Block-diagonal concatenation of CSR graphs (objects with n, row_ptr,
+    col): returns (vertex_offsets int32[G+1], row_ptr int32[n+1], col int32[m],
+    edge_offsets int64[G+1]) with global vertex ids."""
+    ns = [int(g.n) for g in graphs]
+    ms = [int(np.asarray(g.col).shape[0]) for g in graphs]
+    vo = np.zeros(len(graphs) + 1, dtype=np.int64)
+    vo[1:] = np.cumsum(ns)
+    eo = np.zeros(len(graphs) + 1, dtype=np.int64)
+    eo[1:] = np.cumsum(ms)
+    if vo[-1] >= 2 ** 31 or eo[-1] >= 2 ** 31:
+        raise ValueError("batch too large for int32 CSR indices")
+    rp = np.zeros(int(vo[-1]) + 1, dtype=np.int32)
+    col = np.zeros(int(eo[-1]), dtype=np.int32)
+    for k, g in enumerate(graphs):
+        r = np.asarray(g.row_ptr, dtype=np.int64)
+        rp[vo[k] + 1: vo[k + 1] + 1] = (r[1:] + eo[k]).astype(np.int32)
+        col[eo[k]: eo[k + 1]] = (np.asarray(g.col, dtype=np.int64) + vo[k]).astype(np.int32)
+    return vo.astype(np.int32), rp, col, eo
+
+
+def load_batch(graphs=None, vertex_offsets=None, row_ptr=None, col=None, stream=None) -> Graph:
+    """ktruss_load_batch: either a list of CSR graphs (concatenated here), or a
+    prepared block-diagonal CSR with its vertex offsets (host int32[G+1])."""
+    if graphs is not None:
+        vertex_offsets, row_ptr, col, _ = concat_graphs(graphs)
+    vo = np.ascontiguousarray(vertex_offsets, dtype=np.int32)
+    rp_p, rp_kind, rp_keep, rp_len = _as_i32(row_ptr)
+    c_p, c_kind, c_keep, m = _as_i32(col)
+    if m > 0 and rp_kind != c_kind:
+        raise ValueError("row_ptr and col must both be host or both be device arrays")
+    h = ctypes.c_void_p(0)
+    rc = lib().ktruss_load_batch(ctypes.byref(h), vo.shape[0] - 1, vo.ctypes.data, rp_len - 1, m,
+                                 rp_p, c_p, rp_kind, _stream_ptr(stream))
+    _check(rc, "ktruss_load_batch")
+    return Graph(h.value, rp_len - 1, m)
+
+
 NOALLOC_MAX_VERTICES = 1 << 19
 NOALLOC_MAX_EDGES = 1 << 19
 
@@ -283,7 +350,7 @@ def support_noalloc(row_ptr, col, support_out=None, stream=None):
     return support_out, tri.value
 
 
-def ktruss(row_ptr, col, K: int, kernel: int = KERNEL_BALANCED):
+def ktruss(row_ptr, col, K: int, kernel: int = KERNEL_AUTO):
     """One-shot helper: load, run on the device, return (mask, support, stats)."""
     g = load(row_ptr, col)
     g.set_kernel(kernel)

@@ -74,10 +74,15 @@ struct ktruss_graph {
     uint8_t *d_mask = nullptr;              // device outputs for host-kind runs
     int32_t *d_sup = nullptr;
     kt::BalancedScratch bs;
+    // batches (ktruss_load_batch): G graphs, vertex offsets, graph of each vertex
+    int32_t G = 0;
+    int32_t *vo = nullptr, *gid = nullptr, *thr = nullptr, *live_g = nullptr,
+            *removed_g = nullptr, *rounds_g = nullptr;
+    uint8_t *keep = nullptr, *done = nullptr;
     std::vector<void *> owned;
     std::atomic<int> busy{0};
     // options
-    int support_kernel = KTRUSS_KERNEL_BALANCED;
+    int support_kernel = KTRUSS_KERNEL_AUTO;
     int timing = 1;
     // events: [0] run start, [1] run end, then 5 per round
     std::vector<cudaEvent_t> events;
@@ -121,6 +126,34 @@ cudaError_t ensure_events(ktruss_graph *g, size_t count) {
     return cudaSuccess;
 }
 
+// Live graphs below this many edges use the one-thread-per-edge kernel under
+// KTRUSS_KERNEL_AUTO: the balanced step's fixed cost (a dozen small kernels
+// before the support kernel) dominates there.
+constexpr int32_t kAutoSmallEdges = 1 << 17;
+
+// One support step (Alg. 1 Step 1) on the live graph with the handle's kernel
+// choice.  When ev is given (the balanced path), ev[1] is recorded between the
+// balance kernels and the support kernel; otherwise ev[1] is recorded before
+// the support kernel.
+cudaError_t support_step(ktruss_graph *g, const kt::Live &cur, cudaStream_t s, int *launches,
+                         cudaEvent_t *ev) {
+    int k = g->support_kernel;
+    if (k == KTRUSS_KERNEL_AUTO) k = cur.m < kAutoSmallEdges ? KTRUSS_KERNEL_EDGE : KTRUSS_KERNEL_BALANCED;
+    if (k == KTRUSS_KERNEL_BALANCED) {
+        int l = 0;
+        cudaError_t e = kt::launch_support_balanced(cur, g->S, g->cnt, &g->bs, s, &l, ev);
+        *launches += l;
+        return e;
+    }
+    if (ev) {
+        cudaError_t e = cudaEventRecord(ev[1], s);
+        if (e != cudaSuccess) return e;
+    }
+    ++*launches;
+    return k == KTRUSS_KERNEL_EDGE ? kt::launch_support_edge(cur, g->S, g->cnt, s)
+                                   : kt::launch_support_coarse(cur, g->S, g->cnt, s);
+}
+
 float elapsed(cudaEvent_t a, cudaEvent_t b) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
@@ -150,8 +183,9 @@ int ktruss_last_cuda_error(void) { return g_last_cuda_error; }
 
 int ktruss_version(void) { return 100; }
 
-int ktruss_load_csr(ktruss_graph **out, int32_t n, int64_t m, const int32_t *row_ptr,
-                    const int32_t *col, int mem_kind, void *cuda_stream) {
+static int load_impl(ktruss_graph **out, int32_t n, int64_t m, const int32_t *row_ptr,
+                     const int32_t *col, int mem_kind, void *cuda_stream, int32_t G,
+                     const int32_t *vertex_offsets) {
     if (!out) return KTRUSS_EINVAL;
     *out = nullptr;
     if (n < 0 || m < 0 || m >= (int64_t(1) << 31) || !row_ptr || (m > 0 && !col))
@@ -182,6 +216,14 @@ int ktruss_load_csr(ktruss_graph **out, int32_t n, int64_t m, const int32_t *row
               A((void **)&g->pos, eb) && A((void **)&g->tile_count, (tiles + 1) * 4) &&
               A((void **)&g->tile_off, (tiles + 1) * 4) &&
               A((void **)&g->cnt, sizeof(kt::RoundCounters));
+    if (ok && G > 0) {
+        const size_t gb = (size_t(G) + 1) * 4;
+        ok = A((void **)&g->vo, gb) && A((void **)&g->gid, (size_t(n) + 1) * 4) &&
+             A((void **)&g->thr, gb) && A((void **)&g->live_g, gb) &&
+             A((void **)&g->removed_g, gb) && A((void **)&g->rounds_g, gb) &&
+             A((void **)&g->keep, size_t(m) + 1) && A((void **)&g->done, size_t(G) + 1);
+        g->G = G;
+    }
     g->owned = al.owned;
     if (!ok) {
         release(g);
@@ -200,6 +242,12 @@ int ktruss_load_csr(ktruss_graph **out, int32_t n, int64_t m, const int32_t *row
     if (e == cudaSuccess && m > 0) e = cudaMemcpyAsync(g->col0, col, eb, kind, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(g->cnt, 0, sizeof(kt::RoundCounters), s);
     if (e == cudaSuccess) e = kt::launch_validate(g->rp0, g->col0, n, m, &g->cnt->error, s);
+    if (e == cudaSuccess && G > 0) {
+        e = cudaMemcpyAsync(g->vo, vertex_offsets, (size_t(G) + 1) * 4, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = kt::launch_graph_of_vertex(g->vo, G, n, g->gid, s);
+        if (e == cudaSuccess) e = kt::launch_batch_validate(g->rp0, g->col0, n, g->gid,
+                                                            &g->cnt->error, s);
+    }
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(g->cnt_host, g->cnt, sizeof(kt::RoundCounters),
                             cudaMemcpyDeviceToHost, s);
@@ -217,6 +265,128 @@ int ktruss_load_csr(ktruss_graph **out, int32_t n, int64_t m, const int32_t *row
     return KTRUSS_OK;
 }
 
+int ktruss_load_csr(ktruss_graph **out, int32_t n, int64_t m, const int32_t *row_ptr,
+                    const int32_t *col, int mem_kind, void *cuda_stream) {
+    return load_impl(out, n, m, row_ptr, col, mem_kind, cuda_stream, 0, nullptr);
+}
+
+int ktruss_load_batch(ktruss_graph **out, int32_t num_graphs, const int32_t *vertex_offsets,
+                      int32_t n, int64_t m, const int32_t *row_ptr, const int32_t *col,
+                      int mem_kind, void *cuda_stream) {
+    if (!out) return KTRUSS_EINVAL;
+    *out = nullptr;
+    if (num_graphs < 1 || !vertex_offsets) return KTRUSS_EINVAL;
+    if (vertex_offsets[0] != 0 || vertex_offsets[num_graphs] != n) return KTRUSS_EINVAL;
+    for (int32_t k = 0; k < num_graphs; ++k)
+        if (vertex_offsets[k + 1] < vertex_offsets[k]) return KTRUSS_EINVAL;
+    return load_impl(out, n, m, row_ptr, col, mem_kind, cuda_stream, num_graphs, vertex_offsets);
+}
+
+int ktruss_batch_size(const ktruss_graph *g, int32_t *num_graphs) {
+    if (!g || !num_graphs) return KTRUSS_EINVAL;
+    *num_graphs = g->G;
+    return KTRUSS_OK;
+}
+
+int ktruss_run_batch(ktruss_graph *g, const int32_t *K, uint8_t *mask_out, int32_t *support_out,
+                     int32_t *rounds_out, int mem_kind, void *cuda_stream) {
+    if (!g || g->G < 1 || !K || (g->m > 0 && !mask_out)) return KTRUSS_EINVAL;
+    if (mem_kind != KTRUSS_HOST && mem_kind != KTRUSS_DEVICE) return KTRUSS_EINVAL;
+    const int32_t G = g->G;
+    for (int32_t k = 0; k < G; ++k)
+        if (K[k] < 2) return KTRUSS_EINVAL;
+    BusyGuard guard(g);
+    if (!guard.ok) return KTRUSS_EBUSY;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const int32_t n = g->n;
+    const int32_t m = int32_t(g->m);
+    g->has_stats = false;
+    g->removed.clear();
+    g->live.clear();
+    g->tris.clear();
+    g->merge.clear();
+    g->ms_sup.clear();
+    uint8_t *mask_d = mask_out;
+    int32_t *sup_d = support_out;
+    if (mem_kind == KTRUSS_HOST && m > 0) {
+        if (!g->d_mask) {
+            Allocator al;
+            KT_CK(al.alloc((void **)&g->d_mask, size_t(m)));
+            g->owned.push_back(g->d_mask);
+            KT_CK(al.alloc((void **)&g->d_sup, size_t(m) * 4));
+            g->owned.push_back(g->d_sup);
+        }
+        mask_d = g->d_mask;
+        sup_d = support_out ? g->d_sup : nullptr;
+    }
+    // per-graph thresholds K_g - 2 (the staging vector lives until the final
+    // synchronisation below)
+    std::vector<int32_t> thr(G);
+    for (int32_t k = 0; k < G; ++k) thr[k] = K[k] - 2;
+    KT_CK(cudaMemcpyAsync(g->thr, thr.data(), size_t(G) * 4, cudaMemcpyHostToDevice, s));
+    KT_CK(cudaMemsetAsync(g->done, 0, size_t(G), s));
+    KT_CK(cudaMemsetAsync(g->rounds_g, 0, size_t(G) * 4, s));
+    const bool timing = g->timing != 0;
+    if (timing) {
+        KT_CK(ensure_events(g, 2));
+        KT_CK(cudaEventRecord(g->events[0], s));
+    }
+    int launches = 0, support_launches = 0, rounds = 0;
+    kt::Live cur{g->rp0, g->col0, nullptr, n, m};
+    int buf = 0;
+    while (cur.m > 0) {
+        ++rounds;
+        KT_CK(cudaMemsetAsync(g->S, 0, size_t(cur.m) * 4, s));
+        KT_CK(cudaMemsetAsync(g->cnt, 0, sizeof(kt::RoundCounters), s));
+        KT_CK(cudaMemsetAsync(g->live_g, 0, size_t(G) * 4, s));
+        KT_CK(cudaMemsetAsync(g->removed_g, 0, size_t(G) * 4, s));
+        KT_CK(support_step(g, cur, s, &launches, nullptr));
+        ++support_launches;
+        KT_CK(kt::launch_batch_prune(cur, g->S, g->gid, g->thr, g->keep, g->live_g, g->removed_g,
+                                     g->done, g->rounds_g, G, g->tile_count, g->tile_off, g->cnt,
+                                     s, &launches));
+        const int nb = buf;
+        KT_CK(kt::launch_batch_compact(cur, g->S, g->keep, g->done, g->gid, g->tile_off, g->cnt,
+                                       g->pos, g->rp[nb], g->col[nb], g->eid[nb], mask_d, sup_d,
+                                       s, &launches));
+        KT_CK(cudaMemcpyAsync(g->cnt_host, g->cnt, sizeof(kt::RoundCounters),
+                              cudaMemcpyDeviceToHost, s));
+        KT_CK(cudaStreamSynchronize(s));
+        const kt::RoundCounters c = *g->cnt_host;
+        if (c.error) return (c.error & kt::kDevErrTimeout) ? KTRUSS_ETIMEOUT : KTRUSS_ECUDA;
+        g->live.push_back(cur.m);
+        g->tris.push_back(int64_t(c.triangles));
+        g->merge.push_back(int64_t(c.merge_work));
+        g->removed.push_back(int64_t(cur.m) - c.kept);
+        g->ms_sup.push_back(0.f);
+        cur = kt::Live{g->rp[nb], g->col[nb], g->eid[nb], n, c.kept};
+        buf ^= 1;
+    }
+    if (timing) KT_CK(cudaEventRecord(g->events[1], s));
+    if (mem_kind == KTRUSS_HOST && m > 0) {
+        KT_CK(cudaMemcpyAsync(mask_out, mask_d, size_t(m), cudaMemcpyDeviceToHost, s));
+        if (support_out)
+            KT_CK(cudaMemcpyAsync(support_out, sup_d, size_t(m) * 4, cudaMemcpyDeviceToHost, s));
+    }
+    if (rounds_out)
+        KT_CK(cudaMemcpyAsync(rounds_out, g->rounds_g, size_t(G) * 4, cudaMemcpyDeviceToHost, s));
+    KT_CK(cudaStreamSynchronize(s));
+    g->st = ktruss_stats_t{};
+    g->st.rounds = rounds;
+    g->st.edges_in = g->m;
+    g->st.per_round_len = rounds;
+    g->st.removed_per_round = g->removed.data();
+    g->st.live_per_round = g->live.data();
+    g->st.triangles_per_round = g->tris.data();
+    g->st.ms_support_per_round = g->ms_sup.data();
+    g->st.merge_work_per_round = g->merge.data();
+    g->st.ms_total = timing ? elapsed(g->events[0], g->events[1]) : 0.f;
+    g->st.support_launches = support_launches;
+    g->st.kernel_launches = launches;
+    g->has_stats = true;
+    return KTRUSS_OK;
+}
+
 int ktruss_graph_size(const ktruss_graph *g, int32_t *n, int64_t *m) {
     if (!g || !n || !m) return KTRUSS_EINVAL;
     *n = g->n;
@@ -229,7 +399,7 @@ int ktruss_set_option(ktruss_graph *g, int32_t key, int64_t value) {
     switch (key) {
         case KTRUSS_OPT_SUPPORT_KERNEL:
             if (value != KTRUSS_KERNEL_BALANCED && value != KTRUSS_KERNEL_EDGE &&
-                value != KTRUSS_KERNEL_COARSE)
+                value != KTRUSS_KERNEL_COARSE && value != KTRUSS_KERNEL_AUTO)
                 return KTRUSS_EINVAL;
             g->support_kernel = int(value);
             return KTRUSS_OK;
@@ -297,21 +467,8 @@ int ktruss_run(ktruss_graph *g, int32_t K, uint8_t *mask_out, int32_t *support_o
         KT_CK(cudaMemsetAsync(g->S, 0, size_t(cur.m) * 4, s));
         KT_CK(cudaMemsetAsync(g->cnt, 0, sizeof(kt::RoundCounters), s));
         if (timing) KT_CK(cudaEventRecord(g->events[base + 0], s));
-        if (g->support_kernel == KTRUSS_KERNEL_EDGE || g->support_kernel == KTRUSS_KERNEL_COARSE) {
-            if (timing) KT_CK(cudaEventRecord(g->events[base + 1], s));
-            if (g->support_kernel == KTRUSS_KERNEL_EDGE)
-                KT_CK(kt::launch_support_edge(cur, g->S, g->cnt, s));
-            else
-                KT_CK(kt::launch_support_coarse(cur, g->S, g->cnt, s));
-            ++launches;
-            ++support_launches;
-        } else {
-            int l = 0;
-            KT_CK(kt::launch_support_balanced(cur, g->S, g->cnt, &g->bs, s, &l,
-                                              timing ? &g->events[base + 0] : nullptr));
-            launches += l;
-            ++support_launches;
-        }
+        KT_CK(support_step(g, cur, s, &launches, timing ? &g->events[base + 0] : nullptr));
+        ++support_launches;
         if (timing) KT_CK(cudaEventRecord(g->events[base + 2], s));
         KT_CK(kt::launch_prune_count(g->S, cur.m, thr, g->tile_count, g->tile_off, g->cnt, s,
                                      &launches));
@@ -437,17 +594,7 @@ int ktruss_decompose(ktruss_graph *g, int32_t *trussness_out, int32_t *kmax_out,
             ++rounds;
             KT_CK(cudaMemsetAsync(g->S, 0, size_t(cur.m) * 4, s));
             KT_CK(cudaMemsetAsync(g->cnt, 0, sizeof(kt::RoundCounters), s));
-            if (g->support_kernel == KTRUSS_KERNEL_EDGE) {
-                KT_CK(kt::launch_support_edge(cur, g->S, g->cnt, s));
-                ++launches;
-            } else if (g->support_kernel == KTRUSS_KERNEL_COARSE) {
-                KT_CK(kt::launch_support_coarse(cur, g->S, g->cnt, s));
-                ++launches;
-            } else {
-                int l = 0;
-                KT_CK(kt::launch_support_balanced(cur, g->S, g->cnt, &g->bs, s, &l, nullptr));
-                launches += l;
-            }
+            KT_CK(support_step(g, cur, s, &launches, nullptr));
             ++support_launches;
         }
         KT_CK(kt::launch_prune_count(g->S, cur.m, K - 2, g->tile_count, g->tile_off, g->cnt, s,

@@ -176,6 +176,21 @@ cudaError_t launch_compact(const Live &in, const int32_t *S, int32_t thr, const 
     return cudaGetLastError();
 }
 
+cudaError_t launch_scan_tiles(const int32_t *tile_count, int32_t tiles, int32_t *tile_off,
+                              RoundCounters *cnt, cudaStream_t s, int *launches) {
+    scan_tiles_kernel<<<1, 1024, 0, s>>>(tile_count, tiles, tile_off, cnt);
+    ++*launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rowptr(const Live &in, const int32_t *pos, const RoundCounters *cnt,
+                          int32_t *rp_out, cudaStream_t s, int *launches) {
+    const int64_t rows = int64_t(in.n) + 1;
+    rowptr_kernel<<<int((rows + 255) / 256), 256, 0, s>>>(in.rp, in.n, in.m, pos, cnt, rp_out);
+    ++*launches;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_finalize(const Live &g, const int32_t *S, uint8_t *mask_out,
                             int32_t *support_out, cudaStream_t s, int *launches) {
     if (g.m == 0) return cudaSuccess;

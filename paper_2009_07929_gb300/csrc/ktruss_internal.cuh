@@ -98,6 +98,36 @@ cudaError_t launch_compact(const Live &in, const int32_t *S, int32_t thr, const 
                            int32_t *support_out, cudaStream_t s, int *launches,
                            int32_t *level_out = nullptr, int32_t level = 0);
 
+// Exclusive scan of tile counts by one block (total -> cnt->kept).
+cudaError_t launch_scan_tiles(const int32_t *tile_count, int32_t tiles, int32_t *tile_off,
+                              RoundCounters *cnt, cudaStream_t s, int *launches);
+
+// rp_out[i] = pos[rp_in[i]] (cnt->kept where rp_in[i] == m).
+cudaError_t launch_rowptr(const Live &in, const int32_t *pos, const RoundCounters *cnt,
+                          int32_t *rp_out, cudaStream_t s, int *launches);
+
+// ---- batches (batch.cu) -----------------------------------------------------
+// gid[v] = graph of vertex v for vertex offsets vo[G+1].
+cudaError_t launch_graph_of_vertex(const int32_t *vo, int32_t G, int32_t n, int32_t *gid,
+                                   cudaStream_t s);
+// Sets bit 16 of *err if an edge joins two graphs.
+cudaError_t launch_batch_validate(const int32_t *rp, const int32_t *col, int32_t n,
+                                  const int32_t *gid, int32_t *err, cudaStream_t s);
+// Per-graph thresholds: keep flags, per-graph live/removed counts (zero on
+// entry), finished flags and round counters, tile counts and their scan
+// (edges that stay live -> cnt->kept).
+cudaError_t launch_batch_prune(const Live &g, const int32_t *S, const int32_t *gid,
+                               const int32_t *thr, uint8_t *keep, int32_t *live_g,
+                               int32_t *removed_g, uint8_t *done, int32_t *rounds_g, int32_t G,
+                               int32_t *tile_count, int32_t *tile_off, RoundCounters *cnt,
+                               cudaStream_t s, int *launches);
+// Compaction of the edges that stay live; outputs of the edges that leave.
+cudaError_t launch_batch_compact(const Live &in, const int32_t *S, const uint8_t *keep,
+                                 const uint8_t *done, const int32_t *gid, const int32_t *tile_off,
+                                 const RoundCounters *cnt, int32_t *pos, int32_t *rp_out,
+                                 int32_t *col_out, int32_t *eid_out, uint8_t *mask_out,
+                                 int32_t *support_out, cudaStream_t s, int *launches);
+
 // Final outputs of the surviving edges: mask 1 and support S at their input id.
 cudaError_t launch_finalize(const Live &g, const int32_t *S, uint8_t *mask_out,
                             int32_t *support_out, cudaStream_t s, int *launches);
