@@ -228,6 +228,37 @@ def measure_batched(kt, gg, count, m_hi, seed=0):
             "max_graph_rounds": int(max(rounds)) if len(rounds) else 0}
 
 
+def measure_serving(kt, gg, count, m_hi, seed=0):
+    """Serving workload (graphgen.serve_config: R-MAT or G(n,m) with p = 1/2,
+    sizes log-uniform in [1e4, m_hi] edges, K uniform in 3..16) through the
+    request server: first all requests at once (saturated graphs/s), then
+    Poisson arrivals at 70% of that rate (p50/p99 latency, graphs/s)."""
+    reqs = gg.serve_config(count, seed=seed, m_lo=1e4, m_hi=m_hi)
+    edges = sum(g.m for g, _ in reqs)
+    mv = sum(g.n for g, _ in reqs) + 1
+    me = min(edges + 1, (1 << 31) - 1)
+
+    def server():
+        return kt.Server(max_vertices=mv, max_edges=me, max_requests=max(8, count))
+
+    warm = server()
+    kt.serve_poisson(warm, reqs[: min(4, count)], rate=None)
+    warm.close()
+    srv = server()
+    _, sat_s, _ = kt.serve_poisson(srv, reqs, rate=None)
+    srv.close()
+    sat = count / sat_s
+    srv = server()
+    lat, mk, _ = kt.serve_poisson(srv, reqs, rate=0.7 * sat, seed=seed + 1)
+    srv.close()
+    import numpy as np
+    return {"requests": count, "edges": int(edges), "m_range": [10000, int(m_hi)],
+            "saturated_graphs_per_s": round(sat, 2), "arrival_rate": round(0.7 * sat, 2),
+            "graphs_per_s": round(count / mk, 2),
+            "p50_latency_ms": round(float(np.percentile(lat, 50)) * 1e3, 3),
+            "p99_latency_ms": round(float(np.percentile(lat, 99)) * 1e3, 3)}
+
+
 def run_reference(args, world, rank):
     """Reference arm: the CPU oracle as it stands, on a bounded sample."""
     if rank != 0:
@@ -274,6 +305,11 @@ def main():
     ap.add_argument("--no-kmax", action="store_true", help="skip the K_max sweep timing")
     ap.add_argument("--batch-graphs", type=int, default=4096,
                     help="graphs of the batched-vs-plain measurement (0 = skip)")
+    ap.add_argument("--serve-requests", type=int, default=64,
+                    help="requests of the serving measurement (0 = skip)")
+    ap.add_argument("--serve-mmax", type=float, default=1e6,
+                    help="largest request size (edges) of the serving measurement; the full "
+                         "serving workload uses 5e7")
     ap.add_argument("--batch-mmax", type=float, default=1e5,
                     help="largest graph size (edges) of that batch; the full batching "
                          "workload uses 2e6")
@@ -435,6 +471,8 @@ def main():
                              "what": "ktruss_decompose: K = 3 .. K_max, each K from the previous truss"}
     if args.batch_graphs > 0:
         out["batched"] = measure_batched(kt, gg, args.batch_graphs, args.batch_mmax)
+    if args.serve_requests > 0:
+        out["serving"] = measure_serving(kt, gg, args.serve_requests, args.serve_mmax)
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline()
     print(json.dumps(out), flush=True)

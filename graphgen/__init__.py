@@ -283,3 +283,28 @@ def batch_config(count: int, seed: int = 0, m_lo: float = 1e3, m_hi: float = 2e6
             csr = rmat(scale, 16, sub_seed)
         out.append((csr, K))
     return out
+
+
+def serve_config(count: int, seed: int = 0, m_lo: float = 1e4, m_hi: float = 5e7,
+                 k_lo: int = 3, k_hi: int = 16):
+    """The serving workload: `count` requests, each an R-MAT or a G(n, m)
+    graph with probability 1/2, target size log-uniform in [m_lo, m_hi] edges
+    (same recipes as batch_config), K uniform in [k_lo, k_hi].  Returns a list
+    of (CSR, K)."""
+    import math
+    key = stream_key(6, seed, count)
+    out = []
+    for r in range(count):
+        u = _unit(key, 5 * r)
+        mt = int(round(math.exp(math.log(m_lo) + u * (math.log(m_hi) - math.log(m_lo)))))
+        K = k_lo + int(_unit(key, 5 * r + 1) * (k_hi - k_lo + 1))
+        sub_seed = rand_u64(key, 5 * r + 2) & 0x7FFFFFFF
+        if _unit(key, 5 * r + 3) < 0.5:
+            d = 8.0 + _unit(key, 5 * r + 4) * 56.0
+            n = max(int(math.ceil(2 * mt / d)), int(math.ceil(2 * math.sqrt(mt))) + 1)
+            csr = er(n, mt, sub_seed)
+        else:
+            scale = min(30, max(10, int(math.ceil(math.log2(max(mt, 1) / 16.0)))))
+            csr = rmat(scale, 16, sub_seed)
+        out.append((csr, K))
+    return out

@@ -160,6 +160,56 @@ int ktruss_run_batch(ktruss_graph *g, const int32_t *K, uint8_t *mask_out, int32
                      int32_t *rounds_out, int mem_kind, void *cuda_stream);
 
 /*
+ * K-truss request server (continuous batching; the paper serves one graph at
+ * a time).  Requests are graphs in host memory with their own K.  Each
+ * ktruss_server_step admits queued requests in arrival order while they fit
+ * (a free request slot, room for the graph in the live state, and the
+ * request's own device bytes — staged input plus outputs, see
+ * ktruss_server_submit — within the budget), runs one peel round of Alg. 1
+ * over all active requests as one batched computation, and completes the
+ * requests whose round removed nothing (or removed every live edge).  Each
+ * request gets exactly the outputs and round count of its own ktruss_run.
+ *
+ * ktruss_server_create: capacities of the live state (max_vertices,
+ * max_edges < 2^31: sums over active requests), max_requests active at once,
+ * request_bytes_budget = device bytes for the requests' own buffers; work is
+ * issued on cuda_stream.  KTRUSS_EINVAL for bad sizes; KTRUSS_ENOMEM,
+ * KTRUSS_ECUDA.
+ */
+typedef struct ktruss_server ktruss_server;
+int ktruss_server_create(ktruss_server **out, int32_t max_vertices, int64_t max_edges,
+                         int32_t max_requests, int64_t request_bytes_budget, void *cuda_stream);
+
+/*
+ * Queues a request: strictly upper-triangular CSR (n, m, row_ptr, col) in
+ * HOST memory (copied here; the caller may free it on return) and its K >= 2.
+ * mask_out (uint8[m]) and support_out (int32[m] or NULL) are HOST buffers the
+ * caller keeps valid until the request is reported done; they are written
+ * when it completes.  The request's device bytes are 4(n+1+m) + 5m + 768.
+ * *ticket_out (may be NULL) identifies it.  KTRUSS_EINVAL for bad arguments,
+ * a malformed CSR, or a graph that could never fit the server's capacities.
+ */
+int ktruss_server_submit(ktruss_server *srv, int32_t n, int64_t m, const int32_t *row_ptr,
+                         const int32_t *col, int32_t K, uint8_t *mask_out, int32_t *support_out,
+                         int64_t *ticket_out);
+
+/* Admission + one peel round + completion (see above); returns after the
+ * round's work and the completed requests' output copies have finished.
+ * *num_done (may be NULL) = requests completed by this step. */
+int ktruss_server_step(ktruss_server *srv, int32_t *num_done);
+
+/* Drains up to max completed (ticket, rounds) pairs, oldest first. */
+int ktruss_server_take_done(ktruss_server *srv, int64_t *tickets, int32_t *rounds, int32_t max,
+                            int32_t *count);
+
+/* Queued requests, active requests, live edges (each pointer may be NULL). */
+int ktruss_server_status(const ktruss_server *srv, int32_t *queued, int32_t *active,
+                         int64_t *live_edges);
+
+/* Releases the server and every buffer it holds (NULL is a no-op). */
+void ktruss_server_free(ktruss_server *srv);
+
+/*
  * Truss decomposition of the loaded graph: trussness_out[e] = the largest K
  * such that edge e is in the K-truss (2 for an edge in no triangle), and
  * *kmax_out = the largest K whose K-truss is not empty (0 for a graph with no

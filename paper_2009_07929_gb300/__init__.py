@@ -90,6 +90,17 @@ def lib():
         L.ktruss_run_batch.restype = ctypes.c_int
         L.ktruss_batch_size.argtypes = [vp, ctypes.POINTER(i32)]
         L.ktruss_batch_size.restype = ctypes.c_int
+        L.ktruss_server_create.argtypes = [ctypes.POINTER(vp), i32, i64, i32, i64, vp]
+        L.ktruss_server_submit.argtypes = [vp, i32, i64, vp, vp, i32, vp, vp, ctypes.POINTER(i64)]
+        L.ktruss_server_step.argtypes = [vp, ctypes.POINTER(i32)]
+        L.ktruss_server_take_done.argtypes = [vp, vp, vp, i32, ctypes.POINTER(i32)]
+        L.ktruss_server_status.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                           ctypes.POINTER(i64)]
+        L.ktruss_server_free.argtypes = [vp]
+        L.ktruss_server_free.restype = None
+        for f in (L.ktruss_server_create, L.ktruss_server_submit, L.ktruss_server_step,
+                  L.ktruss_server_take_done, L.ktruss_server_status):
+            f.restype = ctypes.c_int
         L.ktruss_decompose.restype = ctypes.c_int
         L.ktruss_stats.argtypes = [vp, ctypes.POINTER(_Stats)]
         L.ktruss_set_option.argtypes = [vp, i32, i64]
@@ -324,6 +335,108 @@ def load_batch(graphs=None, vertex_offsets=None, row_ptr=None, col=None, stream=
                                  rp_p, c_p, rp_kind, _stream_ptr(stream))
     _check(rc, "ktruss_load_batch")
     return Graph(h.value, rp_len - 1, m)
+
+
+class Server:
+    """K-truss request server (ktruss_server_*): continuous batching of
+    requests with different graphs and K.  submit() queues a host CSR;
+    step() admits what fits, runs one batched peel round and returns the
+    requests completed by it as (ticket, rounds, mask, support)."""
+
+    def __init__(self, max_vertices: int, max_edges: int, max_requests: int = 256,
+                 request_bytes: int | None = None, stream=None):
+        if request_bytes is None:
+            request_bytes = 12 * max_edges + 8 * max_vertices + 1024 * max_requests
+        h = ctypes.c_void_p(0)
+        rc = lib().ktruss_server_create(ctypes.byref(h), max_vertices, max_edges, max_requests,
+                                        request_bytes, _stream_ptr(stream))
+        _check(rc, "ktruss_server_create")
+        self._h = h
+        self._pending = {}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().ktruss_server_free(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, row_ptr, col, K: int, support: bool = True) -> int:
+        rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+        c = np.ascontiguousarray(col, dtype=np.int32)
+        m = c.shape[0]
+        mask = np.zeros(max(m, 1), dtype=np.uint8)
+        sup = np.zeros(max(m, 1), dtype=np.int32) if support else None
+        t = ctypes.c_int64(0)
+        rc = lib().ktruss_server_submit(self._h, rp.shape[0] - 1, m, rp.ctypes.data,
+                                        c.ctypes.data if m else None, K, mask.ctypes.data,
+                                        sup.ctypes.data if sup is not None else None,
+                                        ctypes.byref(t))
+        _check(rc, "ktruss_server_submit")
+        self._pending[t.value] = (mask[:m], sup[:m] if sup is not None else None)
+        return t.value
+
+    def step(self):
+        nd = ctypes.c_int32(0)
+        _check(lib().ktruss_server_step(self._h, ctypes.byref(nd)), "ktruss_server_step")
+        out = []
+        if nd.value:
+            tk = np.zeros(nd.value, dtype=np.int64)
+            rd = np.zeros(nd.value, dtype=np.int32)
+            cnt = ctypes.c_int32(0)
+            _check(lib().ktruss_server_take_done(self._h, tk.ctypes.data, rd.ctypes.data,
+                                                 nd.value, ctypes.byref(cnt)),
+                   "ktruss_server_take_done")
+            for t, r in zip(tk[:cnt.value], rd[:cnt.value]):
+                mask, sup = self._pending.pop(int(t))
+                out.append((int(t), int(r), mask, sup))
+        return out
+
+    def status(self):
+        q, a, e = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int64(0)
+        _check(lib().ktruss_server_status(self._h, ctypes.byref(q), ctypes.byref(a),
+                                          ctypes.byref(e)), "ktruss_server_status")
+        return q.value, a.value, e.value
+
+
+def serve_poisson(server, requests, rate, seed=0, clock=None):
+    """Feeds (csr, K) requests to a Server with Poisson arrivals of the given
+    rate (requests/s; None = all at time 0) in real time and steps it until
+    every request is done.  Returns per-request latencies (s, arrival to
+    completion), the makespan and the results by request index."""
+    import time
+    clock = clock or time.perf_counter
+    rng = np.random.default_rng(seed)
+    N = len(requests)
+    arrivals = (np.zeros(N) if rate is None
+                else np.cumsum(rng.exponential(1.0 / rate, size=N)))
+    t0 = clock()
+    i = 0
+    ticket_of = {}
+    latency = np.zeros(N)
+    results = [None] * N
+    done = 0
+    while done < N:
+        now = clock() - t0
+        while i < N and arrivals[i] <= now:
+            g, K = requests[i]
+            ticket_of[server.submit(g.row_ptr, g.col, K)] = i
+            i += 1
+        q, a, _ = server.status()
+        if q == 0 and a == 0:
+            if i < N:
+                time.sleep(max(0.0, min(0.001, arrivals[i] - (clock() - t0))))
+            continue
+        for t, r, mask, sup in server.step():
+            k = ticket_of.pop(t)
+            latency[k] = (clock() - t0) - arrivals[k]
+            results[k] = (r, mask, sup)
+            done += 1
+    return latency, clock() - t0, results
 
 
 NOALLOC_MAX_VERTICES = 1 << 19

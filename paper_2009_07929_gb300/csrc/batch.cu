@@ -173,6 +173,16 @@ cudaError_t launch_batch_validate(const int32_t *rp, const int32_t *col, int32_t
     return cudaGetLastError();
 }
 
+cudaError_t launch_batch_keep(const Live &g, const int32_t *S, const int32_t *gid,
+                              const int32_t *thr, uint8_t *keep, int32_t *live_g,
+                              int32_t *removed_g, cudaStream_t s, int *launches) {
+    if (g.m == 0) return cudaSuccess;
+    batch_prune_kernel<<<(g.m + 255) / 256, 256, 0, s>>>(S, g.col, g.m, gid, thr, keep, live_g,
+                                                         removed_g);
+    ++*launches;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_batch_prune(const Live &g, const int32_t *S, const int32_t *gid,
                                const int32_t *thr, uint8_t *keep, int32_t *live_g,
                                int32_t *removed_g, uint8_t *done, int32_t *rounds_g, int32_t G,

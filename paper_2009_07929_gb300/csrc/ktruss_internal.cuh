@@ -121,6 +121,34 @@ cudaError_t launch_batch_prune(const Live &g, const int32_t *S, const int32_t *g
                                int32_t *removed_g, uint8_t *done, int32_t *rounds_g, int32_t G,
                                int32_t *tile_count, int32_t *tile_off, RoundCounters *cnt,
                                cudaStream_t s, int *launches);
+// Keep flags (support >= threshold of the edge's graph) and per-graph live and
+// removed counts (zero on entry) only.
+cudaError_t launch_batch_keep(const Live &g, const int32_t *S, const int32_t *gid,
+                              const int32_t *thr, uint8_t *keep, int32_t *live_g,
+                              int32_t *removed_g, cudaStream_t s, int *launches);
+
+// ---- request server (server_kernels.cu) --------------------------------------
+// Appends a request's device CSR at vertex base nb / edge base mb of the live CSR.
+cudaError_t launch_server_append(const int32_t *rp_in, const int32_t *col_in, int32_t n, int32_t m,
+                                 int32_t nb, int32_t mb, int32_t slot, int32_t *rp, int32_t *col,
+                                 int32_t *eid, int32_t *gid, cudaStream_t s);
+// Keep flags and per-slot counts (= launch_batch_keep).
+cudaError_t launch_server_prune(const Live &cur, const int32_t *S, const int32_t *gid,
+                                const int32_t *thr, uint8_t *keep, int32_t *live_g,
+                                int32_t *removed_g, cudaStream_t s, int *launches);
+// Finished slots, vertex renumbering (vcnt->kept = surviving vertices),
+// edge compaction (cnt->kept = surviving edges) with outputs of leaving edges
+// through the per-slot pointer tables, new row pointers and slot ids.
+cudaError_t launch_server_round_tail(const Live &cur, const int32_t *S, const uint8_t *keep,
+                                     const int32_t *live_g, const int32_t *removed_g,
+                                     uint8_t *fin, int32_t *rounds_g, int32_t slots,
+                                     const int32_t *gid, int32_t *vmap, int32_t *vtile_count,
+                                     int32_t *vtile_off, RoundCounters *vcnt, int32_t *etile_count,
+                                     int32_t *etile_off, RoundCounters *cnt, int32_t *pos,
+                                     int32_t *rp_out, int32_t *col_out, int32_t *eid_out,
+                                     int32_t *gid_out, uint8_t *const *mask_ptr,
+                                     int32_t *const *sup_ptr, cudaStream_t s, int *launches);
+
 // Compaction of the edges that stay live; outputs of the edges that leave.
 cudaError_t launch_batch_compact(const Live &in, const int32_t *S, const uint8_t *keep,
                                  const uint8_t *done, const int32_t *gid, const int32_t *tile_off,

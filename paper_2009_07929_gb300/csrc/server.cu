@@ -1,0 +1,383 @@
+// K-truss request server: continuous batching of many K-truss queries.
+//
+// Requests (a graph in host memory and its K) are queued by
+// ktruss_server_submit.  Each ktruss_server_step:
+//   1. admits queued requests in arrival order while they fit: a free slot,
+//      room in the live CSR (vertices, edges) and in the device budget for
+//      the request's own input staging and output buffers (its HBM
+//      footprint); an admitted request's graph is copied to the device and
+//      appended to the live CSR;
+//   2. runs one peel round (support step over every active request, then each
+//      request pruned with its own threshold) — the rounds of all active
+//      requests are one batched computation on the device;
+//   3. finishes the requests whose round removed nothing or removed every
+//      live edge (their outputs are already in their device buffers), copies
+//      their outputs to the caller's host buffers and frees their memory.
+// A request therefore goes through exactly the bulk rounds of its own
+// ktruss_run, whatever else is in flight (the paper's Alg. 1 per request).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <deque>
+#include <new>
+#include <vector>
+
+#include "ktruss.h"
+#include "ktruss_internal.cuh"
+
+namespace {
+
+struct Request {
+    int64_t ticket;
+    int32_t n;
+    int64_t m;
+    int32_t K;
+    std::vector<int32_t> rp, col;
+    uint8_t *mask_out;
+    int32_t *support_out;
+};
+
+struct Slot {
+    bool used = false;
+    int64_t ticket = 0;
+    int32_t n = 0;
+    int64_t m = 0;
+    size_t bytes = 0;
+    uint8_t *host_mask = nullptr;
+    int32_t *host_sup = nullptr;
+    uint8_t *dmask = nullptr;
+    int32_t *dsup = nullptr;
+    int32_t *din = nullptr;  // staged input: row_ptr then col
+};
+
+constexpr int32_t kAutoSmallEdges = 1 << 17;
+
+int map_err(cudaError_t e) {
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? KTRUSS_ENOMEM : KTRUSS_ECUDA;
+}
+
+#define SV_CK(call)                                \
+    do {                                           \
+        cudaError_t e_ = (call);                   \
+        if (e_ != cudaSuccess) return map_err(e_); \
+    } while (0)
+
+}  // namespace
+
+struct ktruss_server {
+    int32_t vcap = 0;
+    int64_t ecap = 0;
+    int32_t slots = 0;
+    int64_t budget = 0, used = 0;
+    cudaStream_t s = nullptr;
+    int32_t *rp[2] = {}, *col[2] = {}, *eid[2] = {}, *gid[2] = {};
+    int32_t *S = nullptr, *pos = nullptr, *vmap = nullptr;
+    uint8_t *keep = nullptr, *fin = nullptr;
+    int32_t *thr = nullptr, *live_g = nullptr, *removed_g = nullptr, *rounds_g = nullptr;
+    uint8_t **mask_ptr = nullptr;
+    int32_t **sup_ptr = nullptr;
+    int32_t *etile_count = nullptr, *etile_off = nullptr, *vtile_count = nullptr,
+            *vtile_off = nullptr;
+    kt::RoundCounters *cnt = nullptr;       // [0] edges, [1] vertices
+    kt::RoundCounters *cnt_host = nullptr;  // pinned [2]
+    uint8_t *fin_host = nullptr;            // pinned [slots]
+    int32_t *rounds_host = nullptr;         // pinned [slots]
+    void **ptr_host = nullptr;              // pinned [2 * slots] staging of slot pointers
+    int32_t *thr_host = nullptr;            // pinned [slots]
+    kt::BalancedScratch bs;
+    std::vector<void *> owned;
+    int cur = 0;
+    int32_t n_live = 0;
+    int32_t m_live = 0;
+    int64_t next_ticket = 1;
+    std::deque<Request> queue;
+    std::vector<Slot> slot;
+    std::vector<int64_t> done_tickets;
+    std::vector<int32_t> done_rounds;
+    int64_t steps = 0;
+};
+
+namespace {
+
+void server_release(ktruss_server *v) {
+    if (!v) return;
+    for (Slot &sl : v->slot) {
+        if (sl.dmask) cudaFree(sl.dmask);
+        if (sl.dsup) cudaFree(sl.dsup);
+        if (sl.din) cudaFree(sl.din);
+    }
+    for (void *p : v->owned) cudaFree(p);
+    kt::balanced_scratch_free(&v->bs);
+    if (v->cnt_host) cudaFreeHost(v->cnt_host);
+    if (v->fin_host) cudaFreeHost(v->fin_host);
+    if (v->rounds_host) cudaFreeHost(v->rounds_host);
+    if (v->ptr_host) cudaFreeHost(v->ptr_host);
+    if (v->thr_host) cudaFreeHost(v->thr_host);
+    delete v;
+}
+
+bool valid_csr(int32_t n, int64_t m, const int32_t *rp, const int32_t *col) {
+    if (rp[0] != 0 || rp[n] != m) return false;
+    for (int32_t i = 0; i < n; ++i) {
+        if (rp[i + 1] < rp[i] || rp[i + 1] > m) return false;
+        for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+            if (col[p] <= i || col[p] >= n) return false;
+            if (p > rp[i] && col[p] <= col[p - 1]) return false;
+        }
+    }
+    return true;
+}
+
+// Device bytes a request holds while active besides the shared live CSR:
+// staged input and its output buffers.
+size_t request_bytes(int32_t n, int64_t m) {
+    return (size_t(n) + 1 + size_t(m)) * 4 + size_t(m) * 5 + 768;
+}
+
+cudaError_t support_step(ktruss_server *v, const kt::Live &g, int *launches) {
+    if (g.m < kAutoSmallEdges) {
+        ++*launches;
+        return kt::launch_support_edge(g, v->S, v->cnt, v->s);
+    }
+    return kt::launch_support_balanced(g, v->S, v->cnt, &v->bs, v->s, launches, nullptr);
+}
+
+}  // namespace
+
+extern "C" {
+
+int ktruss_server_create(ktruss_server **out, int32_t max_vertices, int64_t max_edges,
+                         int32_t max_requests, int64_t request_bytes_budget, void *cuda_stream) {
+    if (!out) return KTRUSS_EINVAL;
+    *out = nullptr;
+    if (max_vertices < 1 || max_edges < 1 || max_edges >= (int64_t(1) << 31) || max_requests < 1 ||
+        request_bytes_budget < 0)
+        return KTRUSS_EINVAL;
+    ktruss_server *v = new (std::nothrow) ktruss_server();
+    if (!v) return KTRUSS_ENOMEM;
+    v->vcap = max_vertices;
+    v->ecap = max_edges;
+    v->slots = max_requests;
+    v->budget = request_bytes_budget;
+    v->s = static_cast<cudaStream_t>(cuda_stream);
+    v->slot.resize(size_t(max_requests));
+    const size_t nb = (size_t(max_vertices) + 1) * 4, eb = size_t(max_edges) * 4;
+    const size_t sb = size_t(max_requests) * 4;
+    const int32_t et = kt::compact_tiles(int32_t(max_edges)) + 1;
+    const int32_t vt = kt::compact_tiles(max_vertices) + 1;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](void **p, size_t bytes) {
+        if (e != cudaSuccess) return;
+        e = cudaMalloc(p, bytes ? bytes : 16);
+        if (e == cudaSuccess) v->owned.push_back(*p);
+    };
+    for (int b = 0; b < 2; ++b) {
+        A((void **)&v->rp[b], nb);
+        A((void **)&v->col[b], eb);
+        A((void **)&v->eid[b], eb);
+        A((void **)&v->gid[b], nb);
+    }
+    A((void **)&v->S, eb);
+    A((void **)&v->pos, eb);
+    A((void **)&v->vmap, nb);
+    A((void **)&v->keep, size_t(max_edges));
+    A((void **)&v->fin, size_t(max_requests));
+    A((void **)&v->thr, sb);
+    A((void **)&v->live_g, sb);
+    A((void **)&v->removed_g, sb);
+    A((void **)&v->rounds_g, sb);
+    A((void **)&v->mask_ptr, size_t(max_requests) * sizeof(void *));
+    A((void **)&v->sup_ptr, size_t(max_requests) * sizeof(void *));
+    A((void **)&v->etile_count, size_t(et) * 4);
+    A((void **)&v->etile_off, size_t(et) * 4);
+    A((void **)&v->vtile_count, size_t(vt) * 4);
+    A((void **)&v->vtile_off, size_t(vt) * 4);
+    A((void **)&v->cnt, 2 * sizeof(kt::RoundCounters));
+    if (e == cudaSuccess) e = kt::balanced_scratch_alloc(&v->bs, max_vertices, max_edges);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&v->cnt_host, 2 * sizeof(kt::RoundCounters));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&v->fin_host, size_t(max_requests));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&v->rounds_host, sb);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&v->ptr_host, 2 * size_t(max_requests) * sizeof(void *));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&v->thr_host, sb);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v->rp[0], 0, 4, v->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(v->s);
+    if (e != cudaSuccess) {
+        const int rc = map_err(e);
+        server_release(v);
+        return rc;
+    }
+    *out = v;
+    return KTRUSS_OK;
+}
+
+void ktruss_server_free(ktruss_server *srv) { server_release(srv); }
+
+int ktruss_server_submit(ktruss_server *srv, int32_t n, int64_t m, const int32_t *row_ptr,
+                         const int32_t *col, int32_t K, uint8_t *mask_out, int32_t *support_out,
+                         int64_t *ticket_out) {
+    if (!srv || n < 0 || m < 0 || K < 2 || !row_ptr || (m > 0 && (!col || !mask_out)))
+        return KTRUSS_EINVAL;
+    if (n > srv->vcap || m > srv->ecap ||
+        int64_t(request_bytes(n, m)) > srv->budget)
+        return KTRUSS_EINVAL;  // could never be admitted
+    if (!valid_csr(n, m, row_ptr, col)) return KTRUSS_EINVAL;
+    Request r;
+    r.ticket = srv->next_ticket++;
+    r.n = n;
+    r.m = m;
+    r.K = K;
+    r.rp.assign(row_ptr, row_ptr + n + 1);
+    if (m > 0) r.col.assign(col, col + m);
+    r.mask_out = mask_out;
+    r.support_out = support_out;
+    if (ticket_out) *ticket_out = r.ticket;
+    srv->queue.push_back(std::move(r));
+    return KTRUSS_OK;
+}
+
+int ktruss_server_step(ktruss_server *srv, int32_t *num_done) {
+    if (!srv) return KTRUSS_EINVAL;
+    if (num_done) *num_done = 0;
+    cudaStream_t s = srv->s;
+    int launches = 0;
+    int32_t finished = 0;
+    std::vector<Request> admitted;
+    // ---- 1. admission, in arrival order
+    while (!srv->queue.empty()) {
+        Request &r = srv->queue.front();
+        if (r.m == 0) {  // nothing to peel: 0 rounds, no output
+            srv->done_tickets.push_back(r.ticket);
+            srv->done_rounds.push_back(0);
+            ++finished;
+            srv->queue.pop_front();
+            continue;
+        }
+        int32_t sid = -1;
+        for (int32_t k = 0; k < srv->slots; ++k)
+            if (!srv->slot[size_t(k)].used) {
+                sid = k;
+                break;
+            }
+        const size_t bytes = request_bytes(r.n, r.m);
+        if (sid < 0 || int64_t(srv->n_live) + r.n > srv->vcap ||
+            int64_t(srv->m_live) + r.m > srv->ecap || srv->used + int64_t(bytes) > srv->budget)
+            break;
+        Slot &sl = srv->slot[size_t(sid)];
+        SV_CK(cudaMalloc((void **)&sl.din, (size_t(r.n) + 1 + size_t(r.m)) * 4));
+        SV_CK(cudaMalloc((void **)&sl.dmask, size_t(r.m)));
+        if (r.support_out) SV_CK(cudaMalloc((void **)&sl.dsup, size_t(r.m) * 4));
+        sl.used = true;
+        sl.ticket = r.ticket;
+        sl.n = r.n;
+        sl.m = r.m;
+        sl.bytes = bytes;
+        sl.host_mask = r.mask_out;
+        sl.host_sup = r.support_out;
+        srv->used += int64_t(bytes);
+        int32_t *drp = sl.din, *dcol = sl.din + r.n + 1;
+        SV_CK(cudaMemcpyAsync(drp, r.rp.data(), (size_t(r.n) + 1) * 4, cudaMemcpyHostToDevice, s));
+        SV_CK(cudaMemcpyAsync(dcol, r.col.data(), size_t(r.m) * 4, cudaMemcpyHostToDevice, s));
+        SV_CK(kt::launch_server_append(drp, dcol, r.n, int32_t(r.m), srv->n_live, srv->m_live, sid,
+                                       srv->rp[srv->cur], srv->col[srv->cur], srv->eid[srv->cur],
+                                       srv->gid[srv->cur], s));
+        ++launches;
+        srv->ptr_host[2 * sid] = sl.dmask;
+        srv->ptr_host[2 * sid + 1] = sl.dsup;
+        srv->thr_host[sid] = r.K - 2;
+        SV_CK(cudaMemcpyAsync(srv->mask_ptr + sid, &srv->ptr_host[2 * sid], sizeof(void *),
+                              cudaMemcpyHostToDevice, s));
+        SV_CK(cudaMemcpyAsync(srv->sup_ptr + sid, &srv->ptr_host[2 * sid + 1], sizeof(void *),
+                              cudaMemcpyHostToDevice, s));
+        SV_CK(cudaMemcpyAsync(srv->thr + sid, &srv->thr_host[sid], 4, cudaMemcpyHostToDevice, s));
+        SV_CK(cudaMemsetAsync(srv->rounds_g + sid, 0, 4, s));
+        srv->n_live += r.n;
+        srv->m_live += int32_t(r.m);
+        admitted.push_back(std::move(r));
+        srv->queue.pop_front();
+    }
+    // ---- 2. one peel round over every active request
+    if (srv->m_live > 0) {
+        const int c = srv->cur, o = c ^ 1;
+        const kt::Live g{srv->rp[c], srv->col[c], srv->eid[c], srv->n_live, srv->m_live};
+        SV_CK(cudaMemsetAsync(srv->S, 0, size_t(g.m) * 4, s));
+        SV_CK(cudaMemsetAsync(srv->cnt, 0, 2 * sizeof(kt::RoundCounters), s));
+        SV_CK(cudaMemsetAsync(srv->live_g, 0, size_t(srv->slots) * 4, s));
+        SV_CK(cudaMemsetAsync(srv->removed_g, 0, size_t(srv->slots) * 4, s));
+        SV_CK(support_step(srv, g, &launches));
+        SV_CK(kt::launch_server_prune(g, srv->S, srv->gid[c], srv->thr, srv->keep, srv->live_g,
+                                      srv->removed_g, s, &launches));
+        SV_CK(kt::launch_server_round_tail(
+            g, srv->S, srv->keep, srv->live_g, srv->removed_g, srv->fin, srv->rounds_g,
+            srv->slots, srv->gid[c], srv->vmap, srv->vtile_count, srv->vtile_off, srv->cnt + 1,
+            srv->etile_count, srv->etile_off, srv->cnt, srv->pos, srv->rp[o], srv->col[o],
+            srv->eid[o], srv->gid[o], srv->mask_ptr, srv->sup_ptr, s, &launches));
+        SV_CK(cudaMemcpyAsync(srv->cnt_host, srv->cnt, 2 * sizeof(kt::RoundCounters),
+                              cudaMemcpyDeviceToHost, s));
+        SV_CK(cudaMemcpyAsync(srv->fin_host, srv->fin, size_t(srv->slots), cudaMemcpyDeviceToHost, s));
+        SV_CK(cudaMemcpyAsync(srv->rounds_host, srv->rounds_g, size_t(srv->slots) * 4,
+                              cudaMemcpyDeviceToHost, s));
+        SV_CK(cudaStreamSynchronize(s));
+        srv->m_live = srv->cnt_host[0].kept;
+        srv->n_live = srv->cnt_host[1].kept;
+        srv->cur = o;
+        ++srv->steps;
+        // ---- 3. finished requests: outputs to the caller, memory back
+        std::vector<int32_t> fin_slots;
+        for (int32_t k = 0; k < srv->slots; ++k) {
+            Slot &sl = srv->slot[size_t(k)];
+            if (!sl.used || !srv->fin_host[k]) continue;
+            SV_CK(cudaMemcpyAsync(sl.host_mask, sl.dmask, size_t(sl.m), cudaMemcpyDeviceToHost, s));
+            if (sl.host_sup)
+                SV_CK(cudaMemcpyAsync(sl.host_sup, sl.dsup, size_t(sl.m) * 4,
+                                      cudaMemcpyDeviceToHost, s));
+            fin_slots.push_back(k);
+        }
+        if (!fin_slots.empty()) SV_CK(cudaStreamSynchronize(s));
+        for (int32_t k : fin_slots) {
+            Slot &sl = srv->slot[size_t(k)];
+            srv->done_tickets.push_back(sl.ticket);
+            srv->done_rounds.push_back(srv->rounds_host[k]);
+            ++finished;
+            cudaFree(sl.din);
+            cudaFree(sl.dmask);
+            if (sl.dsup) cudaFree(sl.dsup);
+            srv->used -= int64_t(sl.bytes);
+            sl = Slot{};
+        }
+    } else {
+        SV_CK(cudaStreamSynchronize(s));
+    }
+    if (num_done) *num_done = finished;
+    return KTRUSS_OK;
+}
+
+int ktruss_server_take_done(ktruss_server *srv, int64_t *tickets, int32_t *rounds, int32_t max,
+                            int32_t *count) {
+    if (!srv || !count || max < 0 || (max > 0 && !tickets)) return KTRUSS_EINVAL;
+    const int32_t k = int32_t(std::min<size_t>(size_t(max), srv->done_tickets.size()));
+    for (int32_t i = 0; i < k; ++i) {
+        tickets[i] = srv->done_tickets[size_t(i)];
+        if (rounds) rounds[i] = srv->done_rounds[size_t(i)];
+    }
+    srv->done_tickets.erase(srv->done_tickets.begin(), srv->done_tickets.begin() + k);
+    srv->done_rounds.erase(srv->done_rounds.begin(), srv->done_rounds.begin() + k);
+    *count = k;
+    return KTRUSS_OK;
+}
+
+int ktruss_server_status(const ktruss_server *srv, int32_t *queued, int32_t *active,
+                         int64_t *live_edges) {
+    if (!srv) return KTRUSS_EINVAL;
+    if (queued) *queued = int32_t(srv->queue.size());
+    if (active) {
+        int32_t a = 0;
+        for (const Slot &sl : srv->slot) a += sl.used ? 1 : 0;
+        *active = a;
+    }
+    if (live_edges) *live_edges = srv->m_live;
+    return KTRUSS_OK;
+}
+
+}  // extern "C"

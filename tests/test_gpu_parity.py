@@ -19,7 +19,7 @@ import oracle
 pytestmark = pytest.mark.gpu
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
-KERNELS = [0, 1, 2]  # balanced, thread-per-edge, coarse (thread-per-row)
+KERNELS = [0, 1, 2, 3]  # balanced, thread-per-edge, coarse (thread-per-row), auto
 
 
 @pytest.fixture(scope="module")

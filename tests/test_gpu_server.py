@@ -1,0 +1,115 @@
+"""The K-truss request server (continuous batching) on the GPU: requests that
+arrive while others are being peeled are admitted as slots and memory free up,
+their rounds run together, and every request's result equals its solo result
+exactly (tolerance 0: integer path) — outputs and round count."""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def kt():
+    import paper_2009_07929_gb300 as kt
+    kt.lib()
+    return kt
+
+
+def solo(kt, g, K):
+    import torch
+    h = kt.load(torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col).cuda())
+    m_t, s_t = h.run(K)
+    torch.cuda.synchronize()
+    out = (m_t.cpu().numpy(), s_t.cpu().numpy(), h.stats().rounds)
+    h.close()
+    return out
+
+
+def requests_mixed():
+    reqs = [(gg.complete(12), 12), (gg.book(40), 4), (gg.triangle_strip(50), 4),
+            (gg.star(20), 3), (gg.empty(6), 3), (gg.rmat(12, 16, 9), 5),
+            (gg.er(2000, 16000, 7), 3), (gg.rmat(13, 8, seed=2, n_cliques=5, clique_lo=15,
+                                                 clique_hi=40), 20)]
+    reqs += [(gg.gnp_small(15 + s, 0.45, seed=40 + s), 3 + s % 5) for s in range(12)]
+    reqs += gg.serve_config(10, seed=3, m_lo=1e4, m_hi=2e5)
+    return reqs
+
+
+def test_staggered_arrivals_equal_solo_runs(kt):
+    reqs = requests_mixed()
+    srv = kt.Server(max_vertices=1 << 20, max_edges=1 << 22, max_requests=16)
+    results = {}
+    order = {}
+    i = 0
+    while len(results) < len(reqs):
+        # a few new requests arrive between rounds
+        for _ in range(3):
+            if i < len(reqs):
+                g, K = reqs[i]
+                order[srv.submit(g.row_ptr, g.col, K)] = i
+                i += 1
+        for t, r, mask, sup in srv.step():
+            results[order[t]] = (r, mask, sup)
+    srv.close()
+    for k, (g, K) in enumerate(reqs):
+        r, mask, sup = results[k]
+        if g.m == 0:
+            assert r == 0 and mask.size == 0
+            continue
+        want = oracle.ktruss(g.row_ptr, g.col, K) if g.m < 300000 else None
+        sm, ss, sr = solo(kt, g, K)
+        assert np.array_equal(mask, sm) and np.array_equal(sup, ss) and r == sr, k
+        if want is not None:
+            assert np.array_equal(mask, want.mask) and np.array_equal(sup, want.support)
+            assert r == want.rounds
+
+
+def test_admission_waits_for_memory(kt):
+    # capacity for about one mid-size graph at a time: requests queue and are
+    # admitted as earlier ones complete
+    reqs = gg.serve_config(8, seed=11, m_lo=5e4, m_hi=1.5e5)
+    cap = max(g.m for g, _ in reqs) + 10
+    srv = kt.Server(max_vertices=1 << 20, max_edges=cap, max_requests=4)
+    tickets = [srv.submit(g.row_ptr, g.col, K) for g, K in reqs]
+    seen_queue = False
+    results = {}
+    while len(results) < len(reqs):
+        q, a, live = srv.status()
+        seen_queue |= q > 0 and a > 0
+        assert live <= cap
+        for t, r, mask, sup in srv.step():
+            results[t] = (r, mask, sup)
+    srv.close()
+    assert seen_queue
+    for t, (g, K) in zip(tickets, reqs):
+        r, mask, sup = results[t]
+        sm, ss, sr = solo(kt, g, K)
+        assert np.array_equal(mask, sm) and np.array_equal(sup, ss) and r == sr
+
+
+def test_rejects_requests_that_never_fit(kt):
+    srv = kt.Server(max_vertices=100, max_edges=50, max_requests=2)
+    g = gg.complete(12)  # 66 edges > 50
+    with pytest.raises(kt.KtrussError) as ei:
+        srv.submit(g.row_ptr, g.col, 3)
+    assert ei.value.code == kt.EINVAL
+    bad_rp = np.array([0, 1], np.int32)
+    with pytest.raises(kt.KtrussError):
+        srv.submit(bad_rp, np.array([0], np.int32), 3)  # column not above its row
+    srv.close()
+
+
+def test_poisson_driver_completes_everything(kt):
+    reqs = gg.serve_config(12, seed=5, m_lo=1e4, m_hi=1e5)
+    srv = kt.Server(max_vertices=1 << 20, max_edges=1 << 22, max_requests=8)
+    lat, makespan, results = kt.serve_poisson(srv, reqs, rate=200.0, seed=1)
+    srv.close()
+    assert all(r is not None for r in results)
+    assert (lat > 0).all() and makespan > 0
+    for (g, K), (r, mask, sup) in zip(reqs[:4], results[:4]):
+        want = oracle.ktruss(g.row_ptr, g.col, K)
+        assert np.array_equal(mask, want.mask) and np.array_equal(sup, want.support)
+        assert r == want.rounds
