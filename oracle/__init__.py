@@ -55,7 +55,7 @@ def _load():
         lib = ctypes.CDLL(build())
         vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
         lib.oracle_check_csr.argtypes = [i32, i64, vp, vp]
-        lib.oracle_ktruss.argtypes = [i32, i64, vp, vp, i32, vp, vp, vp, vp, i32, vp]
+        lib.oracle_ktruss.argtypes = [i32, i64, vp, vp, i32, vp, vp, vp, vp, i32, vp, vp]
         lib.oracle_truss_decomposition.argtypes = [i32, i64, vp, vp, vp]
         lib.oracle_edge_support.argtypes = [i32, i64, vp, vp, vp, i64, vp, vp]
         lib.oracle_triangles.argtypes = [i32, i64, vp, vp, vp, vp]
@@ -89,6 +89,7 @@ class KtrussResult:
     rounds: int
     removed_per_round: list = field(default_factory=list)
     triangles: int = 0
+    triangles_per_round: list = field(default_factory=list)
 
 
 def check_csr(row_ptr, col) -> int:
@@ -103,15 +104,17 @@ def ktruss(row_ptr, col, K: int) -> KtrussResult:
     sup = np.zeros(max(m, 1), dtype=np.int32)
     cap = 4096
     removed = np.zeros(cap, dtype=np.int64)
+    tris = np.zeros(cap, dtype=np.int64)
     rounds = ctypes.c_int32(0)
     tri = ctypes.c_int64(0)
     rc = _load().oracle_ktruss(n, m, rp.ctypes.data, _ptr(c), K, mask.ctypes.data, sup.ctypes.data,
                                ctypes.addressof(rounds), removed.ctypes.data, cap,
-                               ctypes.addressof(tri))
+                               ctypes.addressof(tri), tris.ctypes.data)
     if rc != 0:
         raise OracleError(rc)
     r = rounds.value
-    return KtrussResult(mask[:m], sup[:m], r, [int(x) for x in removed[:min(r, cap)]], tri.value)
+    return KtrussResult(mask[:m], sup[:m], r, [int(x) for x in removed[:min(r, cap)]], tri.value,
+                        [int(x) for x in tris[:min(r, cap)]])
 
 
 def truss_decomposition(row_ptr, col) -> np.ndarray:

@@ -13,8 +13,10 @@ from __future__ import annotations
 import numpy as np
 
 
-def ktruss_dense(n: int, row_ptr, col, K: int):
-    """Returns (mask[m] uint8, support[m] int64, rounds) in CSR slot order."""
+def ktruss_dense(n: int, row_ptr, col, K: int, tri_out: list | None = None):
+    """Returns (mask[m] uint8, support[m] int64, rounds) in CSR slot order.
+    When tri_out is a list, the triangle count of each round's live graph is
+    appended to it, as trace(B^3) / 6 for the symmetric live adjacency B."""
     row_ptr = np.asarray(row_ptr, dtype=np.int64)
     col = np.asarray(col, dtype=np.int64)
     m = col.shape[0]
@@ -26,6 +28,8 @@ def ktruss_dense(n: int, row_ptr, col, K: int):
     while A.any():
         rounds += 1
         Asym = A + A.T
+        if tri_out is not None:
+            tri_out.append(int(np.trace(Asym @ Asym @ Asym)) // 6)
         S = (Asym @ Asym) * A
         M = (S >= K - 2).astype(np.int64) * A
         unchanged = np.array_equal(M, A)

@@ -70,11 +70,13 @@ int oracle_check_csr(int32_t n, int64_t m, const int32_t *row_ptr, const int32_t
  *
  * Outputs: mask[m] (1 = edge in the K-truss), support[m] (its support inside
  * the K-truss, 0 for removed edges), *rounds, removed_per_round[0..cap) (edges
- * removed by each round, truncated at cap), *triangles (of the final truss).
+ * removed by each round, truncated at cap), *triangles (of the final truss),
+ * triangles_per_round[0..cap) (triangles of the live graph Step 1 of each
+ * round counted; may be NULL).
  */
 int oracle_ktruss(int32_t n, int64_t m, const int32_t *row_ptr, const int32_t *col, int32_t K,
                   uint8_t *mask, int32_t *support, int32_t *rounds, int64_t *removed_per_round,
-                  int32_t cap, int64_t *triangles) {
+                  int32_t cap, int64_t *triangles, int64_t *triangles_per_round) {
     int rc = oracle_check_csr(n, m, row_ptr, col);
     if (rc != OR_OK) return rc;
     if (K < 2) return OR_EINVAL;
@@ -127,6 +129,7 @@ int oracle_ktruss(int32_t n, int64_t m, const int32_t *row_ptr, const int32_t *c
                 }
             }
         }
+        if (triangles_per_round && r - 1 < cap) triangles_per_round[r - 1] = tri;
         /* Step 2: remove all failing edges at once */
         int64_t removed = 0;
         for (int64_t e = 0; e < m; ++e)

@@ -32,9 +32,10 @@ def run(g, K):
 
 def agree_dense(g, K, res=None):
     r = res if res is not None else run(g, K)
-    mb, sb, rb = ktruss_dense(g.n, g.row_ptr, g.col, K)
+    tri = []
+    mb, sb, rb = ktruss_dense(g.n, g.row_ptr, g.col, K, tri_out=tri)
     return (np.array_equal(r.mask, mb) and np.array_equal(r.support.astype(np.int64), sb)
-            and r.rounds == rb)
+            and r.rounds == rb and r.triangles_per_round == tri)
 
 
 # --------------------------------------------------------------- brute force
@@ -73,6 +74,7 @@ def test_complete_graph_is_n_truss_with_support_n_minus_2(n):
     assert r.mask.all() and (r.support == n - 2).all()
     assert r.rounds == 1 and r.removed_per_round == [0]
     assert r.triangles == n * (n - 1) * (n - 2) // 6
+    assert r.triangles_per_round == [r.triangles]
     r2 = run(g, n + 1)
     assert not r2.mask.any() and not r2.support.any()
     assert r2.rounds == 1 and r2.removed_per_round == [n * (n - 1) // 2]
@@ -93,6 +95,7 @@ def test_book_graph(t):
     assert not r4.mask.any()
     # t >= 2: the spine survives round 1 (support t >= 2) and dies in round 2
     assert r4.rounds == (1 if t == 1 else 2)
+    assert r4.triangles_per_round == ([1] if t == 1 else [t, 0])
 
 
 @pytest.mark.parametrize("leaves", [1, 5, 40])
@@ -112,6 +115,7 @@ def test_triangle_strip_round_count(L):
     diagonals = L - 2
     assert r4.rounds == 2
     assert r4.removed_per_round == [diagonals + 2, (L - 1) - 2]
+    assert r4.triangles_per_round == [L - 2, 0]
     assert not r4.mask.any()
 
 
@@ -273,7 +277,7 @@ MUTANTS = {
 def _load_mutant(path):
     lib = ctypes.CDLL(path)
     vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
-    lib.oracle_ktruss.argtypes = [i32, i64, vp, vp, i32, vp, vp, vp, vp, i32, vp]
+    lib.oracle_ktruss.argtypes = [i32, i64, vp, vp, i32, vp, vp, vp, vp, i32, vp, vp]
     lib.oracle_ktruss.restype = ctypes.c_int
     return lib
 
@@ -284,15 +288,17 @@ def _mutant_run(lib, g, K):
     sup = np.zeros(max(m, 1), np.int32)
     rounds = ctypes.c_int32(0)
     removed = np.zeros(256, np.int64)
+    tris = np.zeros(256, np.int64)
     tri = ctypes.c_int64(0)
     rp = np.ascontiguousarray(g.row_ptr)
     col = np.ascontiguousarray(g.col)
     rc = lib.oracle_ktruss(g.n, m, rp.ctypes.data, col.ctypes.data if m else None, K,
                            mask.ctypes.data, sup.ctypes.data, ctypes.addressof(rounds),
-                           removed.ctypes.data, 256, ctypes.addressof(tri))
+                           removed.ctypes.data, 256, ctypes.addressof(tri), tris.ctypes.data)
     assert rc == 0
     return oracle.KtrussResult(mask[:m], sup[:m], rounds.value,
-                               [int(x) for x in removed[:rounds.value]], tri.value)
+                               [int(x) for x in removed[:rounds.value]], tri.value,
+                               [int(x) for x in tris[:rounds.value]])
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
