@@ -45,6 +45,15 @@ WORKLOAD_DESC = {
 }
 CPU_SAMPLE_SCALE = 17  # oracle sample: R-MAT scale 17, same recipe, full K-truss run
 L2_FLUSH_BYTES = 512 << 20
+UPDATE_MODES = {"never": 0, "always": 1, "auto": 2}  # KTRUSS_UPDATE_*
+
+
+_T0 = time.perf_counter()
+
+
+def progress(msg):
+    """One line per phase on stderr (the JSON line alone goes to stdout)."""
+    print(f"[bench {time.perf_counter() - _T0:8.1f}s] {msg}", file=sys.stderr, flush=True)
 
 
 def peaks():
@@ -182,20 +191,24 @@ def measure_batched(kt, gg, count, m_hi, seed=0):
     Batched: the block-diagonal batch preloaded into one handle, then one
     ktruss_run_batch.  Both timed with CUDA events, graphs resident in HBM."""
     import torch
+    progress(f"batched: generating {count} graphs, m up to {m_hi:g}")
     batch = gg.batch_config(count, seed=seed, m_lo=1e3, m_hi=m_hi)
     graphs = [b[0] for b in batch]
     Ks = [b[1] for b in batch]
     edges = sum(g.m for g in graphs)
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
+    progress(f"batched: {edges} edges generated; loading plain handles")
     # plain
     handles = [kt.load(torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col).to(dev))
                for g in graphs]
     outs = [(torch.empty(max(g.m, 1), dtype=torch.uint8, device=dev)[:g.m],
              torch.empty(max(g.m, 1), dtype=torch.int32, device=dev)[:g.m]) for g in graphs]
+    progress("batched: plain warm-up")
     for h, K, o in zip(handles, Ks, outs):
         h.run(K, out=o)
     torch.cuda.synchronize()
+    progress("batched: plain timed")
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for h, K, o in zip(handles, Ks, outs):
@@ -205,6 +218,7 @@ def measure_batched(kt, gg, count, m_hi, seed=0):
     plain_ms = e0.elapsed_time(e1)
     for h in handles:
         h.close()
+    progress(f"batched: plain {plain_ms:.1f} ms; loading the batch")
     # batched
     vo, rp, col, eo = kt.concat_graphs(graphs)
     hb = kt.load_batch(vertex_offsets=vo, row_ptr=torch.from_numpy(rp).to(dev),
@@ -213,6 +227,7 @@ def measure_batched(kt, gg, count, m_hi, seed=0):
     sb = torch.empty(max(int(eo[-1]), 1), dtype=torch.int32, device=dev)[:int(eo[-1])]
     hb.run_batch(Ks, out=(mb, sb))
     torch.cuda.synchronize()
+    progress("batched: batch timed")
     e0.record(stream)
     _, _, rounds = hb.run_batch(Ks, out=(mb, sb))
     e1.record(stream)
@@ -233,8 +248,10 @@ def measure_serving(kt, gg, count, m_hi, seed=0):
     sizes log-uniform in [1e4, m_hi] edges, K uniform in 3..16) through the
     request server: first all requests at once (saturated graphs/s), then
     Poisson arrivals at 70% of that rate (p50/p99 latency, graphs/s)."""
+    progress(f"serving: generating {count} requests, m up to {m_hi:g}")
     reqs = gg.serve_config(count, seed=seed, m_lo=1e4, m_hi=m_hi)
     edges = sum(g.m for g, _ in reqs)
+    progress(f"serving: {edges} edges; warm-up")
     mv = sum(g.n for g, _ in reqs) + 1
     me = min(edges + 1, (1 << 31) - 1)
 
@@ -245,9 +262,11 @@ def measure_serving(kt, gg, count, m_hi, seed=0):
     kt.serve_poisson(warm, reqs[: min(4, count)], rate=None)
     warm.close()
     srv = server()
+    progress("serving: saturated")
     _, sat_s, _ = kt.serve_poisson(srv, reqs, rate=None)
     srv.close()
     sat = count / sat_s
+    progress(f"serving: saturated {sat:.2f} graphs/s; Poisson arrivals")
     srv = server()
     lat, mk, _ = kt.serve_poisson(srv, reqs, rate=0.7 * sat, seed=seed + 1)
     srv.close()
@@ -305,6 +324,9 @@ def main():
     ap.add_argument("--no-kmax", action="store_true", help="skip the K_max sweep timing")
     ap.add_argument("--batch-graphs", type=int, default=4096,
                     help="graphs of the batched-vs-plain measurement (0 = skip)")
+    ap.add_argument("--update", choices=sorted(UPDATE_MODES), default="auto",
+                    help="supports after the first round: decremental update (auto/always) or "
+                         "recomputed every round (never, Alg. 1 as written)")
     ap.add_argument("--serve-requests", type=int, default=64,
                     help="requests of the serving measurement (0 = skip)")
     ap.add_argument("--serve-mmax", type=float, default=1e6,
@@ -336,7 +358,9 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
         pg = dist
     lib = kt.lib()
+    progress(f"loading workload {args.workload}")
     g = gg.cached_workload(args.workload, 0)
+    progress(f"workload n={g.n} m={g.m}; timed steps")
     n, m = g.n, g.m
     dev = torch.device("cuda", local)
     rp_d = torch.from_numpy(g.row_ptr).to(dev)
@@ -344,6 +368,7 @@ def main():
     h = kt.load(rp_d, col_d)
     h.set_kernel({"balanced": kt.KERNEL_BALANCED, "edge": kt.KERNEL_EDGE,
                   "coarse": kt.KERNEL_COARSE, "auto": kt.KERNEL_AUTO}[args.kernel])
+    h.set_update(UPDATE_MODES[args.update])
     mask = torch.empty(m, dtype=torch.uint8, device=dev)
     sup = torch.empty(m, dtype=torch.int32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
@@ -373,9 +398,11 @@ def main():
             launches += st.kernel_launches
             sup_ms += sum(st.ms_support_per_round)
             sup_launches += st.support_launches
-            bytes_alg += sum(algorithmic_bytes(n, lv, mw, tr) for lv, mw, tr in
+            # rounds whose supports came from the decremental update ran no
+            # support kernel
+            bytes_alg += sum(algorithmic_bytes(n, lv, mw, tr) for lv, mw, tr, up in
                              zip(st.live_per_round, st.merge_work_per_round,
-                                 st.triangles_per_round))
+                                 st.triangles_per_round, st.updated_per_round) if not up)
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
     step_ms = [a.elapsed_time(b) for a, b in ev]
@@ -385,6 +412,27 @@ def main():
     torch.cuda.synchronize()
     value = world * m * args.steps / (tot_ms / 1000.0) / 1e6
 
+    # ---- the same run with S recomputed every round (Alg. 1 as written), for
+    # comparison with the decremental update (identical outputs)
+    recompute = None
+    if args.update != "never":
+        h.set_update(kt.UPDATE_NEVER)
+        step()
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            flush.fill_(i)
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        rms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), dev)
+        rst = h.stats()
+        recompute = {"value": round(world * m * args.steps / (rms / 1000.0) / 1e6, 2),
+                     "unit": UNIT, "ms_per_step": round(rms / args.steps, 4),
+                     "support_steps": rst.support_launches, "rounds": rst.rounds}
+        h.set_update(UPDATE_MODES[args.update])
+
+    progress(f"value {value:.1f} Medges/s; e2e")
     # ---- e2e through the C ABI with pinned host buffers
     rp_h = torch.from_numpy(g.row_ptr).pin_memory()
     col_h = torch.from_numpy(g.col).pin_memory()
@@ -423,7 +471,8 @@ def main():
         d1.record(stream)
         torch.cuda.synchronize()
         dec_ms = d0.elapsed_time(d1)
-        dec_steps = h.stats().rounds
+        dec_steps = h.stats().support_launches
+        dec_rounds = h.stats().rounds
 
     if rank != 0:
         if pg:
@@ -457,16 +506,19 @@ def main():
         "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC[args.workload] + f", K={args.K}", "K": args.K,
                    "n": n, "m": m, "rounds": st.rounds, "kernel": args.kernel,
+                   "update": args.update, "support_steps": st.support_launches,
                    "parallelism": f"replicas{world}", "l2": "flushed between steps (512 MiB write)"},
         "e2e": {"value": round(e2e_value, 2), "unit": UNIT,
                 "h2d_bytes_per_step": 4 * (n + 1) + 4 * m, "d2h_bytes_per_step": 5 * m},
         "gpu_launches": launches,
+        "recompute_every_round": recompute,
         "roofline": roofline,
         "clocks": clk.summary(),
         "wall_s_timed": round(wall, 3),
     }
     if kmax is not None:
         out["kmax_sweep"] = {"kmax": kmax, "ms": round(dec_ms, 3), "support_steps": dec_steps,
+                             "rounds": dec_rounds,
                              "Medges_per_s": round(m / (dec_ms / 1e3) / 1e6, 2),
                              "what": "ktruss_decompose: K = 3 .. K_max, each K from the previous truss"}
     if args.batch_graphs > 0:
@@ -474,6 +526,7 @@ def main():
     if args.serve_requests > 0:
         out["serving"] = measure_serving(kt, gg, args.serve_requests, args.serve_mmax)
     if not args.no_cpu_baseline:
+        progress("cpu baseline (oracle)")
         out["cpu_baseline"] = cpu_baseline()
     print(json.dumps(out), flush=True)
     if pg:

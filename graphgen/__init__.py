@@ -268,7 +268,7 @@ def batch_config(count: int, seed: int = 0, m_lo: float = 1e3, m_hi: float = 2e6
     [k_lo, k_hi].  Returns a list of (CSR, K)."""
     import math
     key = stream_key(5, seed, count)
-    out = []
+    specs = []
     for g in range(count):
         u = _unit(key, 4 * g)
         mt = int(round(math.exp(math.log(m_lo) + u * (math.log(m_hi) - math.log(m_lo)))))
@@ -277,12 +277,28 @@ def batch_config(count: int, seed: int = 0, m_lo: float = 1e3, m_hi: float = 2e6
         if g % 2 == 0:
             d = 8.0 + _unit(key, 4 * g + 3) * 56.0
             n = max(int(math.ceil(2 * mt / d)), int(math.ceil(2 * math.sqrt(mt))) + 1)
-            csr = er(n, mt, sub_seed)
+            specs.append((("er", n, mt, sub_seed), K))
         else:
             scale = min(17, max(10, int(math.ceil(math.log2(max(mt, 1) / 16.0)))))
-            csr = rmat(scale, 16, sub_seed)
-        out.append((csr, K))
-    return out
+            specs.append((("rmat", scale, 16, sub_seed), K))
+    return _generate(specs)
+
+
+def _generate(specs):
+    """Builds the graphs of (spec, K) pairs on a thread pool (the C generator
+    releases the GIL); each graph depends only on its own spec."""
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+
+    def one(spec):
+        kind, a, b, sd = spec
+        return er(a, b, sd) if kind == "er" else rmat(a, b, sd)
+
+    _load()
+    workers = max(1, min(len(specs), os.cpu_count() or 1))
+    with ThreadPoolExecutor(max_workers=workers) as ex:
+        graphs = list(ex.map(one, [sp for sp, _ in specs]))
+    return [(g, K) for g, (_, K) in zip(graphs, specs)]
 
 
 def serve_config(count: int, seed: int = 0, m_lo: float = 1e4, m_hi: float = 5e7,
@@ -293,7 +309,7 @@ def serve_config(count: int, seed: int = 0, m_lo: float = 1e4, m_hi: float = 5e7
     of (CSR, K)."""
     import math
     key = stream_key(6, seed, count)
-    out = []
+    specs = []
     for r in range(count):
         u = _unit(key, 5 * r)
         mt = int(round(math.exp(math.log(m_lo) + u * (math.log(m_hi) - math.log(m_lo)))))
@@ -302,9 +318,8 @@ def serve_config(count: int, seed: int = 0, m_lo: float = 1e4, m_hi: float = 5e7
         if _unit(key, 5 * r + 3) < 0.5:
             d = 8.0 + _unit(key, 5 * r + 4) * 56.0
             n = max(int(math.ceil(2 * mt / d)), int(math.ceil(2 * math.sqrt(mt))) + 1)
-            csr = er(n, mt, sub_seed)
+            specs.append((("er", n, mt, sub_seed), K))
         else:
             scale = min(30, max(10, int(math.ceil(math.log2(max(mt, 1) / 16.0)))))
-            csr = rmat(scale, 16, sub_seed)
-        out.append((csr, K))
-    return out
+            specs.append((("rmat", scale, 16, sub_seed), K))
+    return _generate(specs)

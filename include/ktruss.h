@@ -57,22 +57,38 @@ extern "C" {
 #define KTRUSS_KERNEL_COARSE 2   /* one thread per row (coarse-grained Alg. 2), for comparison */
 #define KTRUSS_KERNEL_AUTO 3     /* default: per round, EDGE below 131072 live edges, else BALANCED */
 
+/*
+ * How the supports of the rounds after the first are obtained, selectable
+ * with KTRUSS_OPT_UPDATE.  Alg. 1 recomputes S of the whole live graph each
+ * round.  The decremental update instead subtracts, from every surviving
+ * edge's support, the triangles it loses with the removed edges (each triangle
+ * that contains a removed edge is enumerated once).  Both give the same
+ * supports, masks, removals and round counts; they differ only in time.
+ */
+#define KTRUSS_UPDATE_NEVER 0  /* recompute S every round (Alg. 1 as written) */
+#define KTRUSS_UPDATE_ALWAYS 1 /* decremental update after every round that removes edges */
+#define KTRUSS_UPDATE_AUTO 2   /* default: update when the removed edges that lie in
+                                  triangles are few next to the surviving edges
+                                  (at most one per surviving edge), else recompute */
+
 /* Option keys for ktruss_set_option. */
 #define KTRUSS_OPT_SUPPORT_KERNEL 1 /* KTRUSS_KERNEL_* */
 #define KTRUSS_OPT_TIMING 2         /* 1 = record per-phase CUDA events (default 1) */
+#define KTRUSS_OPT_UPDATE 3         /* KTRUSS_UPDATE_* */
 
 typedef struct ktruss_graph ktruss_graph; /* opaque, library-owned */
 
 /* Statistics of the last ktruss_run on a handle (Alg. 1 bookkeeping). */
 typedef struct {
-    int32_t rounds;            /* executions of the support step (Alg. 1 Step 1) */
+    int32_t rounds;            /* peel rounds (Alg. 1 iterations): supports evaluated on a live graph
+                                  by the support step or the decremental update */
     int64_t edges_in;          /* m */
     int64_t edges_out;         /* edges in the K-truss */
     int64_t triangles_out;     /* triangles of the K-truss */
     int32_t per_round_len;     /* = rounds */
     const int64_t *removed_per_round;   /* [rounds] edges removed by each round */
     const int64_t *live_per_round;      /* [rounds] live edges entering each round */
-    const int64_t *triangles_per_round; /* [rounds] triangles found by each support step */
+    const int64_t *triangles_per_round; /* [rounds] triangles of the live graph of each round */
     const float *ms_support_per_round;  /* [rounds] support kernel time (timing on) */
     const int64_t *merge_work_per_round; /* [rounds] sum over live edges of the lengths of
                                             the two lists each edge task intersects (the
@@ -85,6 +101,10 @@ typedef struct {
     float ms_finalize;         /* final scatter of outputs to input edge order */
     int32_t support_launches;  /* support-kernel launches issued */
     int32_t kernel_launches;   /* all kernels of this library issued by the run */
+    const int32_t *updated_per_round; /* [rounds] 1 where the round's supports came from the
+                                         decremental update of the previous round's (no
+                                         support step ran: its time and merge work are 0) */
+    float ms_update;           /* sum of decremental updates (timing on) */
 } ktruss_stats_t;
 
 /*
@@ -205,6 +225,14 @@ int ktruss_server_take_done(ktruss_server *srv, int64_t *tickets, int32_t *round
 /* Queued requests, active requests, live edges (each pointer may be NULL). */
 int ktruss_server_status(const ktruss_server *srv, int32_t *queued, int32_t *active,
                          int64_t *live_edges);
+
+/* Sets KTRUSS_OPT_UPDATE (KTRUSS_UPDATE_*) for the server's rounds: with the
+ * update, a step takes the supports of requests already active from the
+ * previous step's (updated for the edges it removed) and runs a support step
+ * only over the requests it admits; under AUTO it recomputes everything when
+ * the removed edges that lie in triangles exceed half the live edges.
+ * Results do not depend on it.  KTRUSS_EINVAL for another key or value. */
+int ktruss_server_set_option(ktruss_server *srv, int32_t key, int64_t value);
 
 /* Releases the server and every buffer it holds (NULL is a no-op). */
 void ktruss_server_free(ktruss_server *srv);

@@ -28,7 +28,8 @@ from . import _build
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBUSY = 0, -1, -2, -3, -4, -5
 HOST, DEVICE = 0, 1
 KERNEL_BALANCED, KERNEL_EDGE, KERNEL_COARSE, KERNEL_AUTO = 0, 1, 2, 3
-OPT_SUPPORT_KERNEL, OPT_TIMING = 1, 2
+UPDATE_NEVER, UPDATE_ALWAYS, UPDATE_AUTO = 0, 1, 2
+OPT_SUPPORT_KERNEL, OPT_TIMING, OPT_UPDATE = 1, 2, 3
 
 _lib = None
 
@@ -61,6 +62,8 @@ class _Stats(ctypes.Structure):
         ("ms_finalize", ctypes.c_float),
         ("support_launches", ctypes.c_int32),
         ("kernel_launches", ctypes.c_int32),
+        ("updated_per_round", ctypes.POINTER(ctypes.c_int32)),
+        ("ms_update", ctypes.c_float),
     ]
 
 
@@ -97,9 +100,10 @@ def lib():
         L.ktruss_server_status.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32),
                                            ctypes.POINTER(i64)]
         L.ktruss_server_free.argtypes = [vp]
+        L.ktruss_server_set_option.argtypes = [vp, i32, i64]
         L.ktruss_server_free.restype = None
         for f in (L.ktruss_server_create, L.ktruss_server_submit, L.ktruss_server_step,
-                  L.ktruss_server_take_done, L.ktruss_server_status):
+                  L.ktruss_server_take_done, L.ktruss_server_status, L.ktruss_server_set_option):
             f.restype = ctypes.c_int
         L.ktruss_decompose.restype = ctypes.c_int
         L.ktruss_stats.argtypes = [vp, ctypes.POINTER(_Stats)]
@@ -168,6 +172,8 @@ class Stats:
     ms_finalize: float
     support_launches: int
     kernel_launches: int
+    updated_per_round: list
+    ms_update: float
 
     def __getitem__(self, k):
         return getattr(self, k)
@@ -196,6 +202,11 @@ class Graph:
 
     def set_kernel(self, kernel: int):
         self.set_option(OPT_SUPPORT_KERNEL, kernel)
+
+    def set_update(self, mode: int):
+        """UPDATE_NEVER (recompute S every round, Alg. 1 as written),
+        UPDATE_ALWAYS or UPDATE_AUTO (default): see KTRUSS_OPT_UPDATE."""
+        self.set_option(OPT_UPDATE, mode)
 
     def run(self, K: int, support: bool = True, out=None, stream=None):
         """K-truss on the device (ktruss_run, device outputs on the current
@@ -280,7 +291,8 @@ class Graph:
                      arr(st.triangles_per_round), arr(st.ms_support_per_round, float),
                      arr(st.merge_work_per_round),
                      st.ms_total, st.ms_support, st.ms_balance, st.ms_prune_compact,
-                     st.ms_finalize, st.support_launches, st.kernel_launches)
+                     st.ms_finalize, st.support_launches, st.kernel_launches,
+                     arr(st.updated_per_round), st.ms_update)
 
 
 def load(row_ptr, col, stream=None) -> Graph:
@@ -353,6 +365,11 @@ class Server:
         _check(rc, "ktruss_server_create")
         self._h = h
         self._pending = {}
+
+    def set_update(self, mode: int):
+        """KTRUSS_OPT_UPDATE for the server's rounds (UPDATE_*)."""
+        _check(lib().ktruss_server_set_option(self._h, OPT_UPDATE, mode),
+               "ktruss_server_set_option")
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

@@ -47,19 +47,33 @@ __global__ void batch_validate_kernel(const int32_t *__restrict__ rp, const int3
 
 // Per live edge: keep flag (support >= K_g - 2) and, per graph, the live and
 // removed edge counts of this round (aggregated over warp lanes of one graph).
+// Removed edges with S > 0 are appended to list (when given) at positions
+// taken from *list_count.
 __global__ void __launch_bounds__(256)
 batch_prune_kernel(const int32_t *__restrict__ S, const int32_t *__restrict__ col, int32_t m,
                    const int32_t *__restrict__ gid, const int32_t *__restrict__ thr,
                    uint8_t *__restrict__ keep, int32_t *__restrict__ live_g,
-                   int32_t *__restrict__ removed_g) {
+                   int32_t *__restrict__ removed_g, int32_t *__restrict__ list,
+                   int32_t *list_count) {
     const int lane = threadIdx.x & 31;
     const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     int32_t g = -1;
     bool k = false;
+    int32_t sv = 0;
     if (e < m) {
         g = gid[col[e]];
-        k = S[e] >= thr[g];
+        sv = S[e];
+        k = sv >= thr[g];
         keep[e] = k;
+    }
+    if (list) {
+        const uint32_t b = __ballot_sync(0xffffffffu, e < m && !k && sv > 0);
+        if (b) {
+            int32_t at = 0;
+            if (lane == __ffs(b) - 1) at = atomicAdd(list_count, __popc(b));
+            at = __shfl_sync(0xffffffffu, at, __ffs(b) - 1);
+            if ((b >> lane) & 1u) list[at + __popc(b & ((1u << lane) - 1u))] = int32_t(e);
+        }
     }
     const uint32_t peers = __match_any_sync(0xffffffffu, g);
     const uint32_t drop = __ballot_sync(0xffffffffu, e < m && !k) & peers;
@@ -118,7 +132,8 @@ batch_compact_kernel(const int32_t *__restrict__ col, const int32_t *__restrict_
                      const uint8_t *__restrict__ done, const int32_t *__restrict__ gid, int32_t m,
                      const int32_t *__restrict__ tile_off, int32_t *__restrict__ pos,
                      int32_t *__restrict__ col_out, int32_t *__restrict__ eid_out,
-                     uint8_t *__restrict__ mask_out, int32_t *__restrict__ support_out) {
+                     uint8_t *__restrict__ mask_out, int32_t *__restrict__ support_out,
+                     int32_t *__restrict__ S_out) {
     __shared__ int32_t warp_tot[kWarpsPerTile];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t base = int64_t(blockIdx.x) * kCompactTile + int64_t(w) * kWarpSpan + lane;
@@ -145,6 +160,7 @@ batch_compact_kernel(const int32_t *__restrict__ col, const int32_t *__restrict_
             if ((ballots[j] >> lane) & 1u) {
                 col_out[p] = col[e];
                 eid_out[p] = id;
+                if (S_out) S_out[p] = S[e];
             } else {
                 const bool k = keep[e];
                 mask_out[id] = k ? 1 : 0;
@@ -175,10 +191,11 @@ cudaError_t launch_batch_validate(const int32_t *rp, const int32_t *col, int32_t
 
 cudaError_t launch_batch_keep(const Live &g, const int32_t *S, const int32_t *gid,
                               const int32_t *thr, uint8_t *keep, int32_t *live_g,
-                              int32_t *removed_g, cudaStream_t s, int *launches) {
+                              int32_t *removed_g, cudaStream_t s, int *launches, int32_t *list,
+                              int32_t *list_count) {
     if (g.m == 0) return cudaSuccess;
     batch_prune_kernel<<<(g.m + 255) / 256, 256, 0, s>>>(S, g.col, g.m, gid, thr, keep, live_g,
-                                                         removed_g);
+                                                         removed_g, list, list_count);
     ++*launches;
     return cudaGetLastError();
 }
@@ -187,9 +204,13 @@ cudaError_t launch_batch_prune(const Live &g, const int32_t *S, const int32_t *g
                                const int32_t *thr, uint8_t *keep, int32_t *live_g,
                                int32_t *removed_g, uint8_t *done, int32_t *rounds_g, int32_t G,
                                int32_t *tile_count, int32_t *tile_off, RoundCounters *cnt,
-                               cudaStream_t s, int *launches) {
+                               cudaStream_t s, int *launches, int32_t *list) {
+    if (list) {
+        cudaError_t e = cudaMemsetAsync(&cnt->removed_tri, 0, sizeof(int32_t), s);
+        if (e != cudaSuccess) return e;
+    }
     batch_prune_kernel<<<(g.m + 255) / 256, 256, 0, s>>>(S, g.col, g.m, gid, thr, keep, live_g,
-                                                         removed_g);
+                                                         removed_g, list, &cnt->removed_tri);
     batch_done_kernel<<<(G + 255) / 256, 256, 0, s>>>(G, live_g, removed_g, done, rounds_g);
     const int32_t tiles = compact_tiles(g.m);
     batch_count_kernel<<<tiles, kCompactThreads, 0, s>>>(keep, done, gid, g.col, g.m, tile_count);
@@ -205,12 +226,13 @@ cudaError_t launch_batch_compact(const Live &in, const int32_t *S, const uint8_t
                                  const uint8_t *done, const int32_t *gid, const int32_t *tile_off,
                                  const RoundCounters *cnt, int32_t *pos, int32_t *rp_out,
                                  int32_t *col_out, int32_t *eid_out, uint8_t *mask_out,
-                                 int32_t *support_out, cudaStream_t s, int *launches) {
+                                 int32_t *support_out, cudaStream_t s, int *launches,
+                                 int32_t *S_out) {
     const int32_t tiles = compact_tiles(in.m);
     if (tiles > 0) {
         batch_compact_kernel<<<tiles, kCompactThreads, 0, s>>>(
             in.col, in.eid, S, keep, done, gid, in.m, tile_off, pos, col_out, eid_out, mask_out,
-            support_out);
+            support_out, S_out);
         ++*launches;
     }
     cudaError_t e = cudaGetLastError();

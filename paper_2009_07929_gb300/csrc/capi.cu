@@ -2,19 +2,22 @@
 // Alg. 1 (support step, prune, compaction, convergence test) and statistics.
 //
 // One round on the caller's stream:
-//   memset S = 0                      (Alg. 1 recomputes S from scratch)
-//   support step                      (Alg. 3 edge tasks; balanced or per-edge kernel)
+//   supports S of the live graph: either memset S = 0 + support step (Alg. 3
+//        edge tasks; balanced or per-edge kernel), or already in S from the
+//        decremental update at the end of the previous round
 //   prune count + tile scan           (Step 2: keep iff S >= K-2)
-//   4-byte read of the kept count     (the isUnchanged test, the only host sync)
+//   read of the round counters        (the isUnchanged test, the only host sync)
 //   if nothing was removed: finalize outputs of the survivors, stop
-//   else compact survivors into the other CSR buffer (removed edges' outputs
-//        are written here), continue while any edge is live.
+//   else optionally update S of the survivors (update.cu), then compact the
+//        survivors into the other CSR buffer (removed edges' outputs are
+//        written here), continue while any edge is live.
 #include <cuda_runtime.h>
 
 #include <atomic>
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "ktruss.h"
@@ -67,10 +70,10 @@ struct ktruss_graph {
     int32_t *rp0 = nullptr, *col0 = nullptr;
     // double-buffered live graph
     int32_t *rp[2] = {nullptr, nullptr}, *col[2] = {nullptr, nullptr}, *eid[2] = {nullptr, nullptr};
-    int32_t *S = nullptr, *pos = nullptr;
+    int32_t *S = nullptr, *S2 = nullptr, *pos = nullptr;
     int32_t *tile_count = nullptr, *tile_off = nullptr;
-    kt::RoundCounters *cnt = nullptr;       // device
-    kt::RoundCounters *cnt_host = nullptr;  // pinned mirror
+    kt::RoundCounters *cnt = nullptr;       // device [2]: the round's, the update's
+    kt::RoundCounters *cnt_host = nullptr;  // pinned mirror [2]
     uint8_t *d_mask = nullptr;              // device outputs for host-kind runs
     int32_t *d_sup = nullptr;
     kt::BalancedScratch bs;
@@ -83,14 +86,16 @@ struct ktruss_graph {
     std::atomic<int> busy{0};
     // options
     int support_kernel = KTRUSS_KERNEL_AUTO;
+    int update_mode = KTRUSS_UPDATE_AUTO;
     int timing = 1;
-    // events: [0] run start, [1] run end, then 5 per round
+    // events: [0] run start, [1] run end, then kEventsPerRound per round
     std::vector<cudaEvent_t> events;
     // stats of the last run
     bool has_stats = false;
     ktruss_stats_t st{};
     std::vector<int64_t> removed, live, tris, merge;
     std::vector<float> ms_sup;
+    std::vector<int32_t> upd;
 };
 
 namespace {
@@ -131,17 +136,42 @@ cudaError_t ensure_events(ktruss_graph *g, size_t count) {
 // before the support kernel) dominates there.
 constexpr int32_t kAutoSmallEdges = 1 << 17;
 
+// Per-round events: [0] before the support step, [1] balance done, [2] support
+// done, [3] prune + counter read done, [4] update done, [5] compaction or
+// finalize done.
+constexpr size_t kEventsPerRound = 6;
+
+// After a round that removed edges: take the next round's supports from the
+// decremental update (true) or recompute them (false).  Under AUTO the update
+// is used while the removed edges that lie in triangles are at most as many
+// as the surviving edges; either choice gives the same results.
+bool use_update(int mode, int32_t removed_tri, int32_t kept) {
+    if (mode == KTRUSS_UPDATE_NEVER || kept == 0) return false;
+    if (mode == KTRUSS_UPDATE_ALWAYS) return true;
+    return removed_tri <= kept;
+}
+
+void clear_round_stats(ktruss_graph *g) {
+    g->has_stats = false;
+    g->removed.clear();
+    g->live.clear();
+    g->tris.clear();
+    g->merge.clear();
+    g->ms_sup.clear();
+    g->upd.clear();
+}
+
 // One support step (Alg. 1 Step 1) on the live graph with the handle's kernel
 // choice.  When ev is given (the balanced path), ev[1] is recorded between the
 // balance kernels and the support kernel; otherwise ev[1] is recorded before
 // the support kernel.
-cudaError_t support_step(ktruss_graph *g, const kt::Live &cur, cudaStream_t s, int *launches,
-                         cudaEvent_t *ev) {
+cudaError_t support_step(ktruss_graph *g, const kt::Live &cur, int32_t *S, cudaStream_t s,
+                         int *launches, cudaEvent_t *ev) {
     int k = g->support_kernel;
     if (k == KTRUSS_KERNEL_AUTO) k = cur.m < kAutoSmallEdges ? KTRUSS_KERNEL_EDGE : KTRUSS_KERNEL_BALANCED;
     if (k == KTRUSS_KERNEL_BALANCED) {
         int l = 0;
-        cudaError_t e = kt::launch_support_balanced(cur, g->S, g->cnt, &g->bs, s, &l, ev);
+        cudaError_t e = kt::launch_support_balanced(cur, S, g->cnt, &g->bs, s, &l, ev);
         *launches += l;
         return e;
     }
@@ -150,8 +180,54 @@ cudaError_t support_step(ktruss_graph *g, const kt::Live &cur, cudaStream_t s, i
         if (e != cudaSuccess) return e;
     }
     ++*launches;
-    return k == KTRUSS_KERNEL_EDGE ? kt::launch_support_edge(cur, g->S, g->cnt, s)
-                                   : kt::launch_support_coarse(cur, g->S, g->cnt, s);
+    return k == KTRUSS_KERNEL_EDGE ? kt::launch_support_edge(cur, S, g->cnt, s)
+                                   : kt::launch_support_coarse(cur, S, g->cnt, s);
+}
+
+// Device output buffers of a run: the caller's for device-kind runs, the
+// handle's (allocated on first use) for host-kind runs.
+cudaError_t host_outputs(ktruss_graph *g, int mem_kind, bool want_support, uint8_t **mask_d,
+                         int32_t **sup_d) {
+    if (mem_kind != KTRUSS_HOST || g->m == 0) return cudaSuccess;
+    if (!g->d_mask) {
+        Allocator al;
+        cudaError_t e = al.alloc((void **)&g->d_mask, size_t(g->m));
+        if (e != cudaSuccess) return e;
+        g->owned.push_back(g->d_mask);
+        e = al.alloc((void **)&g->d_sup, size_t(g->m) * 4);
+        if (e != cudaSuccess) return e;
+        g->owned.push_back(g->d_sup);
+    }
+    *mask_d = g->d_mask;
+    *sup_d = want_support ? g->d_sup : nullptr;
+    return cudaSuccess;
+}
+
+void fill_stats(ktruss_graph *g, int32_t rounds, int64_t edges_out, int64_t tri_out,
+                float ms_total, float ms_support, float ms_balance, float ms_prune,
+                float ms_final, float ms_update, int support_launches, int launches) {
+    if (g->ms_sup.size() < size_t(rounds)) g->ms_sup.resize(size_t(rounds), 0.f);
+    g->st = ktruss_stats_t{};
+    g->st.rounds = rounds;
+    g->st.edges_in = g->m;
+    g->st.edges_out = edges_out;
+    g->st.triangles_out = tri_out;
+    g->st.per_round_len = rounds;
+    g->st.removed_per_round = g->removed.data();
+    g->st.live_per_round = g->live.data();
+    g->st.triangles_per_round = g->tris.data();
+    g->st.ms_support_per_round = g->ms_sup.data();
+    g->st.merge_work_per_round = g->merge.data();
+    g->st.ms_total = ms_total;
+    g->st.ms_support = ms_support;
+    g->st.ms_balance = ms_balance;
+    g->st.ms_prune_compact = ms_prune;
+    g->st.ms_finalize = ms_final;
+    g->st.support_launches = support_launches;
+    g->st.kernel_launches = launches;
+    g->st.updated_per_round = g->upd.data();
+    g->st.ms_update = ms_update;
+    g->has_stats = true;
 }
 
 float elapsed(cudaEvent_t a, cudaEvent_t b) {
@@ -212,16 +288,17 @@ static int load_impl(ktruss_graph **out, int32_t n, int64_t m, const int32_t *ro
     bool ok = A((void **)&g->rp0, rpb) && A((void **)&g->col0, eb) && A((void **)&g->rp[0], rpb) &&
               A((void **)&g->rp[1], rpb) && A((void **)&g->col[0], eb) &&
               A((void **)&g->col[1], eb) && A((void **)&g->eid[0], eb) &&
-              A((void **)&g->eid[1], eb) && A((void **)&g->S, eb) &&
+              A((void **)&g->eid[1], eb) && A((void **)&g->S, eb) && A((void **)&g->S2, eb) &&
               A((void **)&g->pos, eb) && A((void **)&g->tile_count, (tiles + 1) * 4) &&
               A((void **)&g->tile_off, (tiles + 1) * 4) &&
-              A((void **)&g->cnt, sizeof(kt::RoundCounters));
+              A((void **)&g->keep, size_t(m) + 1) &&
+              A((void **)&g->cnt, 2 * sizeof(kt::RoundCounters));
     if (ok && G > 0) {
         const size_t gb = (size_t(G) + 1) * 4;
         ok = A((void **)&g->vo, gb) && A((void **)&g->gid, (size_t(n) + 1) * 4) &&
              A((void **)&g->thr, gb) && A((void **)&g->live_g, gb) &&
              A((void **)&g->removed_g, gb) && A((void **)&g->rounds_g, gb) &&
-             A((void **)&g->keep, size_t(m) + 1) && A((void **)&g->done, size_t(G) + 1);
+             A((void **)&g->done, size_t(G) + 1);
         g->G = G;
     }
     g->owned = al.owned;
@@ -234,13 +311,14 @@ static int load_impl(ktruss_graph **out, int32_t n, int64_t m, const int32_t *ro
         return KTRUSS_ENOMEM;
     }
     cudaError_t e = kt::balanced_scratch_alloc(&g->bs, n, m);
-    if (e == cudaSuccess) e = cudaMallocHost((void **)&g->cnt_host, sizeof(kt::RoundCounters));
+    if (e == cudaSuccess)
+        e = cudaMallocHost((void **)&g->cnt_host, 2 * sizeof(kt::RoundCounters));
     if (e == cudaSuccess) e = cudaGetDevice(&g->device);
     const cudaMemcpyKind kind =
         mem_kind == KTRUSS_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     if (e == cudaSuccess) e = cudaMemcpyAsync(g->rp0, row_ptr, rpb, kind, s);
     if (e == cudaSuccess && m > 0) e = cudaMemcpyAsync(g->col0, col, eb, kind, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(g->cnt, 0, sizeof(kt::RoundCounters), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->cnt, 0, 2 * sizeof(kt::RoundCounters), s);
     if (e == cudaSuccess) e = kt::launch_validate(g->rp0, g->col0, n, m, &g->cnt->error, s);
     if (e == cudaSuccess && G > 0) {
         e = cudaMemcpyAsync(g->vo, vertex_offsets, (size_t(G) + 1) * 4, cudaMemcpyHostToDevice, s);
@@ -300,25 +378,10 @@ int ktruss_run_batch(ktruss_graph *g, const int32_t *K, uint8_t *mask_out, int32
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     const int32_t n = g->n;
     const int32_t m = int32_t(g->m);
-    g->has_stats = false;
-    g->removed.clear();
-    g->live.clear();
-    g->tris.clear();
-    g->merge.clear();
-    g->ms_sup.clear();
+    clear_round_stats(g);
     uint8_t *mask_d = mask_out;
     int32_t *sup_d = support_out;
-    if (mem_kind == KTRUSS_HOST && m > 0) {
-        if (!g->d_mask) {
-            Allocator al;
-            KT_CK(al.alloc((void **)&g->d_mask, size_t(m)));
-            g->owned.push_back(g->d_mask);
-            KT_CK(al.alloc((void **)&g->d_sup, size_t(m) * 4));
-            g->owned.push_back(g->d_sup);
-        }
-        mask_d = g->d_mask;
-        sup_d = support_out ? g->d_sup : nullptr;
-    }
+    KT_CK(host_outputs(g, mem_kind, support_out != nullptr, &mask_d, &sup_d));
     // per-graph thresholds K_g - 2 (the staging vector lives until the final
     // synchronisation below)
     std::vector<int32_t> thr(G);
@@ -331,36 +394,56 @@ int ktruss_run_batch(ktruss_graph *g, const int32_t *K, uint8_t *mask_out, int32
         KT_CK(ensure_events(g, 2));
         KT_CK(cudaEventRecord(g->events[0], s));
     }
+    const bool track = g->update_mode != KTRUSS_UPDATE_NEVER;
+    const kt::UpdateScratch us = kt::update_scratch(&g->bs);
     int launches = 0, support_launches = 0, rounds = 0;
     kt::Live cur{g->rp0, g->col0, nullptr, n, m};
     int buf = 0;
+    int32_t *S = g->S, *S_next = g->S2;
+    bool have_s = false;
+    int64_t tri_cur = 0;
     while (cur.m > 0) {
         ++rounds;
-        KT_CK(cudaMemsetAsync(g->S, 0, size_t(cur.m) * 4, s));
-        KT_CK(cudaMemsetAsync(g->cnt, 0, sizeof(kt::RoundCounters), s));
+        const bool updated = have_s;
+        if (!have_s) {
+            KT_CK(cudaMemsetAsync(S, 0, size_t(cur.m) * 4, s));
+            KT_CK(cudaMemsetAsync(g->cnt, 0, sizeof(kt::RoundCounters), s));
+            KT_CK(support_step(g, cur, S, s, &launches, nullptr));
+            ++support_launches;
+        }
         KT_CK(cudaMemsetAsync(g->live_g, 0, size_t(G) * 4, s));
         KT_CK(cudaMemsetAsync(g->removed_g, 0, size_t(G) * 4, s));
-        KT_CK(support_step(g, cur, s, &launches, nullptr));
-        ++support_launches;
-        KT_CK(kt::launch_batch_prune(cur, g->S, g->gid, g->thr, g->keep, g->live_g, g->removed_g,
+        KT_CK(kt::launch_batch_prune(cur, S, g->gid, g->thr, g->keep, g->live_g, g->removed_g,
                                      g->done, g->rounds_g, G, g->tile_count, g->tile_off, g->cnt,
-                                     s, &launches));
-        const int nb = buf;
-        KT_CK(kt::launch_batch_compact(cur, g->S, g->keep, g->done, g->gid, g->tile_off, g->cnt,
-                                       g->pos, g->rp[nb], g->col[nb], g->eid[nb], mask_d, sup_d,
-                                       s, &launches));
-        KT_CK(cudaMemcpyAsync(g->cnt_host, g->cnt, sizeof(kt::RoundCounters),
+                                     s, &launches, track ? us.list : nullptr));
+        KT_CK(cudaMemcpyAsync(g->cnt_host, g->cnt, 2 * sizeof(kt::RoundCounters),
                               cudaMemcpyDeviceToHost, s));
         KT_CK(cudaStreamSynchronize(s));
-        const kt::RoundCounters c = *g->cnt_host;
+        const kt::RoundCounters c = g->cnt_host[0];
         if (c.error) return (c.error & kt::kDevErrTimeout) ? KTRUSS_ETIMEOUT : KTRUSS_ECUDA;
+        tri_cur = updated ? tri_cur - int64_t(g->cnt_host[1].triangles) : int64_t(c.triangles);
         g->live.push_back(cur.m);
-        g->tris.push_back(int64_t(c.triangles));
-        g->merge.push_back(int64_t(c.merge_work));
+        g->tris.push_back(tri_cur);
+        g->merge.push_back(updated ? 0 : int64_t(c.merge_work));
         g->removed.push_back(int64_t(cur.m) - c.kept);
         g->ms_sup.push_back(0.f);
+        g->upd.push_back(updated ? 1 : 0);
+        // kept = edges that stay live (kept edges of unfinished graphs); the
+        // finished graphs leave at this compaction with their outputs
+        const bool upd = track && use_update(g->update_mode, c.removed_tri, c.kept);
+        if (upd) {
+            KT_CK(cudaMemsetAsync(g->cnt + 1, 0, sizeof(kt::RoundCounters), s));
+            KT_CK(kt::launch_support_update(cur, g->keep, us.list, c.removed_tri, S,
+                                            &g->cnt[1].triangles, us, s, &launches));
+        }
+        const int nb = buf;
+        KT_CK(kt::launch_batch_compact(cur, S, g->keep, g->done, g->gid, g->tile_off, g->cnt,
+                                       g->pos, g->rp[nb], g->col[nb], g->eid[nb], mask_d, sup_d,
+                                       s, &launches, upd ? S_next : nullptr));
         cur = kt::Live{g->rp[nb], g->col[nb], g->eid[nb], n, c.kept};
         buf ^= 1;
+        if (upd) std::swap(S, S_next);
+        have_s = upd;
     }
     if (timing) KT_CK(cudaEventRecord(g->events[1], s));
     if (mem_kind == KTRUSS_HOST && m > 0) {
@@ -371,19 +454,8 @@ int ktruss_run_batch(ktruss_graph *g, const int32_t *K, uint8_t *mask_out, int32
     if (rounds_out)
         KT_CK(cudaMemcpyAsync(rounds_out, g->rounds_g, size_t(G) * 4, cudaMemcpyDeviceToHost, s));
     KT_CK(cudaStreamSynchronize(s));
-    g->st = ktruss_stats_t{};
-    g->st.rounds = rounds;
-    g->st.edges_in = g->m;
-    g->st.per_round_len = rounds;
-    g->st.removed_per_round = g->removed.data();
-    g->st.live_per_round = g->live.data();
-    g->st.triangles_per_round = g->tris.data();
-    g->st.ms_support_per_round = g->ms_sup.data();
-    g->st.merge_work_per_round = g->merge.data();
-    g->st.ms_total = timing ? elapsed(g->events[0], g->events[1]) : 0.f;
-    g->st.support_launches = support_launches;
-    g->st.kernel_launches = launches;
-    g->has_stats = true;
+    fill_stats(g, rounds, 0, 0, timing ? elapsed(g->events[0], g->events[1]) : 0.f, 0.f, 0.f,
+               0.f, 0.f, 0.f, support_launches, launches);
     return KTRUSS_OK;
 }
 
@@ -407,6 +479,12 @@ int ktruss_set_option(ktruss_graph *g, int32_t key, int64_t value) {
             if (value != 0 && value != 1) return KTRUSS_EINVAL;
             g->timing = int(value);
             return KTRUSS_OK;
+        case KTRUSS_OPT_UPDATE:
+            if (value != KTRUSS_UPDATE_NEVER && value != KTRUSS_UPDATE_ALWAYS &&
+                value != KTRUSS_UPDATE_AUTO)
+                return KTRUSS_EINVAL;
+            g->update_mode = int(value);
+            return KTRUSS_OK;
         default:
             return KTRUSS_EINVAL;
     }
@@ -422,27 +500,10 @@ int ktruss_run(ktruss_graph *g, int32_t K, uint8_t *mask_out, int32_t *support_o
     const int32_t n = g->n;
     const int32_t m = int32_t(g->m);
     const int32_t thr = K - 2;
-
-    g->has_stats = false;
-    g->removed.clear();
-    g->live.clear();
-    g->tris.clear();
-    g->merge.clear();
-    g->ms_sup.clear();
-
+    clear_round_stats(g);
     uint8_t *mask_d = mask_out;
     int32_t *sup_d = support_out;
-    if (mem_kind == KTRUSS_HOST && m > 0) {
-        if (!g->d_mask) {
-            Allocator al;
-            KT_CK(al.alloc((void **)&g->d_mask, size_t(m)));
-            g->owned.push_back(g->d_mask);
-            KT_CK(al.alloc((void **)&g->d_sup, size_t(m) * 4));
-            g->owned.push_back(g->d_sup);
-        }
-        mask_d = g->d_mask;
-        sup_d = support_out ? g->d_sup : nullptr;
-    }
+    KT_CK(host_outputs(g, mem_kind, support_out != nullptr, &mask_d, &sup_d));
 
     const bool timing = g->timing != 0;
     int launches = 0, support_launches = 0;
@@ -450,53 +511,79 @@ int ktruss_run(ktruss_graph *g, int32_t K, uint8_t *mask_out, int32_t *support_o
         KT_CK(ensure_events(g, 2));
         KT_CK(cudaEventRecord(g->events[0], s));
     }
-
+    const bool track = g->update_mode != KTRUSS_UPDATE_NEVER;
+    const kt::UpdateScratch us = kt::update_scratch(&g->bs);
     kt::Live cur{g->rp0, g->col0, nullptr, n, m};
     int buf = 0;
     int32_t rounds = 0;
-    int64_t tri_final = 0;
-    float ms_balance = 0.f, ms_support = 0.f, ms_prune = 0.f, ms_final = 0.f;
-    std::vector<int> ev_base;
+    int32_t *S = g->S, *S_next = g->S2;
+    bool have_s = false;  // S holds the supports of cur (from the update)
+    int64_t tri_cur = 0, tri_final = 0;
+    std::vector<size_t> ev_base;
+    cudaEvent_t *ev = nullptr;
+    auto mark = [&](size_t k) -> cudaError_t {
+        return timing ? cudaEventRecord(ev[k], s) : cudaSuccess;
+    };
     while (cur.m > 0) {
         ++rounds;
-        size_t base = 2 + size_t(rounds - 1) * 5;
         if (timing) {
-            KT_CK(ensure_events(g, base + 5));
-            ev_base.push_back(int(base));
+            const size_t base = 2 + size_t(rounds - 1) * kEventsPerRound;
+            KT_CK(ensure_events(g, base + kEventsPerRound));
+            ev_base.push_back(base);
+            ev = g->events.data() + base;
         }
-        KT_CK(cudaMemsetAsync(g->S, 0, size_t(cur.m) * 4, s));
-        KT_CK(cudaMemsetAsync(g->cnt, 0, sizeof(kt::RoundCounters), s));
-        if (timing) KT_CK(cudaEventRecord(g->events[base + 0], s));
-        KT_CK(support_step(g, cur, s, &launches, timing ? &g->events[base + 0] : nullptr));
-        ++support_launches;
-        if (timing) KT_CK(cudaEventRecord(g->events[base + 2], s));
-        KT_CK(kt::launch_prune_count(g->S, cur.m, thr, g->tile_count, g->tile_off, g->cnt, s,
-                                     &launches));
-        KT_CK(cudaMemcpyAsync(g->cnt_host, g->cnt, sizeof(kt::RoundCounters),
+        const bool updated = have_s;
+        if (!have_s) {
+            KT_CK(cudaMemsetAsync(S, 0, size_t(cur.m) * 4, s));
+            KT_CK(cudaMemsetAsync(g->cnt, 0, sizeof(kt::RoundCounters), s));
+            KT_CK(mark(0));
+            KT_CK(support_step(g, cur, S, s, &launches, timing ? ev : nullptr));
+            ++support_launches;
+        } else {
+            KT_CK(mark(0));
+            KT_CK(mark(1));
+        }
+        KT_CK(mark(2));
+        KT_CK(kt::launch_prune_count(S, cur.m, thr, g->tile_count, g->tile_off, g->cnt, s,
+                                     &launches, track ? g->keep : nullptr,
+                                     track ? us.list : nullptr));
+        KT_CK(cudaMemcpyAsync(g->cnt_host, g->cnt, 2 * sizeof(kt::RoundCounters),
                               cudaMemcpyDeviceToHost, s));
         KT_CK(cudaStreamSynchronize(s));
-        const kt::RoundCounters c = *g->cnt_host;
+        const kt::RoundCounters c = g->cnt_host[0];
         if (c.error) return (c.error & kt::kDevErrTimeout) ? KTRUSS_ETIMEOUT : KTRUSS_ECUDA;
+        tri_cur = updated ? tri_cur - int64_t(g->cnt_host[1].triangles) : int64_t(c.triangles);
         const int32_t kept = c.kept;
         const int64_t removed = int64_t(cur.m) - kept;
         g->removed.push_back(removed);
         g->live.push_back(cur.m);
-        g->tris.push_back(int64_t(c.triangles));
-        g->merge.push_back(int64_t(c.merge_work));
+        g->tris.push_back(tri_cur);
+        g->merge.push_back(updated ? 0 : int64_t(c.merge_work));
+        g->upd.push_back(updated ? 1 : 0);
+        KT_CK(mark(3));
         if (removed == 0) {
-            if (timing) KT_CK(cudaEventRecord(g->events[base + 3], s));
-            KT_CK(kt::launch_finalize(cur, g->S, mask_d, sup_d, s, &launches));
-            if (timing) KT_CK(cudaEventRecord(g->events[base + 4], s));
-            tri_final = int64_t(c.triangles);
+            KT_CK(mark(4));
+            KT_CK(kt::launch_finalize(cur, S, mask_d, sup_d, s, &launches));
+            KT_CK(mark(5));
+            tri_final = tri_cur;
             break;
         }
-        if (timing) KT_CK(cudaEventRecord(g->events[base + 3], s));
+        const bool upd = track && use_update(g->update_mode, c.removed_tri, kept);
+        if (upd) {
+            KT_CK(cudaMemsetAsync(g->cnt + 1, 0, sizeof(kt::RoundCounters), s));
+            KT_CK(kt::launch_support_update(cur, g->keep, us.list, c.removed_tri, S,
+                                            &g->cnt[1].triangles, us, s, &launches));
+        }
+        KT_CK(mark(4));
         const int nb = buf;
-        KT_CK(kt::launch_compact(cur, g->S, thr, g->tile_off, g->cnt, g->pos, g->rp[nb],
-                                 g->col[nb], g->eid[nb], mask_d, sup_d, s, &launches));
-        if (timing) KT_CK(cudaEventRecord(g->events[base + 4], s));
+        KT_CK(kt::launch_compact(cur, S, thr, g->tile_off, g->cnt, g->pos, g->rp[nb], g->col[nb],
+                                 g->eid[nb], mask_d, sup_d, s, &launches, nullptr, 0,
+                                 upd ? g->keep : nullptr, upd ? S_next : nullptr));
+        KT_CK(mark(5));
         cur = kt::Live{g->rp[nb], g->col[nb], g->eid[nb], n, kept};
         buf ^= 1;
+        if (upd) std::swap(S, S_next);
+        have_s = upd;
         tri_final = 0;
     }
     if (timing) KT_CK(cudaEventRecord(g->events[1], s));
@@ -507,17 +594,20 @@ int ktruss_run(ktruss_graph *g, int32_t K, uint8_t *mask_out, int32_t *support_o
     }
     KT_CK(cudaStreamSynchronize(s));
 
-    float ms_total = 0.f;
+    float ms_total = 0.f, ms_balance = 0.f, ms_support = 0.f, ms_prune = 0.f, ms_final = 0.f,
+          ms_upd = 0.f;
     if (timing) {
         ms_total = elapsed(g->events[0], g->events[1]);
         for (size_t r = 0; r < ev_base.size(); ++r) {
-            const size_t b = size_t(ev_base[r]);
-            const float bal = elapsed(g->events[b + 0], g->events[b + 1]);
-            const float sup = elapsed(g->events[b + 1], g->events[b + 2]);
-            const float pr = elapsed(g->events[b + 2], g->events[b + 3]);
-            const float tail = elapsed(g->events[b + 3], g->events[b + 4]);
+            const cudaEvent_t *e = g->events.data() + ev_base[r];
+            const float bal = elapsed(e[0], e[1]);
+            const float sup = elapsed(e[1], e[2]);
+            const float pr = elapsed(e[2], e[3]);
+            const float up = elapsed(e[3], e[4]);
+            const float tail = elapsed(e[4], e[5]);
             ms_balance += bal;
             ms_support += sup;
+            ms_upd += up;
             g->ms_sup.push_back(sup);
             if (r + 1 == ev_base.size() && g->removed.back() == 0) {
                 ms_prune += pr;
@@ -531,25 +621,8 @@ int ktruss_run(ktruss_graph *g, int32_t K, uint8_t *mask_out, int32_t *support_o
     }
     int64_t edges_out = 0;
     if (rounds > 0 && g->removed.back() == 0) edges_out = g->live.back();
-    g->st = ktruss_stats_t{};
-    g->st.rounds = rounds;
-    g->st.edges_in = g->m;
-    g->st.edges_out = edges_out;
-    g->st.triangles_out = tri_final;
-    g->st.per_round_len = rounds;
-    g->st.removed_per_round = g->removed.data();
-    g->st.live_per_round = g->live.data();
-    g->st.triangles_per_round = g->tris.data();
-    g->st.ms_support_per_round = g->ms_sup.data();
-    g->st.merge_work_per_round = g->merge.data();
-    g->st.ms_total = ms_total;
-    g->st.ms_support = ms_support;
-    g->st.ms_balance = ms_balance;
-    g->st.ms_prune_compact = ms_prune;
-    g->st.ms_finalize = ms_final;
-    g->st.support_launches = support_launches;
-    g->st.kernel_launches = launches;
-    g->has_stats = true;
+    fill_stats(g, rounds, edges_out, tri_final, ms_total, ms_support, ms_balance, ms_prune,
+               ms_final, ms_upd, support_launches, launches);
     return KTRUSS_OK;
 }
 
@@ -562,91 +635,90 @@ int ktruss_decompose(ktruss_graph *g, int32_t *trussness_out, int32_t *kmax_out,
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     const int32_t n = g->n;
     const int32_t m = int32_t(g->m);
-    g->has_stats = false;
-    g->removed.clear();
-    g->live.clear();
-    g->tris.clear();
-    g->merge.clear();
-    g->ms_sup.clear();
+    clear_round_stats(g);
     int32_t *tr_d = trussness_out;
     if (mem_kind == KTRUSS_HOST && m > 0) {
-        if (!g->d_mask) {
-            Allocator al;
-            KT_CK(al.alloc((void **)&g->d_mask, size_t(m)));
-            g->owned.push_back(g->d_mask);
-            KT_CK(al.alloc((void **)&g->d_sup, size_t(m) * 4));
-            g->owned.push_back(g->d_sup);
-        }
-        tr_d = g->d_sup;
+        uint8_t *unused_mask = nullptr;
+        KT_CK(host_outputs(g, mem_kind, true, &unused_mask, &tr_d));
     }
     const bool timing = g->timing != 0;
     if (timing) {
         KT_CK(ensure_events(g, 2));
         KT_CK(cudaEventRecord(g->events[0], s));
     }
+    const bool track = g->update_mode != KTRUSS_UPDATE_NEVER;
+    const kt::UpdateScratch us = kt::update_scratch(&g->bs);
     int launches = 0, support_launches = 0, rounds = 0;
     kt::Live cur{g->rp0, g->col0, nullptr, n, m};
     int buf = 0;
+    int32_t *S = g->S, *S_next = g->S2;
     int32_t K = 3;          // the whole graph is the 2-truss
     bool have_s = false;    // S holds the supports of the current live graph
+    bool fresh = true;      // the current live graph has not been pruned yet
+    bool updated = false;   // ... and its supports came from the update
+    int64_t tri_cur = 0;
     while (cur.m > 0) {
-        if (!have_s) {
+        if (fresh) {
             ++rounds;
-            KT_CK(cudaMemsetAsync(g->S, 0, size_t(cur.m) * 4, s));
-            KT_CK(cudaMemsetAsync(g->cnt, 0, sizeof(kt::RoundCounters), s));
-            KT_CK(support_step(g, cur, s, &launches, nullptr));
-            ++support_launches;
+            if (!have_s) {
+                KT_CK(cudaMemsetAsync(S, 0, size_t(cur.m) * 4, s));
+                KT_CK(cudaMemsetAsync(g->cnt, 0, sizeof(kt::RoundCounters), s));
+                KT_CK(support_step(g, cur, S, s, &launches, nullptr));
+                ++support_launches;
+            }
         }
-        KT_CK(kt::launch_prune_count(g->S, cur.m, K - 2, g->tile_count, g->tile_off, g->cnt, s,
-                                     &launches));
-        KT_CK(cudaMemcpyAsync(g->cnt_host, g->cnt, sizeof(kt::RoundCounters),
+        KT_CK(kt::launch_prune_count(S, cur.m, K - 2, g->tile_count, g->tile_off, g->cnt, s,
+                                     &launches, track ? g->keep : nullptr,
+                                     track ? us.list : nullptr));
+        KT_CK(cudaMemcpyAsync(g->cnt_host, g->cnt, 2 * sizeof(kt::RoundCounters),
                               cudaMemcpyDeviceToHost, s));
         KT_CK(cudaStreamSynchronize(s));
-        const kt::RoundCounters c = *g->cnt_host;
+        const kt::RoundCounters c = g->cnt_host[0];
         if (c.error) return (c.error & kt::kDevErrTimeout) ? KTRUSS_ETIMEOUT : KTRUSS_ECUDA;
         const int32_t kept = c.kept;
-        if (!have_s) {
+        if (fresh) {
+            tri_cur = updated ? tri_cur - int64_t(g->cnt_host[1].triangles) : int64_t(c.triangles);
             g->live.push_back(cur.m);
-            g->tris.push_back(int64_t(c.triangles));
-            g->merge.push_back(int64_t(c.merge_work));
+            g->tris.push_back(tri_cur);
+            g->merge.push_back(updated ? 0 : int64_t(c.merge_work));
             g->removed.push_back(int64_t(cur.m) - kept);
             g->ms_sup.push_back(0.f);
-        } else if (!g->removed.empty()) {
+            g->upd.push_back(updated ? 1 : 0);
+        } else {
             g->removed.back() += int64_t(cur.m) - kept;
         }
+        fresh = false;
+        have_s = true;
         if (kept == cur.m) {
             // cur is the (non-empty) K-truss: the (K+1)-truss lies inside it,
             // and its supports are already in S
             ++K;
-            have_s = true;
             continue;
         }
+        const bool upd = track && use_update(g->update_mode, c.removed_tri, kept);
+        if (upd) {
+            KT_CK(cudaMemsetAsync(g->cnt + 1, 0, sizeof(kt::RoundCounters), s));
+            KT_CK(kt::launch_support_update(cur, g->keep, us.list, c.removed_tri, S,
+                                            &g->cnt[1].triangles, us, s, &launches));
+        }
         const int nb = buf;
-        KT_CK(kt::launch_compact(cur, g->S, K - 2, g->tile_off, g->cnt, g->pos, g->rp[nb],
+        KT_CK(kt::launch_compact(cur, S, K - 2, g->tile_off, g->cnt, g->pos, g->rp[nb],
                                  g->col[nb], g->eid[nb], nullptr, nullptr, s, &launches, tr_d,
-                                 K - 1));
+                                 K - 1, upd ? g->keep : nullptr, upd ? S_next : nullptr));
         cur = kt::Live{g->rp[nb], g->col[nb], g->eid[nb], n, kept};
         buf ^= 1;
-        have_s = false;
+        if (upd) std::swap(S, S_next);
+        have_s = upd;
+        updated = upd;
+        fresh = true;
     }
     if (timing) KT_CK(cudaEventRecord(g->events[1], s));
     if (mem_kind == KTRUSS_HOST && m > 0)
         KT_CK(cudaMemcpyAsync(trussness_out, tr_d, size_t(m) * 4, cudaMemcpyDeviceToHost, s));
     KT_CK(cudaStreamSynchronize(s));
     if (kmax_out) *kmax_out = m == 0 ? 0 : K - 1;
-    g->st = ktruss_stats_t{};
-    g->st.rounds = rounds;
-    g->st.edges_in = g->m;
-    g->st.per_round_len = rounds;
-    g->st.removed_per_round = g->removed.data();
-    g->st.live_per_round = g->live.data();
-    g->st.triangles_per_round = g->tris.data();
-    g->st.ms_support_per_round = g->ms_sup.data();
-    g->st.merge_work_per_round = g->merge.data();
-    g->st.ms_total = timing ? elapsed(g->events[0], g->events[1]) : 0.f;
-    g->st.support_launches = support_launches;
-    g->st.kernel_launches = launches;
-    g->has_stats = true;
+    fill_stats(g, rounds, 0, 0, timing ? elapsed(g->events[0], g->events[1]) : 0.f, 0.f, 0.f,
+               0.f, 0.f, 0.f, support_launches, launches);
     return KTRUSS_OK;
 }
 

@@ -19,17 +19,35 @@ constexpr int kWarpsPerTile = kCompactThreads / 32;
 constexpr int kWarpSpan = kCompactTile / kWarpsPerTile;  // 512 slots per warp
 static_assert(kWarpSpan == 32 * kCompactItemsPerThread, "tile geometry");
 
+// Appends the lanes of `ballot` (this warp) to list at a position taken from
+// *count with one atomic.
+__device__ __forceinline__ void warp_append(uint32_t ballot, int lane, int32_t value,
+                                            int32_t *__restrict__ list, int32_t *count) {
+    if (!ballot) return;
+    int32_t at = 0;
+    if (lane == __ffs(ballot) - 1) at = atomicAdd(count, __popc(ballot));
+    at = __shfl_sync(0xffffffffu, at, __ffs(ballot) - 1);
+    if ((ballot >> lane) & 1u) list[at + __popc(ballot & ((1u << lane) - 1u))] = value;
+}
+
 __global__ void __launch_bounds__(kCompactThreads)
 prune_count_kernel(const int32_t *__restrict__ S, int32_t m, int32_t thr,
-                   int32_t *__restrict__ tile_count) {
+                   int32_t *__restrict__ tile_count, uint8_t *__restrict__ keep,
+                   int32_t *__restrict__ list, RoundCounters *cnt) {
     __shared__ int32_t warp_tot[kWarpsPerTile];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t base = int64_t(blockIdx.x) * kCompactTile + int64_t(w) * kWarpSpan + lane;
     int32_t c = 0;
-#pragma unroll
+#pragma unroll 4
     for (int j = 0; j < kCompactItemsPerThread; ++j) {
         const int64_t e = base + j * 32;
-        c += (e < m && __ldg(S + e) >= thr) ? 1 : 0;
+        const int32_t sv = e < m ? __ldg(S + e) : 0;
+        const bool k = e < m && sv >= thr;
+        c += k ? 1 : 0;
+        if (keep && e < m) keep[e] = k;
+        if (list)
+            warp_append(__ballot_sync(0xffffffffu, e < m && !k && sv > 0), lane, int32_t(e), list,
+                        &cnt->removed_tri);
     }
     c = __reduce_add_sync(0xffffffffu, c);
     if (lane == 0) warp_tot[w] = c;
@@ -86,7 +104,8 @@ compact_kernel(const int32_t *__restrict__ col, const int32_t *__restrict__ eid,
                const int32_t *__restrict__ tile_off, int32_t *__restrict__ pos,
                int32_t *__restrict__ col_out, int32_t *__restrict__ eid_out,
                uint8_t *__restrict__ mask_out, int32_t *__restrict__ support_out,
-               int32_t *__restrict__ level_out, int32_t level) {
+               int32_t *__restrict__ level_out, int32_t level, const uint8_t *__restrict__ keep_in,
+               int32_t *__restrict__ S_out) {
     __shared__ int32_t warp_tot[kWarpsPerTile];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t base = int64_t(blockIdx.x) * kCompactTile + int64_t(w) * kWarpSpan + lane;
@@ -95,7 +114,7 @@ compact_kernel(const int32_t *__restrict__ col, const int32_t *__restrict__ eid,
 #pragma unroll
     for (int j = 0; j < kCompactItemsPerThread; ++j) {
         const int64_t e = base + j * 32;
-        const bool keep = e < m && __ldg(S + e) >= thr;
+        const bool keep = e < m && (keep_in ? keep_in[e] != 0 : __ldg(S + e) >= thr);
         ballots[j] = __ballot_sync(0xffffffffu, keep);
         c += __popc(ballots[j]);
     }
@@ -114,6 +133,7 @@ compact_kernel(const int32_t *__restrict__ col, const int32_t *__restrict__ eid,
             if ((ballots[j] >> lane) & 1u) {
                 col_out[p] = __ldg(col + e);
                 eid_out[p] = id;
+                if (S_out) S_out[p] = S[e];
             } else {
                 if (mask_out) mask_out[id] = 0;
                 if (support_out) support_out[id] = 0;
@@ -147,10 +167,15 @@ __global__ void finalize_kernel(const int32_t *__restrict__ eid, const int32_t *
 
 cudaError_t launch_prune_count(const int32_t *S, int32_t m, int32_t thr, int32_t *tile_count,
                                int32_t *tile_off, RoundCounters *cnt, cudaStream_t s,
-                               int *launches) {
+                               int *launches, uint8_t *keep, int32_t *list) {
     const int32_t tiles = compact_tiles(m);
+    if (list) {
+        cudaError_t e = cudaMemsetAsync(&cnt->removed_tri, 0, sizeof(int32_t), s);
+        if (e != cudaSuccess) return e;
+    }
     if (tiles > 0) {
-        prune_count_kernel<<<tiles, kCompactThreads, 0, s>>>(S, m, thr, tile_count);
+        prune_count_kernel<<<tiles, kCompactThreads, 0, s>>>(S, m, thr, tile_count, keep, list,
+                                                             cnt);
         ++*launches;
     }
     scan_tiles_kernel<<<1, 1024, 0, s>>>(tile_count, tiles, tile_off, cnt);
@@ -162,12 +187,14 @@ cudaError_t launch_compact(const Live &in, const int32_t *S, int32_t thr, const 
                            const RoundCounters *cnt, int32_t *pos, int32_t *rp_out,
                            int32_t *col_out, int32_t *eid_out, uint8_t *mask_out,
                            int32_t *support_out, cudaStream_t s, int *launches,
-                           int32_t *level_out, int32_t level) {
+                           int32_t *level_out, int32_t level, const uint8_t *keep,
+                           int32_t *S_out) {
     const int32_t tiles = compact_tiles(in.m);
     if (tiles > 0) {
         compact_kernel<<<tiles, kCompactThreads, 0, s>>>(in.col, in.eid, S, in.m, thr, tile_off,
                                                          pos, col_out, eid_out, mask_out,
-                                                         support_out, level_out, level);
+                                                         support_out, level_out, level, keep,
+                                                         S_out);
         ++*launches;
     }
     const int64_t rows = int64_t(in.n) + 1;

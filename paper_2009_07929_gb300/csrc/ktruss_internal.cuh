@@ -25,6 +25,8 @@ struct RoundCounters {
     unsigned long long merge_work; // sum over live edges of tail + row-kappa lengths
     int32_t kept;                  // edges with support >= K-2
     int32_t error;                 // nonzero: a kernel detected an inconsistency
+    int32_t removed_tri;           // removed edges with support > 0 (listed by prune)
+    int32_t pad_;
 };
 
 // Device error bits in RoundCounters::error during a run.
@@ -64,6 +66,20 @@ size_t balanced_scratch_bytes(int32_t n, int64_t m);
 cudaError_t balanced_scratch_alloc(BalancedScratch *bs, int32_t n, int64_t m);
 void balanced_scratch_free(BalancedScratch *bs);
 
+// Views of the balanced scratch used by the support update (which never runs
+// at the same time as the balanced support step): lower-neighbour lists of
+// the live graph (lcnt, lrp, lfill over n+1 vertices; lsrc, lslot over m
+// edges), the list of removed edges that lie in triangles (m), and the tile
+// arrays of an int32 scan over n+1 entries.
+struct UpdateScratch {
+    int32_t *lsrc, *lslot, *list, *lcnt, *lrp, *lfill;
+    int32_t *scan_sum, *scan_off, *scan_tot;
+};
+UpdateScratch update_scratch(const BalancedScratch *bs);
+// out[i] = in[0] + ... + in[i-1] for i in [0, count) (int32, count <= cap_n + 1).
+cudaError_t launch_scan_i32(const int32_t *in, int32_t *out, int64_t count,
+                            const UpdateScratch &u, cudaStream_t s, int *launches);
+
 // Balanced support step: work estimate + int64 scan + partition + staged
 // warp-cooperative intersection.  Adds supports into S (zero on entry).
 // Kernel launches issued are added to *launches.  When ev is given, ev[1] is
@@ -71,6 +87,17 @@ void balanced_scratch_free(BalancedScratch *bs);
 cudaError_t launch_support_balanced(const Live &g, int32_t *S, RoundCounters *cnt,
                                     BalancedScratch *bs, cudaStream_t s, int *launches,
                                     cudaEvent_t *ev);
+
+// ---- decremental support update (update.cu) --------------------------------
+// S holds the exact supports of the live graph g and keep[] the decision of
+// this round (0 = removed).  Subtracts from S[e] of every kept edge e the
+// number of triangles of g that contain e and at least one removed edge, and
+// adds the number of those triangles into *destroyed.  list[0..nlist) are the
+// removed edges with S > 0 (removed edges with S = 0 lie in no triangle).
+// Afterwards the kept edges' S are their supports in g minus the removed edges.
+cudaError_t launch_support_update(const Live &g, const uint8_t *keep, const int32_t *list,
+                                  int32_t nlist, int32_t *S, unsigned long long *destroyed,
+                                  const UpdateScratch &u, cudaStream_t s, int *launches);
 
 // ---- prune + compaction + finalize (compact.cu) ---------------------------
 // Tile geometry of the compaction kernels.
@@ -81,22 +108,27 @@ constexpr int kCompactTile = kCompactThreads * kCompactItemsPerThread;
 inline int32_t compact_tiles(int32_t m) { return (m + kCompactTile - 1) / kCompactTile; }
 
 // Counts edges with S >= thr per tile into tile_count[tiles], then scans the
-// tile counts into tile_off[tiles] and writes the total into cnt->kept.
+// tile counts into tile_off[tiles] and writes the total into cnt->kept.  When
+// keep is given, keep[e] = (S[e] >= thr); when list is given, the removed edges
+// with S > 0 are appended to it and counted in cnt->removed_tri (reset here).
 cudaError_t launch_prune_count(const int32_t *S, int32_t m, int32_t thr, int32_t *tile_count,
                                int32_t *tile_off, RoundCounters *cnt, cudaStream_t s,
-                               int *launches);
+                               int *launches, uint8_t *keep = nullptr, int32_t *list = nullptr);
 
 // Scatters kept edges (S >= thr) of `in` into (col_out, eid_out) in order,
 // writes the exclusive kept-prefix of every slot into pos[m_in] (pos[m] =
 // total), writes removed edges' final outputs (mask 0, support 0 at their
 // input edge id) and builds rp_out[i] = pos[rp_in[i]] (cnt->kept for
 // rp_in[i] == m).  mask_out / support_out may be null; when level_out is not
-// null, removed edges also get level_out[id] = level (trussness).
+// null, removed edges also get level_out[id] = level (trussness).  When keep is
+// given it decides which edges stay (instead of S >= thr); when S_out is given,
+// kept edges carry their S into S_out at their new slot.
 cudaError_t launch_compact(const Live &in, const int32_t *S, int32_t thr, const int32_t *tile_off,
                            const RoundCounters *cnt, int32_t *pos, int32_t *rp_out,
                            int32_t *col_out, int32_t *eid_out, uint8_t *mask_out,
                            int32_t *support_out, cudaStream_t s, int *launches,
-                           int32_t *level_out = nullptr, int32_t level = 0);
+                           int32_t *level_out = nullptr, int32_t level = 0,
+                           const uint8_t *keep = nullptr, int32_t *S_out = nullptr);
 
 // Exclusive scan of tile counts by one block (total -> cnt->kept).
 cudaError_t launch_scan_tiles(const int32_t *tile_count, int32_t tiles, int32_t *tile_off,
@@ -116,26 +148,31 @@ cudaError_t launch_batch_validate(const int32_t *rp, const int32_t *col, int32_t
 // Per-graph thresholds: keep flags, per-graph live/removed counts (zero on
 // entry), finished flags and round counters, tile counts and their scan
 // (edges that stay live -> cnt->kept).
+// When list is given, removed edges with S > 0 are appended to it and counted
+// in cnt->removed_tri (reset here).
 cudaError_t launch_batch_prune(const Live &g, const int32_t *S, const int32_t *gid,
                                const int32_t *thr, uint8_t *keep, int32_t *live_g,
                                int32_t *removed_g, uint8_t *done, int32_t *rounds_g, int32_t G,
                                int32_t *tile_count, int32_t *tile_off, RoundCounters *cnt,
-                               cudaStream_t s, int *launches);
+                               cudaStream_t s, int *launches, int32_t *list = nullptr);
 // Keep flags (support >= threshold of the edge's graph) and per-graph live and
 // removed counts (zero on entry) only.
 cudaError_t launch_batch_keep(const Live &g, const int32_t *S, const int32_t *gid,
                               const int32_t *thr, uint8_t *keep, int32_t *live_g,
-                              int32_t *removed_g, cudaStream_t s, int *launches);
+                              int32_t *removed_g, cudaStream_t s, int *launches,
+                              int32_t *list = nullptr, int32_t *list_count = nullptr);
 
 // ---- request server (server_kernels.cu) --------------------------------------
 // Appends a request's device CSR at vertex base nb / edge base mb of the live CSR.
 cudaError_t launch_server_append(const int32_t *rp_in, const int32_t *col_in, int32_t n, int32_t m,
                                  int32_t nb, int32_t mb, int32_t slot, int32_t *rp, int32_t *col,
                                  int32_t *eid, int32_t *gid, cudaStream_t s);
-// Keep flags and per-slot counts (= launch_batch_keep).
+// Keep flags and per-slot counts (= launch_batch_keep); removed edges with
+// S > 0 appended to list when given (count in *list_count, zero on entry).
 cudaError_t launch_server_prune(const Live &cur, const int32_t *S, const int32_t *gid,
                                 const int32_t *thr, uint8_t *keep, int32_t *live_g,
-                                int32_t *removed_g, cudaStream_t s, int *launches);
+                                int32_t *removed_g, cudaStream_t s, int *launches,
+                                int32_t *list = nullptr, int32_t *list_count = nullptr);
 // Finished slots, vertex renumbering (vcnt->kept = surviving vertices),
 // edge compaction (cnt->kept = surviving edges) with outputs of leaving edges
 // through the per-slot pointer tables, new row pointers and slot ids.
@@ -147,14 +184,17 @@ cudaError_t launch_server_round_tail(const Live &cur, const int32_t *S, const ui
                                      int32_t *etile_off, RoundCounters *cnt, int32_t *pos,
                                      int32_t *rp_out, int32_t *col_out, int32_t *eid_out,
                                      int32_t *gid_out, uint8_t *const *mask_ptr,
-                                     int32_t *const *sup_ptr, cudaStream_t s, int *launches);
+                                     int32_t *const *sup_ptr, cudaStream_t s, int *launches,
+                                     int32_t *S_out = nullptr);
 
 // Compaction of the edges that stay live; outputs of the edges that leave.
+// When S_out is given, edges that stay carry their S into S_out.
 cudaError_t launch_batch_compact(const Live &in, const int32_t *S, const uint8_t *keep,
                                  const uint8_t *done, const int32_t *gid, const int32_t *tile_off,
                                  const RoundCounters *cnt, int32_t *pos, int32_t *rp_out,
                                  int32_t *col_out, int32_t *eid_out, uint8_t *mask_out,
-                                 int32_t *support_out, cudaStream_t s, int *launches);
+                                 int32_t *support_out, cudaStream_t s, int *launches,
+                                 int32_t *S_out = nullptr);
 
 // Final outputs of the surviving edges: mask 1 and support S at their input id.
 cudaError_t launch_finalize(const Live &g, const int32_t *S, uint8_t *mask_out,

@@ -7,9 +7,13 @@
 //      the request's own input staging and output buffers (its HBM
 //      footprint); an admitted request's graph is copied to the device and
 //      appended to the live CSR;
-//   2. runs one peel round (support step over every active request, then each
+//   2. runs one peel round (supports of every active request, then each
 //      request pruned with its own threshold) — the rounds of all active
-//      requests are one batched computation on the device;
+//      requests are one batched computation on the device.  Supports come
+//      from one support step over the whole live CSR, or (decremental update,
+//      the default) from the previous step's supports updated for the edges
+//      it removed, plus a support step of each request admitted in this step
+//      over its own CSR;
 //   3. finishes the requests whose round removed nothing or removed every
 //      live edge (their outputs are already in their device buffers), copies
 //      their outputs to the caller's host buffers and frees their memory.
@@ -73,15 +77,15 @@ struct ktruss_server {
     int64_t budget = 0, used = 0;
     cudaStream_t s = nullptr;
     int32_t *rp[2] = {}, *col[2] = {}, *eid[2] = {}, *gid[2] = {};
-    int32_t *S = nullptr, *pos = nullptr, *vmap = nullptr;
+    int32_t *S = nullptr, *S2 = nullptr, *pos = nullptr, *vmap = nullptr;
     uint8_t *keep = nullptr, *fin = nullptr;
     int32_t *thr = nullptr, *live_g = nullptr, *removed_g = nullptr, *rounds_g = nullptr;
     uint8_t **mask_ptr = nullptr;
     int32_t **sup_ptr = nullptr;
     int32_t *etile_count = nullptr, *etile_off = nullptr, *vtile_count = nullptr,
             *vtile_off = nullptr;
-    kt::RoundCounters *cnt = nullptr;       // [0] edges, [1] vertices
-    kt::RoundCounters *cnt_host = nullptr;  // pinned [2]
+    kt::RoundCounters *cnt = nullptr;       // [0] edges, [1] vertices, [2] update
+    kt::RoundCounters *cnt_host = nullptr;  // pinned [3]
     uint8_t *fin_host = nullptr;            // pinned [slots]
     int32_t *rounds_host = nullptr;         // pinned [slots]
     void **ptr_host = nullptr;              // pinned [2 * slots] staging of slot pointers
@@ -91,6 +95,8 @@ struct ktruss_server {
     int cur = 0;
     int32_t n_live = 0;
     int32_t m_live = 0;
+    int32_t m_valid = 0;  // leading live edges whose S was carried from the last step
+    int update_mode = KTRUSS_UPDATE_AUTO;
     int64_t next_ticket = 1;
     std::deque<Request> queue;
     std::vector<Slot> slot;
@@ -136,13 +142,20 @@ size_t request_bytes(int32_t n, int64_t m) {
     return (size_t(n) + 1 + size_t(m)) * 4 + size_t(m) * 5 + 768;
 }
 
-cudaError_t support_step(ktruss_server *v, const kt::Live &g, int *launches) {
+cudaError_t support_step(ktruss_server *v, const kt::Live &g, int32_t *S, int *launches) {
     if (g.m < kAutoSmallEdges) {
         ++*launches;
-        return kt::launch_support_edge(g, v->S, v->cnt, v->s);
+        return kt::launch_support_edge(g, S, v->cnt, v->s);
     }
-    return kt::launch_support_balanced(g, v->S, v->cnt, &v->bs, v->s, launches, nullptr);
+    return kt::launch_support_balanced(g, S, v->cnt, &v->bs, v->s, launches, nullptr);
 }
+
+// A request admitted in the current step: its CSR as staged on the device
+// (request-local vertex ids) and its first slot in the live CSR.
+struct Fresh {
+    const int32_t *rp, *col;
+    int32_t n, m, mb;
+};
 
 }  // namespace
 
@@ -180,6 +193,7 @@ int ktruss_server_create(ktruss_server **out, int32_t max_vertices, int64_t max_
         A((void **)&v->gid[b], nb);
     }
     A((void **)&v->S, eb);
+    A((void **)&v->S2, eb);
     A((void **)&v->pos, eb);
     A((void **)&v->vmap, nb);
     A((void **)&v->keep, size_t(max_edges));
@@ -194,9 +208,9 @@ int ktruss_server_create(ktruss_server **out, int32_t max_vertices, int64_t max_
     A((void **)&v->etile_off, size_t(et) * 4);
     A((void **)&v->vtile_count, size_t(vt) * 4);
     A((void **)&v->vtile_off, size_t(vt) * 4);
-    A((void **)&v->cnt, 2 * sizeof(kt::RoundCounters));
+    A((void **)&v->cnt, 3 * sizeof(kt::RoundCounters));
     if (e == cudaSuccess) e = kt::balanced_scratch_alloc(&v->bs, max_vertices, max_edges);
-    if (e == cudaSuccess) e = cudaMallocHost((void **)&v->cnt_host, 2 * sizeof(kt::RoundCounters));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&v->cnt_host, 3 * sizeof(kt::RoundCounters));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&v->fin_host, size_t(max_requests));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&v->rounds_host, sb);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&v->ptr_host, 2 * size_t(max_requests) * sizeof(void *));
@@ -213,6 +227,16 @@ int ktruss_server_create(ktruss_server **out, int32_t max_vertices, int64_t max_
 }
 
 void ktruss_server_free(ktruss_server *srv) { server_release(srv); }
+
+int ktruss_server_set_option(ktruss_server *srv, int32_t key, int64_t value) {
+    if (!srv) return KTRUSS_EINVAL;
+    if (key != KTRUSS_OPT_UPDATE) return KTRUSS_EINVAL;
+    if (value != KTRUSS_UPDATE_NEVER && value != KTRUSS_UPDATE_ALWAYS &&
+        value != KTRUSS_UPDATE_AUTO)
+        return KTRUSS_EINVAL;
+    srv->update_mode = int(value);
+    return KTRUSS_OK;
+}
 
 int ktruss_server_submit(ktruss_server *srv, int32_t n, int64_t m, const int32_t *row_ptr,
                          const int32_t *col, int32_t K, uint8_t *mask_out, int32_t *support_out,
@@ -244,6 +268,7 @@ int ktruss_server_step(ktruss_server *srv, int32_t *num_done) {
     int launches = 0;
     int32_t finished = 0;
     std::vector<Request> admitted;
+    std::vector<Fresh> fresh;
     // ---- 1. admission, in arrival order
     while (!srv->queue.empty()) {
         Request &r = srv->queue.front();
@@ -292,6 +317,7 @@ int ktruss_server_step(ktruss_server *srv, int32_t *num_done) {
                               cudaMemcpyHostToDevice, s));
         SV_CK(cudaMemcpyAsync(srv->thr + sid, &srv->thr_host[sid], 4, cudaMemcpyHostToDevice, s));
         SV_CK(cudaMemsetAsync(srv->rounds_g + sid, 0, 4, s));
+        fresh.push_back(Fresh{drp, dcol, r.n, int32_t(r.m), srv->m_live});
         srv->n_live += r.n;
         srv->m_live += int32_t(r.m);
         admitted.push_back(std::move(r));
@@ -301,18 +327,49 @@ int ktruss_server_step(ktruss_server *srv, int32_t *num_done) {
     if (srv->m_live > 0) {
         const int c = srv->cur, o = c ^ 1;
         const kt::Live g{srv->rp[c], srv->col[c], srv->eid[c], srv->n_live, srv->m_live};
-        SV_CK(cudaMemsetAsync(srv->S, 0, size_t(g.m) * 4, s));
-        SV_CK(cudaMemsetAsync(srv->cnt, 0, 2 * sizeof(kt::RoundCounters), s));
+        SV_CK(cudaMemsetAsync(srv->cnt, 0, 3 * sizeof(kt::RoundCounters), s));
+        if (srv->m_valid == 0) {
+            // supports of the whole live CSR
+            SV_CK(cudaMemsetAsync(srv->S, 0, size_t(g.m) * 4, s));
+            SV_CK(support_step(srv, g, srv->S, &launches));
+        } else if (srv->m_live > srv->m_valid) {
+            // carried supports for the older requests; a support step per
+            // request admitted now, over its own CSR (its slots follow the
+            // live CSR's in order, so its supports land at its first slot)
+            SV_CK(cudaMemsetAsync(srv->S + srv->m_valid, 0,
+                                  size_t(srv->m_live - srv->m_valid) * 4, s));
+            for (const Fresh &f : fresh) {
+                const kt::Live rg{f.rp, f.col, nullptr, f.n, f.m};
+                SV_CK(support_step(srv, rg, srv->S + f.mb, &launches));
+            }
+        }
         SV_CK(cudaMemsetAsync(srv->live_g, 0, size_t(srv->slots) * 4, s));
         SV_CK(cudaMemsetAsync(srv->removed_g, 0, size_t(srv->slots) * 4, s));
-        SV_CK(support_step(srv, g, &launches));
+        const bool track = srv->update_mode != KTRUSS_UPDATE_NEVER;
+        const kt::UpdateScratch us = kt::update_scratch(&srv->bs);
         SV_CK(kt::launch_server_prune(g, srv->S, srv->gid[c], srv->thr, srv->keep, srv->live_g,
-                                      srv->removed_g, s, &launches));
+                                      srv->removed_g, s, &launches, track ? us.list : nullptr,
+                                      &srv->cnt[0].removed_tri));
+        bool upd = false;
+        if (track) {
+            SV_CK(cudaMemcpyAsync(srv->cnt_host, srv->cnt, sizeof(kt::RoundCounters),
+                                  cudaMemcpyDeviceToHost, s));
+            SV_CK(cudaStreamSynchronize(s));
+            const int32_t nlist = srv->cnt_host[0].removed_tri;
+            // survivors are not known before the round tail: the live edges
+            // that are not listed bound them from above
+            upd = srv->update_mode == KTRUSS_UPDATE_ALWAYS ||
+                  int64_t(nlist) * 2 <= int64_t(srv->m_live);
+            if (upd && nlist > 0)
+                SV_CK(kt::launch_support_update(g, srv->keep, us.list, nlist, srv->S,
+                                                &srv->cnt[2].triangles, us, s, &launches));
+        }
         SV_CK(kt::launch_server_round_tail(
             g, srv->S, srv->keep, srv->live_g, srv->removed_g, srv->fin, srv->rounds_g,
             srv->slots, srv->gid[c], srv->vmap, srv->vtile_count, srv->vtile_off, srv->cnt + 1,
             srv->etile_count, srv->etile_off, srv->cnt, srv->pos, srv->rp[o], srv->col[o],
-            srv->eid[o], srv->gid[o], srv->mask_ptr, srv->sup_ptr, s, &launches));
+            srv->eid[o], srv->gid[o], srv->mask_ptr, srv->sup_ptr, s, &launches,
+            upd ? srv->S2 : nullptr));
         SV_CK(cudaMemcpyAsync(srv->cnt_host, srv->cnt, 2 * sizeof(kt::RoundCounters),
                               cudaMemcpyDeviceToHost, s));
         SV_CK(cudaMemcpyAsync(srv->fin_host, srv->fin, size_t(srv->slots), cudaMemcpyDeviceToHost, s));
@@ -322,6 +379,8 @@ int ktruss_server_step(ktruss_server *srv, int32_t *num_done) {
         srv->m_live = srv->cnt_host[0].kept;
         srv->n_live = srv->cnt_host[1].kept;
         srv->cur = o;
+        if (upd) std::swap(srv->S, srv->S2);
+        srv->m_valid = upd ? srv->m_live : 0;
         ++srv->steps;
         // ---- 3. finished requests: outputs to the caller, memory back
         std::vector<int32_t> fin_slots;

@@ -138,7 +138,8 @@ edge_compact_kernel(const int32_t *__restrict__ col, const int32_t *__restrict__
                     const int32_t *__restrict__ vmap, int32_t m,
                     const int32_t *__restrict__ tile_off, int32_t *__restrict__ pos,
                     int32_t *__restrict__ col_out, int32_t *__restrict__ eid_out,
-                    uint8_t *const *__restrict__ mask_ptr, int32_t *const *__restrict__ sup_ptr) {
+                    uint8_t *const *__restrict__ mask_ptr, int32_t *const *__restrict__ sup_ptr,
+                    int32_t *__restrict__ S_out) {
     __shared__ int32_t warp_tot[kWarpsPerTile];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t base = int64_t(blockIdx.x) * kCompactTile + int64_t(w) * kWarpSpan + lane;
@@ -165,6 +166,7 @@ edge_compact_kernel(const int32_t *__restrict__ col, const int32_t *__restrict__
             if ((ballots[j] >> lane) & 1u) {
                 col_out[p] = vmap[c0];
                 eid_out[p] = eid[e];
+                if (S_out) S_out[p] = S[e];
             } else {
                 const int32_t g = gid[c0];
                 const bool k = keep[e];
@@ -214,7 +216,8 @@ cudaError_t launch_server_round_tail(const Live &cur, const int32_t *S, const ui
                                      int32_t *etile_off, RoundCounters *cnt, int32_t *pos,
                                      int32_t *rp_out, int32_t *col_out, int32_t *eid_out,
                                      int32_t *gid_out, uint8_t *const *mask_ptr,
-                                     int32_t *const *sup_ptr, cudaStream_t s, int *launches) {
+                                     int32_t *const *sup_ptr, cudaStream_t s, int *launches,
+                                     int32_t *S_out) {
     finish_kernel<<<(slots + 255) / 256, 256, 0, s>>>(slots, live_g, removed_g, fin, rounds_g);
     const int32_t vt = compact_tiles(cur.n);
     if (vt > 0) vertex_count_kernel<<<vt, kCompactThreads, 0, s>>>(gid, fin, cur.n, vtile_count);
@@ -230,7 +233,7 @@ cudaError_t launch_server_round_tail(const Live &cur, const int32_t *S, const ui
     if (et > 0)
         edge_compact_kernel<<<et, kCompactThreads, 0, s>>>(cur.col, cur.eid, S, keep, fin, gid,
                                                            vmap, cur.m, etile_off, pos, col_out,
-                                                           eid_out, mask_ptr, sup_ptr);
+                                                           eid_out, mask_ptr, sup_ptr, S_out);
     vertex_rewrite_kernel<<<int((int64_t(cur.n) + 256) / 256), 256, 0, s>>>(
         cur.rp, gid, fin, vmap, pos, cur.n, cur.m, cnt, &vcnt->kept, rp_out, gid_out);
     *launches += 6;
@@ -239,8 +242,10 @@ cudaError_t launch_server_round_tail(const Live &cur, const int32_t *S, const ui
 
 cudaError_t launch_server_prune(const Live &cur, const int32_t *S, const int32_t *gid,
                                 const int32_t *thr, uint8_t *keep, int32_t *live_g,
-                                int32_t *removed_g, cudaStream_t s, int *launches) {
-    return launch_batch_keep(cur, S, gid, thr, keep, live_g, removed_g, s, launches);
+                                int32_t *removed_g, cudaStream_t s, int *launches, int32_t *list,
+                                int32_t *list_count) {
+    return launch_batch_keep(cur, S, gid, thr, keep, live_g, removed_g, s, launches, list,
+                             list_count);
 }
 
 }  // namespace kt

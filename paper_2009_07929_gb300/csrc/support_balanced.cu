@@ -97,6 +97,9 @@ __device__ __forceinline__ Pair operator+(Pair x, Pair y) { return Pair{x.a + y.
 __device__ __forceinline__ long long shfl_up(long long v, int d) {
     return __shfl_up_sync(0xffffffffu, v, d);
 }
+__device__ __forceinline__ int32_t shfl_up(int32_t v, int d) {
+    return __shfl_up_sync(0xffffffffu, v, d);
+}
 __device__ __forceinline__ Pair shfl_up(Pair v, int d) {
     return Pair{__shfl_up_sync(0xffffffffu, v.a, d), __shfl_up_sync(0xffffffffu, v.b, d)};
 }
@@ -1015,7 +1018,44 @@ size_t carve(void *base, int32_t n, int64_t m, Carve *c) {
     return off;
 }
 
+struct I32Load {
+    const int32_t *a;
+    __device__ __forceinline__ int32_t operator()(int64_t i) const { return a[i]; }
+};
+struct I32Store {
+    int32_t *out;
+    __device__ __forceinline__ void operator()(int64_t i, int32_t v) const { out[i] = v; }
+};
+
 }  // namespace
+
+UpdateScratch update_scratch(const BalancedScratch *bs) {
+    Carve c;
+    carve(bs->base, bs->cap_n, bs->cap_m, &c);
+    return UpdateScratch{c.ekey,
+                         c.epst,
+                         c.eitems,
+                         c.rcount,
+                         c.rstart,
+                         c.arank,
+                         reinterpret_cast<int32_t *>(c.rtile_sum),
+                         reinterpret_cast<int32_t *>(c.rtile_off),
+                         reinterpret_cast<int32_t *>(c.rtot)};
+}
+
+cudaError_t launch_scan_i32(const int32_t *in, int32_t *out, int64_t count,
+                            const UpdateScratch &u, cudaStream_t s, int *launches) {
+    if (count <= 0) return cudaSuccess;
+    const int32_t tiles = int32_t((count + kScanTile - 1) / kScanTile);
+    I32Load ld{in};
+    I32Store st{out};
+    scan_reduce_kernel<int32_t, I32Load><<<tiles, kScanThreads, 0, s>>>(ld, count, u.scan_sum);
+    scan_totals_kernel<int32_t><<<1, 1024, 0, s>>>(u.scan_sum, tiles, u.scan_off, u.scan_tot);
+    scan_apply_kernel<int32_t, I32Load, I32Store>
+        <<<tiles, kScanThreads, 0, s>>>(ld, st, count, u.scan_off);
+    *launches += 3;
+    return cudaGetLastError();
+}
 
 size_t balanced_scratch_bytes(int32_t n, int64_t m) {
     Carve c;

@@ -1,0 +1,175 @@
+// Decremental support update between peel rounds.
+//
+// Alg. 1 recomputes S of the whole live graph in every round.  The supports of
+// the next round are also fixed by this round's: after a round removes the
+// edge set R from the live graph G, the support of a surviving edge e in
+// G \ R is its support in G minus the triangles of G that contain e and at
+// least one edge of R.  Only the triangles touching R change anything, and a
+// removed edge with support 0 touches none.  This file computes that
+// difference exactly (integer arithmetic), so the supports, the masks and the
+// round-by-round removals are those of the recomputation.
+//
+// Every triangle {x, y, w} of G that contains a removed edge is handled once,
+// by its removed edge with the smallest slot:
+//   1. lower-neighbour lists of G: for every vertex v, the u < v with (u, v)
+//      in G and the slot of (u, v) (a count, a scan and a scatter over the
+//      edges; the order inside a list does not matter);
+//   2. one warp per removed edge p = (x, y) with S[p] > 0: it walks the full
+//      neighbourhood (upper row and lower list) of the endpoint z of smaller
+//      degree and, for each neighbour w, looks up the edge between w and the
+//      other endpoint o by binary search in the upper row of min(o, w).  A
+//      found edge closes a triangle; the triangle is credited here unless one
+//      of its other two edges is removed and has a smaller slot, and the
+//      credit subtracts one from each of its kept edges.  The walk stops after
+//      S[p] triangles: S[p] is exactly the number of triangles of G on p.
+#include "ktruss_internal.cuh"
+
+namespace kt {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kSlotsPerThread = 16;
+
+// Row of slot e: the largest row whose first slot is <= e.
+__device__ __forceinline__ int32_t row_of(const int32_t *__restrict__ rp, int32_t n, int32_t e) {
+    int32_t lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int32_t mid = lo + ((hi - lo + 1) >> 1);
+        if (__ldg(rp + mid) <= e) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// First slot in the sorted row segment col[lo, hi) whose column is >= b
+// (hi if there is none).
+__device__ __forceinline__ int32_t lower_bound(const int32_t *__restrict__ col, int32_t lo,
+                                               int32_t hi, int32_t b) {
+    while (lo < hi) {
+        const int32_t mid = lo + ((hi - lo) >> 1);
+        if (__ldg(col + mid) < b) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// lcnt[v] += number of edges (u, v) of the live graph.
+__global__ void __launch_bounds__(kThreads)
+lower_count_kernel(const int32_t *__restrict__ col, int32_t m, int32_t *__restrict__ lcnt) {
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < m; e += stride)
+        atomicAdd(lcnt + __ldg(col + e), 1);
+}
+
+// Scatters (u, slot) of every edge (u, v) into the lower list of v.  A thread
+// visits kSlotsPerThread consecutive slots, finding the row of the first by
+// binary search and following rows from there.
+__global__ void __launch_bounds__(kThreads)
+lower_fill_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, int32_t n,
+                  int32_t m, const int32_t *__restrict__ lrp, int32_t *__restrict__ lfill,
+                  int32_t *__restrict__ lsrc, int32_t *__restrict__ lslot) {
+    const int64_t e0 = (int64_t(blockIdx.x) * kThreads + threadIdx.x) * kSlotsPerThread;
+    if (e0 >= m) return;
+    int32_t u = row_of(rp, n, int32_t(e0));
+    int32_t uend = __ldg(rp + u + 1);
+    const int64_t e1 = e0 + kSlotsPerThread < m ? e0 + kSlotsPerThread : m;
+    for (int64_t e = e0; e < e1; ++e) {
+        if (e >= uend) {
+            u = row_of(rp, n, int32_t(e));
+            uend = __ldg(rp + u + 1);
+        }
+        const int32_t v = __ldg(col + e);
+        const int32_t at = __ldg(lrp + v) + atomicAdd(lfill + v, 1);
+        lsrc[at] = u;
+        lslot[at] = int32_t(e);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads)
+update_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, int32_t n,
+              const int32_t *__restrict__ lrp, const int32_t *__restrict__ lsrc,
+              const int32_t *__restrict__ lslot, const uint8_t *__restrict__ keep,
+              const int32_t *__restrict__ list, int32_t nlist, int32_t *__restrict__ S,
+              unsigned long long *__restrict__ destroyed) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    unsigned long long mine = 0;
+    for (int64_t k = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; k < nlist;
+         k += warps) {
+        const int32_t p = __ldg(list + k);
+        const int32_t x = row_of(rp, n, p);
+        const int32_t y = __ldg(col + p);
+        const int32_t xu0 = __ldg(rp + x), xu1 = __ldg(rp + x + 1);
+        const int32_t yu0 = __ldg(rp + y), yu1 = __ldg(rp + y + 1);
+        const int32_t xl0 = __ldg(lrp + x), xl1 = __ldg(lrp + x + 1);
+        const int32_t yl0 = __ldg(lrp + y), yl1 = __ldg(lrp + y + 1);
+        const bool walk_y = (yu1 - yu0) + (yl1 - yl0) < (xu1 - xu0) + (xl1 - xl0);
+        const int32_t o = walk_y ? x : y;
+        const int32_t zu0 = walk_y ? yu0 : xu0, zu1 = walk_y ? yu1 : xu1;
+        const int32_t zl0 = walk_y ? yl0 : xl0, zl1 = walk_y ? yl1 : xl1;
+        const int32_t nu = zu1 - zu0;
+        const int32_t total = nu + (zl1 - zl0);
+        const int32_t need = __ldg(S + p);
+        int32_t found = 0;
+        for (int32_t b = 0; b < total && found < need; b += 32) {
+            const int32_t i = b + lane;
+            bool hit = false;
+            if (i < total) {
+                int32_t w, qz;
+                if (i < nu) {
+                    qz = zu0 + i;
+                    w = __ldg(col + qz);
+                } else {
+                    const int32_t t = zl0 + (i - nu);
+                    w = __ldg(lsrc + t);
+                    qz = __ldg(lslot + t);
+                }
+                if (w != o) {
+                    const int32_t a = w < o ? w : o, c = w < o ? o : w;
+                    const int32_t lo = __ldg(rp + a), hi = __ldg(rp + a + 1);
+                    const int32_t qo = lower_bound(col, lo, hi, c);
+                    if (qo < hi && __ldg(col + qo) == c) {
+                        hit = true;
+                        const bool rz = keep[qz] == 0, ro = keep[qo] == 0;
+                        if (!((rz && qz < p) || (ro && qo < p))) {
+                            if (!rz) atomicSub(S + qz, 1);
+                            if (!ro) atomicSub(S + qo, 1);
+                            ++mine;
+                        }
+                    }
+                }
+            }
+            found += __popc(__ballot_sync(0xffffffffu, hit));
+        }
+    }
+    for (int d = 16; d > 0; d >>= 1) mine += __shfl_down_sync(0xffffffffu, mine, d);
+    if (lane == 0 && mine) atomicAdd(destroyed, mine);
+}
+
+}  // namespace
+
+cudaError_t launch_support_update(const Live &g, const uint8_t *keep, const int32_t *list,
+                                  int32_t nlist, int32_t *S, unsigned long long *destroyed,
+                                  const UpdateScratch &u, cudaStream_t s, int *launches) {
+    if (nlist <= 0 || g.m == 0) return cudaSuccess;
+    const int64_t rows = int64_t(g.n) + 1;
+    cudaError_t e = cudaMemsetAsync(u.lcnt, 0, size_t(rows) * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(u.lfill, 0, size_t(rows) * 4, s);
+    if (e != cudaSuccess) return e;
+    int64_t cblocks = (int64_t(g.m) + kThreads - 1) / kThreads;
+    if (cblocks > 152 * 16) cblocks = 152 * 16;
+    lower_count_kernel<<<int(cblocks), kThreads, 0, s>>>(g.col, g.m, u.lcnt);
+    ++*launches;
+    e = launch_scan_i32(u.lcnt, u.lrp, rows, u, s, launches);
+    if (e != cudaSuccess) return e;
+    const int64_t fblocks =
+        (int64_t(g.m) + int64_t(kThreads) * kSlotsPerThread - 1) / (int64_t(kThreads) * kSlotsPerThread);
+    lower_fill_kernel<<<int(fblocks), kThreads, 0, s>>>(g.rp, g.col, g.n, g.m, u.lrp, u.lfill,
+                                                        u.lsrc, u.lslot);
+    int64_t ublocks = (int64_t(nlist) * 32 + kThreads - 1) / kThreads;
+    if (ublocks > 152 * 32) ublocks = 152 * 32;
+    update_kernel<<<int(ublocks), kThreads, 0, s>>>(g.rp, g.col, g.n, u.lrp, u.lsrc, u.lslot, keep,
+                                                    list, nlist, S, destroyed);
+    *launches += 2;
+    return cudaGetLastError();
+}
+
+}  // namespace kt

@@ -19,13 +19,15 @@ def kt():
     return kt
 
 
-def run_batch(kt, graphs, Ks, kernel=None):
+def run_batch(kt, graphs, Ks, kernel=None, update=None):
     import torch
     vo, rp, col, eo = kt.concat_graphs(graphs)
     h = kt.load_batch(vertex_offsets=vo, row_ptr=torch.from_numpy(rp).cuda(),
                       col=torch.from_numpy(col).cuda())
     if kernel is not None:
         h.set_kernel(kernel)
+    if update is not None:
+        h.set_update(update)
     mask, sup, rounds = h.run_batch(Ks)
     torch.cuda.synchronize()
     mask, sup = mask.cpu().numpy(), sup.cpu().numpy()
@@ -43,10 +45,10 @@ def mixed_small_graphs():
     return gs, Ks
 
 
-@pytest.mark.parametrize("kernel", [0, 1, 3])
-def test_batch_equals_solo_oracle(kt, kernel):
+@pytest.mark.parametrize("kernel,update", [(0, None), (1, None), (3, 0), (3, 1), (3, 2)])
+def test_batch_equals_solo_oracle(kt, kernel, update):
     gs, Ks = mixed_small_graphs()
-    mask, sup, rounds, eo, st = run_batch(kt, gs, Ks, kernel)
+    mask, sup, rounds, eo, st = run_batch(kt, gs, Ks, kernel, update)
     for k, (g, K) in enumerate(zip(gs, Ks)):
         r = oracle.ktruss(g.row_ptr, g.col, K)
         assert np.array_equal(mask[eo[k]:eo[k + 1]], r.mask), k
@@ -55,14 +57,16 @@ def test_batch_equals_solo_oracle(kt, kernel):
     assert st.rounds == max(rounds)
 
 
-def test_batch_config_shape_equals_solo_gpu(kt):
+@pytest.mark.parametrize("update", [0, 1, 2])
+def test_batch_config_shape_equals_solo_gpu(kt, update):
     import torch
     batch = gg.batch_config(48, seed=1, m_lo=1e3, m_hi=6e4)
     gs = [b[0] for b in batch]
     Ks = [b[1] for b in batch]
-    mask, sup, rounds, eo, _ = run_batch(kt, gs, Ks)
+    mask, sup, rounds, eo, _ = run_batch(kt, gs, Ks, update=update)
     for k, (g, K) in enumerate(batch):
         h = kt.load(torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col).cuda())
+        h.set_update(0)  # the solo reference recomputes every round (Alg. 1 as written)
         m_t, s_t = h.run(K)
         torch.cuda.synchronize()
         assert np.array_equal(mask[eo[k]:eo[k + 1]], m_t.cpu().numpy()), k

@@ -20,6 +20,7 @@ pytestmark = pytest.mark.gpu
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 KERNELS = [0, 1, 2, 3]  # balanced, thread-per-edge, coarse (thread-per-row), auto
+UPDATES = [0, 1, 2]     # recompute every round, decremental update always, auto
 
 
 @pytest.fixture(scope="module")
@@ -31,13 +32,15 @@ def kt():
     return kt
 
 
-def gpu_run(kt, g, K, kernel=0, host=False):
+def gpu_run(kt, g, K, kernel=0, host=False, update=None):
     import torch
     if host:
         h = kt.load(g.row_ptr, g.col)
     else:
         h = kt.load(torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col).cuda())
     h.set_kernel(kernel)
+    if update is not None:
+        h.set_update(update)
     if host:
         mask, sup = h.run_host(K)
     else:
@@ -49,16 +52,77 @@ def gpu_run(kt, g, K, kernel=0, host=False):
     return mask, sup, st
 
 
-def assert_parity(kt, g, K, kernel=0, host=False):
+def assert_parity(kt, g, K, kernel=0, host=False, update=None):
     r = oracle.ktruss(g.row_ptr, g.col, K)
-    mask, sup, st = gpu_run(kt, g, K, kernel, host)
-    assert np.array_equal(mask, r.mask), f"mask differs (K={K}, kernel={kernel})"
-    assert np.array_equal(sup, r.support), f"support differs (K={K}, kernel={kernel})"
-    assert st.rounds == r.rounds
-    assert st.removed_per_round == r.removed_per_round
+    mask, sup, st = gpu_run(kt, g, K, kernel, host, update)
+    where = f"(K={K}, kernel={kernel}, update={update})"
+    assert np.array_equal(mask, r.mask), f"mask differs {where}"
+    assert np.array_equal(sup, r.support), f"support differs {where}"
+    assert st.rounds == r.rounds, where
+    assert st.removed_per_round == r.removed_per_round, where
+    assert st.triangles_per_round == r.triangles_per_round, where
     assert st.triangles_out == r.triangles
     assert st.edges_out == int(r.mask.sum())
+    # the first round always runs the support step; under UPDATE_NEVER every
+    # round does, under UPDATE_ALWAYS every later round is an update
+    assert len(st.updated_per_round) == st.rounds
+    if st.rounds:
+        assert st.updated_per_round[0] == 0
+        assert st.support_launches == st.rounds - sum(st.updated_per_round)
+    if update == 0:
+        assert not any(st.updated_per_round)
+    if update == 1:
+        assert all(st.updated_per_round[1:])
     return r, st
+
+
+# ---------------------------------------------- decremental support update
+# Every mode must give the recomputation's results round by round.
+
+@pytest.mark.parametrize("update", UPDATES)
+@pytest.mark.parametrize("seed", range(10))
+def test_er2000_update_modes(kt, seed, update):
+    g = gg.workload("er2000", seed)
+    for K in (3, 4, 5):
+        assert_parity(kt, g, K, 3, update=update)
+
+
+@pytest.mark.parametrize("update", UPDATES)
+def test_update_modes_on_small_and_structured_graphs(kt, update):
+    cases = [gg.empty(0), gg.empty(17), gg.from_edges(2, [(0, 1)]), gg.star(50),
+             gg.triangle_strip(4), gg.triangle_strip(101), gg.complete(3), gg.complete(33),
+             gg.book(7), gg.book(70000)]
+    for g in cases:
+        for K in (2, 3, 4, 5, 34):
+            assert_parity(kt, g, K, 3, update=update)
+    for s in range(60):
+        g = gg.gnp_small(5 + s % 36, (0.1, 0.3, 0.6, 0.9)[s % 4], seed=2000 + s)
+        for K in (3, 4, 6):
+            assert_parity(kt, g, K, 3, update=update)
+
+
+@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("update", [1, 2])
+def test_update_modes_on_deep_cascades_and_long_rows(kt, update, kernel):
+    for g, K, rounds in deep_cascade_graphs():
+        assert_parity(kt, g, K, kernel, update=update)
+    L = 20000
+    edges = [(0, j) for j in range(1, L + 1)]
+    edges += [(j, j + 1) for j in range(1, L)] + [(j, j + 7) for j in range(1, L - 7, 3)]
+    g = gg.from_edges(L + 1, edges)
+    for K in (3, 4, 5):
+        assert_parity(kt, g, K, kernel, update=update)
+
+
+@pytest.mark.parametrize("update", UPDATES)
+def test_update_modes_on_rmat(kt, update):
+    for scale, seed in ((12, 0), (14, 1), (16, 2)):
+        g = gg.rmat(scale, 16, seed)
+        for K in (3, 4, 7, 12):
+            assert_parity(kt, g, K, 3, update=update)
+    g = gg.rmat(14, 8, seed=3, n_cliques=8, clique_lo=20, clique_hi=60)
+    for K in (5, 12, 30):
+        assert_parity(kt, g, K, 3, update=update)
 
 
 # ---------------------------------------------------------------- config 1
@@ -203,8 +267,8 @@ def test_support_optional(kt):
 
 # ------------------------------------------------ truss decomposition
 
-@pytest.mark.parametrize("kernel", KERNELS)
-def test_decomposition_matches_oracle(kt, kernel):
+@pytest.mark.parametrize("kernel,update", [(k, None) for k in KERNELS] + [(3, u) for u in UPDATES])
+def test_decomposition_matches_oracle(kt, kernel, update):
     import torch
     graphs = [gg.complete(9), gg.book(20), gg.star(10), gg.triangle_strip(30), gg.empty(5),
               gg.er(2000, 16000, 1), gg.rmat(12, 16, 0),
@@ -212,6 +276,8 @@ def test_decomposition_matches_oracle(kt, kernel):
     for g in graphs:
         h = kt.load(torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col).cuda())
         h.set_kernel(kernel)
+        if update is not None:
+            h.set_update(update)
         tr, kmax = h.decompose()
         torch.cuda.synchronize()
         got = tr.cpu().numpy()

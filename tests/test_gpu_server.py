@@ -21,6 +21,7 @@ def kt():
 def solo(kt, g, K):
     import torch
     h = kt.load(torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col).cuda())
+    h.set_update(0)  # recompute every round: Alg. 1 as written
     m_t, s_t = h.run(K)
     torch.cuda.synchronize()
     out = (m_t.cpu().numpy(), s_t.cpu().numpy(), h.stats().rounds)
@@ -38,9 +39,11 @@ def requests_mixed():
     return reqs
 
 
-def test_staggered_arrivals_equal_solo_runs(kt):
+@pytest.mark.parametrize("update", [0, 1, 2])
+def test_staggered_arrivals_equal_solo_runs(kt, update):
     reqs = requests_mixed()
     srv = kt.Server(max_vertices=1 << 20, max_edges=1 << 22, max_requests=16)
+    srv.set_update(update)
     results = {}
     order = {}
     i = 0
