@@ -24,7 +24,7 @@ __global__ void graph_of_vertex_kernel(const int32_t *__restrict__ vo, int32_t G
     if (v >= n) return;
     int32_t lo = 0, hi = G - 1;
     while (lo < hi) {
-        const int32_t mid = (lo + hi + 1) >> 1;
+        const int32_t mid = lo + ((hi - lo + 1) >> 1);
         if (vo[mid] <= v) lo = mid; else hi = mid - 1;
     }
     gid[v] = lo;

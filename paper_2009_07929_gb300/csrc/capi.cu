@@ -14,6 +14,8 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <chrono>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -150,6 +152,56 @@ bool use_update(int mode, int32_t removed_tri, int32_t kept) {
     if (mode == KTRUSS_UPDATE_ALWAYS) return true;
     return removed_tri <= kept;
 }
+
+// KTRUSS_TRACE=1: one line per round on stderr (which call, round, live and
+// removed edges, update or support step, host time since the call began).
+struct Trace {
+    bool on = false;
+    const char *what;
+    std::chrono::steady_clock::time_point t0;
+    explicit Trace(const char *w) : what(w), t0(std::chrono::steady_clock::now()) {
+        const char *v = std::getenv("KTRUSS_TRACE");
+        on = v && *v && *v != '0';
+    }
+    void round(int32_t r, int64_t live, int64_t removed, int32_t removed_tri,
+               bool updated) const {
+        if (!on) return;
+        const double ms = std::chrono::duration<double, std::milli>(
+                              std::chrono::steady_clock::now() - t0).count();
+        std::fprintf(stderr,
+                     "[ktruss %s] round %d live %lld removed %lld (in triangles %d) %s %.3f ms\n",
+                     what, int(r), (long long)live, (long long)removed, int(removed_tri),
+                     updated ? "update" : "support", ms);
+    }
+};
+
+}  // namespace
+
+namespace kt {
+namespace {
+const auto g_trace_t0 = std::chrono::steady_clock::now();
+int trace_level() {
+    static const int level = [] {
+        const char *v = std::getenv("KTRUSS_TRACE");
+        return v && *v ? std::atoi(v) : 0;
+    }();
+    return level;
+}
+}  // namespace
+
+bool trace_phases() { return trace_level() >= 2; }
+
+void trace_phase(cudaStream_t s, const char *name) {
+    if (!trace_phases()) return;
+    const cudaError_t e = cudaStreamSynchronize(s);
+    const double ms = std::chrono::duration<double, std::milli>(
+                          std::chrono::steady_clock::now() - g_trace_t0).count();
+    std::fprintf(stderr, "[ktruss phase] %s done (%s) at %.3f ms\n", name,
+                 e == cudaSuccess ? "ok" : cudaGetErrorString(e), ms);
+}
+}  // namespace kt
+
+namespace {
 
 void clear_round_stats(ktruss_graph *g) {
     g->has_stats = false;
@@ -396,6 +448,7 @@ int ktruss_run_batch(ktruss_graph *g, const int32_t *K, uint8_t *mask_out, int32
     }
     const bool track = g->update_mode != KTRUSS_UPDATE_NEVER;
     const kt::UpdateScratch us = kt::update_scratch(&g->bs);
+    const Trace trace("run_batch");
     int launches = 0, support_launches = 0, rounds = 0;
     kt::Live cur{g->rp0, g->col0, nullptr, n, m};
     int buf = 0;
@@ -410,6 +463,7 @@ int ktruss_run_batch(ktruss_graph *g, const int32_t *K, uint8_t *mask_out, int32
             KT_CK(cudaMemsetAsync(g->cnt, 0, sizeof(kt::RoundCounters), s));
             KT_CK(support_step(g, cur, S, s, &launches, nullptr));
             ++support_launches;
+            kt::trace_phase(s, "batch support step");
         }
         KT_CK(cudaMemsetAsync(g->live_g, 0, size_t(G) * 4, s));
         KT_CK(cudaMemsetAsync(g->removed_g, 0, size_t(G) * 4, s));
@@ -428,6 +482,7 @@ int ktruss_run_batch(ktruss_graph *g, const int32_t *K, uint8_t *mask_out, int32
         g->removed.push_back(int64_t(cur.m) - c.kept);
         g->ms_sup.push_back(0.f);
         g->upd.push_back(updated ? 1 : 0);
+        trace.round(rounds, cur.m, int64_t(cur.m) - c.kept, c.removed_tri, updated);
         // kept = edges that stay live (kept edges of unfinished graphs); the
         // finished graphs leave at this compaction with their outputs
         const bool upd = track && use_update(g->update_mode, c.removed_tri, c.kept);
@@ -513,6 +568,7 @@ int ktruss_run(ktruss_graph *g, int32_t K, uint8_t *mask_out, int32_t *support_o
     }
     const bool track = g->update_mode != KTRUSS_UPDATE_NEVER;
     const kt::UpdateScratch us = kt::update_scratch(&g->bs);
+    const Trace trace("run");
     kt::Live cur{g->rp0, g->col0, nullptr, n, m};
     int buf = 0;
     int32_t rounds = 0;
@@ -560,6 +616,7 @@ int ktruss_run(ktruss_graph *g, int32_t K, uint8_t *mask_out, int32_t *support_o
         g->tris.push_back(tri_cur);
         g->merge.push_back(updated ? 0 : int64_t(c.merge_work));
         g->upd.push_back(updated ? 1 : 0);
+        trace.round(rounds, cur.m, removed, c.removed_tri, updated);
         KT_CK(mark(3));
         if (removed == 0) {
             KT_CK(mark(4));
@@ -648,6 +705,7 @@ int ktruss_decompose(ktruss_graph *g, int32_t *trussness_out, int32_t *kmax_out,
     }
     const bool track = g->update_mode != KTRUSS_UPDATE_NEVER;
     const kt::UpdateScratch us = kt::update_scratch(&g->bs);
+    const Trace trace("decompose");
     int launches = 0, support_launches = 0, rounds = 0;
     kt::Live cur{g->rp0, g->col0, nullptr, n, m};
     int buf = 0;
@@ -687,6 +745,7 @@ int ktruss_decompose(ktruss_graph *g, int32_t *trussness_out, int32_t *kmax_out,
         } else {
             g->removed.back() += int64_t(cur.m) - kept;
         }
+        trace.round(rounds, cur.m, int64_t(cur.m) - kept, c.removed_tri, updated);
         fresh = false;
         have_s = true;
         if (kept == cur.m) {

@@ -35,6 +35,12 @@ constexpr int32_t kDevErrInternal = 2;  // an internal consistency check failed
 
 constexpr int kWarp = 32;
 
+// KTRUSS_TRACE=2 (or more): the launchers synchronise the stream after each
+// phase and print its name and the time since the process loaded the library
+// on stderr (a debugging aid; off by default).
+bool trace_phases();
+void trace_phase(cudaStream_t s, const char *name);
+
 // ---- validation (validate.cu) ----------------------------------------------
 // Sets *err to a nonzero bit mask if (rp, col) violates the upper-triangular
 // CSR contract.  *err must be zero on entry.

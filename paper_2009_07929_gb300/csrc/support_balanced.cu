@@ -33,6 +33,7 @@
 // All credits are integer additions, so the result does not depend on the
 // order in which CTAs, warps or the counting sort place the work.
 #include <cstdint>
+#include <cstdio>
 
 #include "ktruss_internal.cuh"
 
@@ -80,7 +81,22 @@ constexpr int32_t kIntMax = 0x7fffffff;
 // sched[] words
 constexpr int kSchedChunkNext = 0;
 constexpr int kSchedNChunks = 1;
+constexpr int kSchedGiveUp = 2;  // first loop that gave up (code), then two values
 constexpr int kSchedWords = 8;
+
+// Loops whose bound comes from the hash tables' load factor end after at most
+// a region's bucket count of steps; one that would exceed it records where it
+// gave up in sched[kSchedGiveUp..+2] (first one wins), sets the round's error
+// bit and stops.  None is expected to trigger.
+constexpr int32_t kGiveUpInsert = 1, kGiveUpFind = 2, kGiveUpProbe = 3, kGiveUpStage = 4;
+__device__ __noinline__ void give_up(int32_t *sched, int32_t *err, int32_t code, int32_t v1,
+                                     int32_t v2) {
+    if (atomicCAS(sched + kSchedGiveUp, 0, code) == 0) {
+        sched[kSchedGiveUp + 1] = v1;
+        sched[kSchedGiveUp + 2] = v2;
+    }
+    atomicOr(err, kDevErrInternal);
+}
 
 struct ChunkPlan {
     long long chunk;  // items per chunk
@@ -178,12 +194,12 @@ __device__ __forceinline__ uint32_t match_bytes(uint32_t word, uint32_t fp4) {
     return ~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x | 0x7F7F7F7Fu);
 }
 
-__device__ __forceinline__ void table_insert(uint32_t *fpw, uint16_t *slots, int32_t bbase, int lb,
+__device__ __forceinline__ bool table_insert(uint32_t *fpw, uint16_t *slots, int32_t bbase, int lb,
                                              int32_t w, int32_t s) {
     const uint32_t bm = (1u << lb) - 1u;
     const uint32_t fp = fingerprint(w);
     uint32_t b = (uint32_t(w) * kHashMul) >> (32 - lb);
-    for (;;) {
+    for (uint32_t step = 0; step <= bm; ++step) {
         const int32_t at = bbase + int32_t(b);
         uint32_t old = fpw[at];
         while ((old >> 24) == 0) {  // bucket not full: take its first free entry
@@ -191,22 +207,24 @@ __device__ __forceinline__ void table_insert(uint32_t *fpw, uint16_t *slots, int
             const uint32_t prev = atomicCAS(fpw + at, old, old | (fp << (8 * j)));
             if (prev == old) {
                 slots[4 * at + j] = uint16_t(s);
-                return;
+                return true;
             }
             old = prev;
         }
         b = (b + 1) & bm;
     }
+    return false;  // region full: cannot happen at load factor <= 1/4
 }
 
-// Local slot of column w in the region (bbase, lb), or -1.
+// Local slot of column w in the region (bbase, lb), -1 if absent, -2 if the
+// walk visited every bucket of the region (cannot happen at load factor <= 1/4).
 __device__ __forceinline__ int32_t table_find(const uint32_t *fpw, const uint16_t *slots,
                                               const int32_t *vals, int32_t bbase, int lb,
                                               int32_t w) {
     const uint32_t bm = (1u << lb) - 1u;
     const uint32_t fp4 = fingerprint(w) * 0x01010101u;
     uint32_t b = (uint32_t(w) * kHashMul) >> (32 - lb);
-    for (;;) {
+    for (uint32_t step = 0;;) {
         const int32_t at = bbase + int32_t(b);
         const uint32_t word = fpw[at];
         for (uint32_t mm = match_bytes(word, fp4); mm; mm &= mm - 1u) {
@@ -214,6 +232,7 @@ __device__ __forceinline__ int32_t table_find(const uint32_t *fpw, const uint16_
             if (vals[sl] == w) return sl;
         }
         if ((word >> 24) == 0) return -1;
+        if (++step > bm) return -2;
         b = (b + 1) & bm;
     }
 }
@@ -508,6 +527,7 @@ struct SupportArgs {
     int32_t *sched;
     int32_t *S;
     unsigned long long *tri;
+    int32_t *err;
 };
 
 // Exclusive block-wide prefix of v (kThreads threads); *total = sum.
@@ -591,7 +611,7 @@ __device__ __forceinline__ void probe_range(const SupportArgs &A, SupportSmem &s
                     const int32_t w = wv[u];
                     const uint32_t fp4 = fingerprint(w) * 0x01010101u;
                     uint32_t b = (uint32_t(w) * kHashMul) >> sh;
-                    for (;;) {
+                    for (uint32_t step = 0;;) {
                         const int32_t at = bb + int32_t(b);
                         const uint32_t word = sm.fpw[at];
                         int32_t q = -1;
@@ -609,12 +629,17 @@ __device__ __forceinline__ void probe_range(const SupportArgs &A, SupportSmem &s
                             break;
                         }
                         if ((word >> 24) == 0) break;
+                        if (++step > bm) {  // only reached past a full bucket
+                            give_up(A.sched, A.err, kGiveUpProbe, key, lb);
+                            break;
+                        }
                         b = (b + 1) & bm;
                     }
                 }
             }
             for (; i < nwin; ++i) {
                 const int32_t q = table_find(sm.fpw, sm.slots, sm.vals, bb, lb, __ldg(src + 32 * i));
+                if (q == -2) give_up(A.sched, A.err, kGiveUpFind, key, lb);
                 if (q >= 0) {
                     atomicAdd(&sm.cnt[q], 1);
                     atomicAdd(dst + 32 * i, 1);
@@ -660,6 +685,7 @@ __device__ __forceinline__ void probe_range(const SupportArgs &A, SupportSmem &s
                 const int32_t bb = single ? 0 : sm.tbase[key];
                 const int lb = single ? piece_lb : sm.tlb[key];
                 const int32_t q = table_find(sm.fpw, sm.slots, sm.vals, bb, lb, wv[u]);
+                if (q == -2) give_up(A.sched, A.err, kGiveUpFind, key, lb);
                 if (q >= 0) {
                     atomicAdd(&sm.cnt[q], 1);
                     atomicAdd(A.S + x[u], 1);
@@ -744,7 +770,7 @@ __device__ void long_row(const SupportArgs &A, SupportSmem &sm, int32_t rbase, i
             for (int k = 0; k < kWarps; ++k) mv = min(mv, sm.ctl[16 + k]);
             int32_t lo = 0, hi = npieces - 1;  // last piece starting at a column <= mv
             while (lo < hi) {
-                const int32_t mid = (lo + hi + 1) >> 1;
+                const int32_t mid = lo + ((hi - lo + 1) >> 1);
                 if (__ldg(A.col + rbase + mid * kCap) <= mv) lo = mid; else hi = mid - 1;
             }
             sm.ctl[2] = mv == kIntMax ? npieces : lo;
@@ -764,17 +790,19 @@ __device__ void long_row(const SupportArgs &A, SupportSmem &sm, int32_t rbase, i
                 int32_t lo = k, hi = ke;
                 if (k < ke && __ldg(A.col + k) < vhi) {
                     lo = k + 1;
-                    for (int32_t step = 1;; step <<= 1) {
-                        const int32_t t = k + step;
+                    // positions stay below 2^31 (int32 slots); the step and
+                    // the probe position are kept in 64 bits so neither wraps
+                    for (int64_t step = 1;; step <<= 1) {
+                        const int64_t t = int64_t(k) + step;
                         if (t >= ke) break;
                         if (__ldg(A.col + t) >= vhi) {
-                            hi = t;
+                            hi = int32_t(t);
                             break;
                         }
-                        lo = t + 1;
+                        lo = int32_t(t) + 1;
                     }
                     while (lo < hi) {
-                        const int32_t mid = (lo + hi) >> 1;
+                        const int32_t mid = lo + ((hi - lo) >> 1);
                         if (__ldg(A.col + mid) < vhi) lo = mid + 1; else hi = mid;
                     }
                 } else {
@@ -793,7 +821,8 @@ __device__ void long_row(const SupportArgs &A, SupportSmem &sm, int32_t rbase, i
                 for (int q = tid; q < plen; q += kThreads) {
                     const int32_t w = __ldg(A.col + ps + q);
                     sm.vals[q] = w;
-                    table_insert(sm.fpw, sm.slots, 0, lb, w, q);
+                    if (!table_insert(sm.fpw, sm.slots, 0, lb, w, q))
+                        give_up(A.sched, A.err, kGiveUpInsert, plen, lb);
                 }
                 __syncthreads();
                 probe_runs(A, sm, nruns, items, true, lb);
@@ -910,7 +939,8 @@ support_kernel(SupportArgs A) {
                 const int32_t g = sm.gbase[lr] + (k - sm.loc[lr]);
                 const int32_t w = __ldg(A.col + g);
                 sm.vals[k] = w;
-                table_insert(sm.fpw, sm.slots, sm.tbase[lr], sm.tlb[lr], w, k);
+                if (!table_insert(sm.fpw, sm.slots, sm.tbase[lr], sm.tlb[lr], w, k))
+                    give_up(A.sched, A.err, kGiveUpInsert, lr, sm.tlb[lr]);
             }
             __syncthreads();
             const int32_t sLo = max(pa, sm.segb[0]);
@@ -944,6 +974,10 @@ support_kernel(SupportArgs A) {
                 }
             }
             __syncthreads();
+            if (nr == 0) {  // no row fits a stage: cannot happen for rows <= kCap
+                if (tid == 0) give_up(A.sched, A.err, kGiveUpStage, a, L);
+                break;
+            }
             a += nr;
         }
     }
@@ -1097,6 +1131,7 @@ cudaError_t launch_support_balanced(const Live &g, int32_t *S, RoundCounters *cn
                             (kEdgeThreads * kEdgesPerThread));
     classify_kernel<<<eblocks, kEdgeThreads, 0, s>>>(g.rp, g.col, n, m, c.ekey, c.epst, c.eitems,
                                                      c.rcount, &cnt->merge_work);
+    trace_phase(s, "classify");
     // row scan: segment starts and active-row ranks (row n has count 0, so the
     // entries at n are the totals)
     const int64_t rows = int64_t(n) + 1;
@@ -1109,9 +1144,11 @@ cudaError_t launch_support_balanced(const Live &g, int32_t *S, RoundCounters *cn
         <<<rtiles, kScanThreads, 0, s>>>(rl, rs, rows, c.rtile_off);
     active_rows_kernel<<<int((rows + 255) / 256), 256, 0, s>>>(c.rcount, c.rstart, c.arank,
                                                                c.rtot, n, c.arow, c.aseg);
+    trace_phase(s, "row scan + active rows");
     scatter_kernel<<<(m + 255) / 256, 256, 0, s>>>(c.ekey, c.epst, c.eitems, m, c.rstart,
                                                    c.arank, c.rcount, c.seg, c.pst, c.sitems,
                                                    c.sact);
+    trace_phase(s, "scatter");
     // item scan over the segments (at most m of them; entries past nseg are 0)
     const int32_t itiles = int32_t((int64_t(m) + kScanTile - 1) / kScanTile);
     ItemLoad il{c.sitems, c.rtot};
@@ -1120,8 +1157,19 @@ cudaError_t launch_support_balanced(const Live &g, int32_t *S, RoundCounters *cn
     scan_totals_kernel<long long><<<1, 1024, 0, s>>>(c.itile_sum, itiles, c.itile_off, c.itot);
     scan_apply_kernel<long long, ItemLoad, ItemStore>
         <<<itiles, kScanThreads, 0, s>>>(il, is, m, c.itile_off);
+    trace_phase(s, "item scan");
     plan_kernel<<<1, 1, 0, s>>>(c.itot, c.rtot, c.wp, c.plan, c.sched, g_support_blocks);
     partition_kernel<<<64, 256, 0, s>>>(c.wp, c.aseg, c.plan, c.sched, c.bound);
+    trace_phase(s, "plan + partition");
+    if (trace_phases()) {
+        ChunkPlan hp{};
+        int32_t hs[kSchedWords] = {};
+        if (cudaMemcpy(&hp, c.plan, sizeof(hp), cudaMemcpyDeviceToHost) == cudaSuccess &&
+            cudaMemcpy(hs, c.sched, sizeof(hs), cudaMemcpyDeviceToHost) == cudaSuccess)
+            std::fprintf(stderr, "[ktruss phase] plan: items %lld chunk %lld chunks %d segments %d "
+                         "active rows %d (n %d m %d)\n", hp.total, hp.chunk, hs[kSchedNChunks],
+                         hp.nseg, hp.nact, n, m);
+    }
     *launches += 12;
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -1130,8 +1178,16 @@ cudaError_t launch_support_balanced(const Live &g, int32_t *S, RoundCounters *cn
         if (e != cudaSuccess) return e;
     }
     SupportArgs A{g.rp, g.col, c.seg, c.pst, c.sact, c.wp, c.arow, c.aseg, c.plan, c.bound,
-                  c.sched, S, &cnt->triangles};
+                  c.sched, S, &cnt->triangles, &cnt->error};
     support_kernel<<<g_support_blocks, kThreads, sizeof(SupportSmem), s>>>(A);
+    trace_phase(s, "support_kernel");
+    if (trace_phases()) {
+        int32_t hs[kSchedWords] = {};
+        if (cudaMemcpy(hs, c.sched, sizeof(hs), cudaMemcpyDeviceToHost) == cudaSuccess &&
+            hs[kSchedGiveUp] != 0)
+            std::fprintf(stderr, "[ktruss phase] support_kernel gave up: code %d values %d %d\n",
+                         hs[kSchedGiveUp], hs[kSchedGiveUp + 1], hs[kSchedGiveUp + 2]);
+    }
     *launches += 1;
     return cudaGetLastError();
 }

@@ -15,7 +15,7 @@ __device__ __forceinline__ int32_t row_of_slot(const int32_t *__restrict__ rp, i
                                                int32_t e) {
     int32_t lo = 0, hi = n - 1;
     while (lo < hi) {
-        const int32_t mid = (lo + hi + 1) >> 1;
+        const int32_t mid = lo + ((hi - lo + 1) >> 1);
         if (__ldg(rp + mid) <= e) lo = mid; else hi = mid - 1;
     }
     return lo;

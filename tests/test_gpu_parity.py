@@ -212,6 +212,41 @@ def test_small_rmat_with_long_rows(kt, kernel):
             assert_parity(kt, g, K, kernel)
 
 
+def test_long_rows_at_slots_above_2_30(kt):
+    """Disjoint copies of a graph whose hub row is longer than a shared-memory
+    stage, enough of them that the last copies' rows sit at CSR slots above
+    2^30: searches over slot positions must not wrap there.  Every copy must
+    get the oracle's result for one copy."""
+    import torch
+    L = 20000
+    edges = [(0, j) for j in range(1, L + 1)]
+    edges += [(j, j + 1) for j in range(1, L)] + [(j, j + 7) for j in range(1, L - 7, 3)]
+    base = gg.from_edges(L + 1, edges)
+    copies = (1 << 30) // base.m + 64
+    n, m = base.n * copies, base.m * copies
+    assert m > (1 << 30) + 32 * base.m and n < (1 << 31)
+    rp = np.empty(n + 1, np.int32)
+    rp[:n] = (base.row_ptr[:-1][None, :] +
+              (np.arange(copies, dtype=np.int32) * np.int32(base.m))[:, None]).ravel()
+    rp[n] = m
+    col = (base.col[None, :] + (np.arange(copies, dtype=np.int32) * np.int32(base.n))[:, None]).ravel()
+    h = kt.load(torch.from_numpy(rp).cuda(), torch.from_numpy(col).cuda())
+    del rp, col
+    h.set_kernel(0)  # balanced: long rows go through the piecewise path
+    for K in (3, 4):
+        r = oracle.ktruss(base.row_ptr, base.col, K)
+        m_t, s_t = h.run(K)
+        torch.cuda.synchronize()
+        mask = m_t.cpu().numpy().reshape(copies, base.m)
+        sup = s_t.cpu().numpy().reshape(copies, base.m)
+        del m_t, s_t
+        assert (mask == r.mask[None, :]).all(), K
+        assert (sup == r.support[None, :]).all(), K
+        assert h.stats().rounds == r.rounds
+    h.close()
+    torch.cuda.empty_cache()
+
+
 def test_rmat_with_cliques_kmax(kt):
     g = gg.rmat(14, 8, seed=3, n_cliques=8, clique_lo=20, clique_hi=60)
     tr = oracle.truss_decomposition(g.row_ptr, g.col)
