@@ -69,7 +69,8 @@ extern "C" {
 #define KTRUSS_UPDATE_ALWAYS 1 /* decremental update after every round that removes edges */
 #define KTRUSS_UPDATE_AUTO 2   /* default: update when the removed edges that lie in
                                   triangles are few next to the surviving edges
-                                  (at most one per surviving edge), else recompute */
+                                  (at most one per four surviving edges), else
+                                  recompute */
 
 /* Option keys for ktruss_set_option. */
 #define KTRUSS_OPT_SUPPORT_KERNEL 1 /* KTRUSS_KERNEL_* */
@@ -230,7 +231,7 @@ int ktruss_server_status(const ktruss_server *srv, int32_t *queued, int32_t *act
  * update, a step takes the supports of requests already active from the
  * previous step's (updated for the edges it removed) and runs a support step
  * only over the requests it admits; under AUTO it recomputes everything when
- * the removed edges that lie in triangles exceed half the live edges.
+ * the removed edges that lie in triangles exceed a quarter of the live edges.
  * Results do not depend on it.  KTRUSS_EINVAL for another key or value. */
 int ktruss_server_set_option(ktruss_server *srv, int32_t key, int64_t value);
 

@@ -45,26 +45,31 @@ __global__ void batch_validate_kernel(const int32_t *__restrict__ rp, const int3
     }
 }
 
-// Per live edge: keep flag (support >= K_g - 2) and, per graph, the live and
-// removed edge counts of this round (aggregated over warp lanes of one graph).
-// Removed edges with S > 0 are appended to list (when given) at positions
-// taken from *list_count.
+// Per live edge: keep flag (support >= K_g - 2) and, per graph, whether this
+// round kept some edge (kept_g) and removed some edge (removed_g): both are
+// 0/1 flags set with a plain store after a read shows them unset.  Removed
+// edges with S > 0 are appended to list (when given) at positions taken from
+// *list_count; when ldeg is given, each removed edge (u, v) subtracts one from
+// ldeg[v].
 __global__ void __launch_bounds__(256)
 batch_prune_kernel(const int32_t *__restrict__ S, const int32_t *__restrict__ col, int32_t m,
                    const int32_t *__restrict__ gid, const int32_t *__restrict__ thr,
-                   uint8_t *__restrict__ keep, int32_t *__restrict__ live_g,
-                   int32_t *__restrict__ removed_g, int32_t *__restrict__ list,
-                   int32_t *list_count) {
+                   uint8_t *__restrict__ keep, int32_t *kept_g, int32_t *removed_g,
+                   int32_t *__restrict__ list, int32_t *list_count, int32_t *__restrict__ ldeg) {
     const int lane = threadIdx.x & 31;
     const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     int32_t g = -1;
     bool k = false;
     int32_t sv = 0;
     if (e < m) {
-        g = gid[col[e]];
+        const int32_t v = col[e];
+        g = gid[v];
         sv = S[e];
         k = sv >= thr[g];
         keep[e] = k;
+        int32_t *f = k ? kept_g + g : removed_g + g;
+        if (*f == 0) *f = 1;  // a stale 0 only repeats the store
+        if (!k && ldeg) atomicSub(ldeg + v, 1);
     }
     if (list) {
         const uint32_t b = __ballot_sync(0xffffffffu, e < m && !k && sv > 0);
@@ -75,22 +80,16 @@ batch_prune_kernel(const int32_t *__restrict__ S, const int32_t *__restrict__ co
             if ((b >> lane) & 1u) list[at + __popc(b & ((1u << lane) - 1u))] = int32_t(e);
         }
     }
-    const uint32_t peers = __match_any_sync(0xffffffffu, g);
-    const uint32_t drop = __ballot_sync(0xffffffffu, e < m && !k) & peers;
-    if (g >= 0 && lane == __ffs(peers) - 1) {
-        atomicAdd(live_g + g, __popc(peers));
-        if (drop) atomicAdd(removed_g + g, __popc(drop));
-    }
 }
 
 // Per graph: count the round for graphs that had live edges; a graph with
 // live edges and no removal is finished.
-__global__ void batch_done_kernel(int32_t G, const int32_t *__restrict__ live_g,
+__global__ void batch_done_kernel(int32_t G, const int32_t *__restrict__ kept_g,
                                   const int32_t *__restrict__ removed_g,
                                   uint8_t *__restrict__ done, int32_t *__restrict__ rounds_g) {
     const int32_t g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= G) return;
-    if (live_g[g] > 0) {
+    if (kept_g[g] || removed_g[g]) {
         rounds_g[g] += 1;
         done[g] = removed_g[g] == 0;
     }
@@ -190,28 +189,28 @@ cudaError_t launch_batch_validate(const int32_t *rp, const int32_t *col, int32_t
 }
 
 cudaError_t launch_batch_keep(const Live &g, const int32_t *S, const int32_t *gid,
-                              const int32_t *thr, uint8_t *keep, int32_t *live_g,
+                              const int32_t *thr, uint8_t *keep, int32_t *kept_g,
                               int32_t *removed_g, cudaStream_t s, int *launches, int32_t *list,
                               int32_t *list_count) {
     if (g.m == 0) return cudaSuccess;
-    batch_prune_kernel<<<(g.m + 255) / 256, 256, 0, s>>>(S, g.col, g.m, gid, thr, keep, live_g,
-                                                         removed_g, list, list_count);
+    batch_prune_kernel<<<(g.m + 255) / 256, 256, 0, s>>>(S, g.col, g.m, gid, thr, keep, kept_g,
+                                                         removed_g, list, list_count, nullptr);
     ++*launches;
     return cudaGetLastError();
 }
 
 cudaError_t launch_batch_prune(const Live &g, const int32_t *S, const int32_t *gid,
-                               const int32_t *thr, uint8_t *keep, int32_t *live_g,
+                               const int32_t *thr, uint8_t *keep, int32_t *kept_g,
                                int32_t *removed_g, uint8_t *done, int32_t *rounds_g, int32_t G,
                                int32_t *tile_count, int32_t *tile_off, RoundCounters *cnt,
-                               cudaStream_t s, int *launches, int32_t *list) {
+                               cudaStream_t s, int *launches, int32_t *list, int32_t *ldeg) {
     if (list) {
         cudaError_t e = cudaMemsetAsync(&cnt->removed_tri, 0, sizeof(int32_t), s);
         if (e != cudaSuccess) return e;
     }
-    batch_prune_kernel<<<(g.m + 255) / 256, 256, 0, s>>>(S, g.col, g.m, gid, thr, keep, live_g,
-                                                         removed_g, list, &cnt->removed_tri);
-    batch_done_kernel<<<(G + 255) / 256, 256, 0, s>>>(G, live_g, removed_g, done, rounds_g);
+    batch_prune_kernel<<<(g.m + 255) / 256, 256, 0, s>>>(S, g.col, g.m, gid, thr, keep, kept_g,
+                                                         removed_g, list, &cnt->removed_tri, ldeg);
+    batch_done_kernel<<<(G + 255) / 256, 256, 0, s>>>(G, kept_g, removed_g, done, rounds_g);
     const int32_t tiles = compact_tiles(g.m);
     batch_count_kernel<<<tiles, kCompactThreads, 0, s>>>(keep, done, gid, g.col, g.m, tile_count);
     *launches += 3;

@@ -81,9 +81,10 @@ struct ktruss_graph {
     kt::BalancedScratch bs;
     // batches (ktruss_load_batch): G graphs, vertex offsets, graph of each vertex
     int32_t G = 0;
-    int32_t *vo = nullptr, *gid = nullptr, *thr = nullptr, *live_g = nullptr,
+    int32_t *vo = nullptr, *gid = nullptr, *thr = nullptr, *kept_g = nullptr,
             *removed_g = nullptr, *rounds_g = nullptr;
     uint8_t *keep = nullptr, *done = nullptr;
+    kt::UpdateState ust;  // lower degrees and vertex flags of the support update
     std::vector<void *> owned;
     std::atomic<int> busy{0};
     // options
@@ -145,12 +146,14 @@ constexpr size_t kEventsPerRound = 6;
 
 // After a round that removed edges: take the next round's supports from the
 // decremental update (true) or recompute them (false).  Under AUTO the update
-// is used while the removed edges that lie in triangles are at most as many
-// as the surviving edges; either choice gives the same results.
+// is used while the removed edges that lie in triangles are at most a quarter
+// of the surviving edges: on the full batching workload one listed edge cost
+// the update about 2 ns and one surviving edge cost a support step about
+// 0.5 ns.  Either choice gives the same results.
 bool use_update(int mode, int32_t removed_tri, int32_t kept) {
     if (mode == KTRUSS_UPDATE_NEVER || kept == 0) return false;
     if (mode == KTRUSS_UPDATE_ALWAYS) return true;
-    return removed_tri <= kept;
+    return int64_t(removed_tri) * 4 <= int64_t(kept);
 }
 
 // KTRUSS_TRACE=1: one line per round on stderr (which call, round, live and
@@ -344,11 +347,12 @@ static int load_impl(ktruss_graph **out, int32_t n, int64_t m, const int32_t *ro
               A((void **)&g->pos, eb) && A((void **)&g->tile_count, (tiles + 1) * 4) &&
               A((void **)&g->tile_off, (tiles + 1) * 4) &&
               A((void **)&g->keep, size_t(m) + 1) &&
+              A((void **)&g->ust.ldeg, rpb) && A((void **)&g->ust.flag, size_t(n) + 1) &&
               A((void **)&g->cnt, 2 * sizeof(kt::RoundCounters));
     if (ok && G > 0) {
         const size_t gb = (size_t(G) + 1) * 4;
         ok = A((void **)&g->vo, gb) && A((void **)&g->gid, (size_t(n) + 1) * 4) &&
-             A((void **)&g->thr, gb) && A((void **)&g->live_g, gb) &&
+             A((void **)&g->thr, gb) && A((void **)&g->kept_g, gb) &&
              A((void **)&g->removed_g, gb) && A((void **)&g->rounds_g, gb) &&
              A((void **)&g->done, size_t(G) + 1);
         g->G = G;
@@ -431,6 +435,7 @@ int ktruss_run_batch(ktruss_graph *g, const int32_t *K, uint8_t *mask_out, int32
     const int32_t n = g->n;
     const int32_t m = int32_t(g->m);
     clear_round_stats(g);
+    g->ust.ldeg_valid = false;
     uint8_t *mask_d = mask_out;
     int32_t *sup_d = support_out;
     KT_CK(host_outputs(g, mem_kind, support_out != nullptr, &mask_d, &sup_d));
@@ -465,11 +470,12 @@ int ktruss_run_batch(ktruss_graph *g, const int32_t *K, uint8_t *mask_out, int32
             ++support_launches;
             kt::trace_phase(s, "batch support step");
         }
-        KT_CK(cudaMemsetAsync(g->live_g, 0, size_t(G) * 4, s));
+        KT_CK(cudaMemsetAsync(g->kept_g, 0, size_t(G) * 4, s));
         KT_CK(cudaMemsetAsync(g->removed_g, 0, size_t(G) * 4, s));
-        KT_CK(kt::launch_batch_prune(cur, S, g->gid, g->thr, g->keep, g->live_g, g->removed_g,
+        KT_CK(kt::launch_batch_prune(cur, S, g->gid, g->thr, g->keep, g->kept_g, g->removed_g,
                                      g->done, g->rounds_g, G, g->tile_count, g->tile_off, g->cnt,
-                                     s, &launches, track ? us.list : nullptr));
+                                     s, &launches, track ? us.list : nullptr,
+                                     g->ust.ldeg_valid ? g->ust.ldeg : nullptr));
         KT_CK(cudaMemcpyAsync(g->cnt_host, g->cnt, 2 * sizeof(kt::RoundCounters),
                               cudaMemcpyDeviceToHost, s));
         KT_CK(cudaStreamSynchronize(s));
@@ -489,7 +495,7 @@ int ktruss_run_batch(ktruss_graph *g, const int32_t *K, uint8_t *mask_out, int32
         if (upd) {
             KT_CK(cudaMemsetAsync(g->cnt + 1, 0, sizeof(kt::RoundCounters), s));
             KT_CK(kt::launch_support_update(cur, g->keep, us.list, c.removed_tri, S,
-                                            &g->cnt[1].triangles, us, s, &launches));
+                                            &g->cnt[1].triangles, us, &g->ust, s, &launches));
         }
         const int nb = buf;
         KT_CK(kt::launch_batch_compact(cur, S, g->keep, g->done, g->gid, g->tile_off, g->cnt,
@@ -556,6 +562,7 @@ int ktruss_run(ktruss_graph *g, int32_t K, uint8_t *mask_out, int32_t *support_o
     const int32_t m = int32_t(g->m);
     const int32_t thr = K - 2;
     clear_round_stats(g);
+    g->ust.ldeg_valid = false;
     uint8_t *mask_d = mask_out;
     int32_t *sup_d = support_out;
     KT_CK(host_outputs(g, mem_kind, support_out != nullptr, &mask_d, &sup_d));
@@ -602,7 +609,8 @@ int ktruss_run(ktruss_graph *g, int32_t K, uint8_t *mask_out, int32_t *support_o
         KT_CK(mark(2));
         KT_CK(kt::launch_prune_count(S, cur.m, thr, g->tile_count, g->tile_off, g->cnt, s,
                                      &launches, track ? g->keep : nullptr,
-                                     track ? us.list : nullptr));
+                                     track ? us.list : nullptr, cur.col,
+                                     g->ust.ldeg_valid ? g->ust.ldeg : nullptr));
         KT_CK(cudaMemcpyAsync(g->cnt_host, g->cnt, 2 * sizeof(kt::RoundCounters),
                               cudaMemcpyDeviceToHost, s));
         KT_CK(cudaStreamSynchronize(s));
@@ -629,7 +637,7 @@ int ktruss_run(ktruss_graph *g, int32_t K, uint8_t *mask_out, int32_t *support_o
         if (upd) {
             KT_CK(cudaMemsetAsync(g->cnt + 1, 0, sizeof(kt::RoundCounters), s));
             KT_CK(kt::launch_support_update(cur, g->keep, us.list, c.removed_tri, S,
-                                            &g->cnt[1].triangles, us, s, &launches));
+                                            &g->cnt[1].triangles, us, &g->ust, s, &launches));
         }
         KT_CK(mark(4));
         const int nb = buf;
@@ -693,6 +701,7 @@ int ktruss_decompose(ktruss_graph *g, int32_t *trussness_out, int32_t *kmax_out,
     const int32_t n = g->n;
     const int32_t m = int32_t(g->m);
     clear_round_stats(g);
+    g->ust.ldeg_valid = false;
     int32_t *tr_d = trussness_out;
     if (mem_kind == KTRUSS_HOST && m > 0) {
         uint8_t *unused_mask = nullptr;
@@ -727,7 +736,8 @@ int ktruss_decompose(ktruss_graph *g, int32_t *trussness_out, int32_t *kmax_out,
         }
         KT_CK(kt::launch_prune_count(S, cur.m, K - 2, g->tile_count, g->tile_off, g->cnt, s,
                                      &launches, track ? g->keep : nullptr,
-                                     track ? us.list : nullptr));
+                                     track ? us.list : nullptr, cur.col,
+                                     g->ust.ldeg_valid ? g->ust.ldeg : nullptr));
         KT_CK(cudaMemcpyAsync(g->cnt_host, g->cnt, 2 * sizeof(kt::RoundCounters),
                               cudaMemcpyDeviceToHost, s));
         KT_CK(cudaStreamSynchronize(s));
@@ -758,7 +768,7 @@ int ktruss_decompose(ktruss_graph *g, int32_t *trussness_out, int32_t *kmax_out,
         if (upd) {
             KT_CK(cudaMemsetAsync(g->cnt + 1, 0, sizeof(kt::RoundCounters), s));
             KT_CK(kt::launch_support_update(cur, g->keep, us.list, c.removed_tri, S,
-                                            &g->cnt[1].triangles, us, s, &launches));
+                                            &g->cnt[1].triangles, us, &g->ust, s, &launches));
         }
         const int nb = buf;
         KT_CK(kt::launch_compact(cur, S, K - 2, g->tile_off, g->cnt, g->pos, g->rp[nb],

@@ -33,7 +33,8 @@ __device__ __forceinline__ void warp_append(uint32_t ballot, int lane, int32_t v
 __global__ void __launch_bounds__(kCompactThreads)
 prune_count_kernel(const int32_t *__restrict__ S, int32_t m, int32_t thr,
                    int32_t *__restrict__ tile_count, uint8_t *__restrict__ keep,
-                   int32_t *__restrict__ list, RoundCounters *cnt) {
+                   int32_t *__restrict__ list, RoundCounters *cnt,
+                   const int32_t *__restrict__ col, int32_t *__restrict__ ldeg) {
     __shared__ int32_t warp_tot[kWarpsPerTile];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t base = int64_t(blockIdx.x) * kCompactTile + int64_t(w) * kWarpSpan + lane;
@@ -45,6 +46,7 @@ prune_count_kernel(const int32_t *__restrict__ S, int32_t m, int32_t thr,
         const bool k = e < m && sv >= thr;
         c += k ? 1 : 0;
         if (keep && e < m) keep[e] = k;
+        if (ldeg && e < m && !k) atomicSub(ldeg + __ldg(col + e), 1);
         if (list)
             warp_append(__ballot_sync(0xffffffffu, e < m && !k && sv > 0), lane, int32_t(e), list,
                         &cnt->removed_tri);
@@ -167,7 +169,8 @@ __global__ void finalize_kernel(const int32_t *__restrict__ eid, const int32_t *
 
 cudaError_t launch_prune_count(const int32_t *S, int32_t m, int32_t thr, int32_t *tile_count,
                                int32_t *tile_off, RoundCounters *cnt, cudaStream_t s,
-                               int *launches, uint8_t *keep, int32_t *list) {
+                               int *launches, uint8_t *keep, int32_t *list, const int32_t *col,
+                               int32_t *ldeg) {
     const int32_t tiles = compact_tiles(m);
     if (list) {
         cudaError_t e = cudaMemsetAsync(&cnt->removed_tri, 0, sizeof(int32_t), s);
@@ -175,7 +178,7 @@ cudaError_t launch_prune_count(const int32_t *S, int32_t m, int32_t thr, int32_t
     }
     if (tiles > 0) {
         prune_count_kernel<<<tiles, kCompactThreads, 0, s>>>(S, m, thr, tile_count, keep, list,
-                                                             cnt);
+                                                             cnt, col, ldeg);
         ++*launches;
     }
     scan_tiles_kernel<<<1, 1024, 0, s>>>(tile_count, tiles, tile_off, cnt);

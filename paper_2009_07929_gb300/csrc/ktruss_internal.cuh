@@ -78,8 +78,18 @@ void balanced_scratch_free(BalancedScratch *bs);
 // edges), the list of removed edges that lie in triangles (m), and the tile
 // arrays of an int32 scan over n+1 entries.
 struct UpdateScratch {
-    int32_t *lsrc, *lslot, *list, *lcnt, *lrp, *lfill;
+    int32_t *lsrc, *lslot, *list, *lx, *lcnt, *lrp, *lfill;
     int32_t *scan_sum, *scan_off, *scan_tot;
+};
+
+// State of the update that lives across rounds (owned by the caller): the
+// lower degree of every vertex in the live graph (ldeg, n+1 ints; valid once
+// ldeg_valid, after which prune subtracts the edges it removes) and one flag
+// byte per vertex.
+struct UpdateState {
+    int32_t *ldeg = nullptr;
+    uint8_t *flag = nullptr;
+    bool ldeg_valid = false;
 };
 UpdateScratch update_scratch(const BalancedScratch *bs);
 // out[i] = in[0] + ... + in[i-1] for i in [0, count) (int32, count <= cap_n + 1).
@@ -101,9 +111,11 @@ cudaError_t launch_support_balanced(const Live &g, int32_t *S, RoundCounters *cn
 // adds the number of those triangles into *destroyed.  list[0..nlist) are the
 // removed edges with S > 0 (removed edges with S = 0 lie in no triangle).
 // Afterwards the kept edges' S are their supports in g minus the removed edges.
+// st->ldeg is computed here the first time (st->ldeg_valid false).
 cudaError_t launch_support_update(const Live &g, const uint8_t *keep, const int32_t *list,
                                   int32_t nlist, int32_t *S, unsigned long long *destroyed,
-                                  const UpdateScratch &u, cudaStream_t s, int *launches);
+                                  const UpdateScratch &u, UpdateState *st, cudaStream_t s,
+                                  int *launches);
 
 // ---- prune + compaction + finalize (compact.cu) ---------------------------
 // Tile geometry of the compaction kernels.
@@ -116,10 +128,12 @@ inline int32_t compact_tiles(int32_t m) { return (m + kCompactTile - 1) / kCompa
 // Counts edges with S >= thr per tile into tile_count[tiles], then scans the
 // tile counts into tile_off[tiles] and writes the total into cnt->kept.  When
 // keep is given, keep[e] = (S[e] >= thr); when list is given, the removed edges
-// with S > 0 are appended to it and counted in cnt->removed_tri (reset here).
+// with S > 0 are appended to it and counted in cnt->removed_tri (reset here);
+// when ldeg is given, every removed edge (u, v) subtracts one from ldeg[v].
 cudaError_t launch_prune_count(const int32_t *S, int32_t m, int32_t thr, int32_t *tile_count,
                                int32_t *tile_off, RoundCounters *cnt, cudaStream_t s,
-                               int *launches, uint8_t *keep = nullptr, int32_t *list = nullptr);
+                               int *launches, uint8_t *keep = nullptr, int32_t *list = nullptr,
+                               const int32_t *col = nullptr, int32_t *ldeg = nullptr);
 
 // Scatters kept edges (S >= thr) of `in` into (col_out, eid_out) in order,
 // writes the exclusive kept-prefix of every slot into pos[m_in] (pos[m] =
@@ -151,20 +165,23 @@ cudaError_t launch_graph_of_vertex(const int32_t *vo, int32_t G, int32_t n, int3
 // Sets bit 16 of *err if an edge joins two graphs.
 cudaError_t launch_batch_validate(const int32_t *rp, const int32_t *col, int32_t n,
                                   const int32_t *gid, int32_t *err, cudaStream_t s);
-// Per-graph thresholds: keep flags, per-graph live/removed counts (zero on
-// entry), finished flags and round counters, tile counts and their scan
-// (edges that stay live -> cnt->kept).
+// Per-graph thresholds: keep flags, per-graph flags kept_g / removed_g (the
+// round kept / removed some edge of the graph; zero on entry), finished flags
+// and round counters, tile counts and their scan (edges that stay live ->
+// cnt->kept).
 // When list is given, removed edges with S > 0 are appended to it and counted
-// in cnt->removed_tri (reset here).
+// in cnt->removed_tri (reset here); when ldeg is given, every removed edge
+// (u, v) subtracts one from ldeg[v].
 cudaError_t launch_batch_prune(const Live &g, const int32_t *S, const int32_t *gid,
-                               const int32_t *thr, uint8_t *keep, int32_t *live_g,
+                               const int32_t *thr, uint8_t *keep, int32_t *kept_g,
                                int32_t *removed_g, uint8_t *done, int32_t *rounds_g, int32_t G,
                                int32_t *tile_count, int32_t *tile_off, RoundCounters *cnt,
-                               cudaStream_t s, int *launches, int32_t *list = nullptr);
-// Keep flags (support >= threshold of the edge's graph) and per-graph live and
-// removed counts (zero on entry) only.
+                               cudaStream_t s, int *launches, int32_t *list = nullptr,
+                               int32_t *ldeg = nullptr);
+// Keep flags (support >= threshold of the edge's graph) and the per-graph
+// kept_g / removed_g flags (zero on entry) only.
 cudaError_t launch_batch_keep(const Live &g, const int32_t *S, const int32_t *gid,
-                              const int32_t *thr, uint8_t *keep, int32_t *live_g,
+                              const int32_t *thr, uint8_t *keep, int32_t *kept_g,
                               int32_t *removed_g, cudaStream_t s, int *launches,
                               int32_t *list = nullptr, int32_t *list_count = nullptr);
 
@@ -173,17 +190,17 @@ cudaError_t launch_batch_keep(const Live &g, const int32_t *S, const int32_t *gi
 cudaError_t launch_server_append(const int32_t *rp_in, const int32_t *col_in, int32_t n, int32_t m,
                                  int32_t nb, int32_t mb, int32_t slot, int32_t *rp, int32_t *col,
                                  int32_t *eid, int32_t *gid, cudaStream_t s);
-// Keep flags and per-slot counts (= launch_batch_keep); removed edges with
+// Keep flags and per-slot kept / removed flags (= launch_batch_keep); removed edges with
 // S > 0 appended to list when given (count in *list_count, zero on entry).
 cudaError_t launch_server_prune(const Live &cur, const int32_t *S, const int32_t *gid,
-                                const int32_t *thr, uint8_t *keep, int32_t *live_g,
+                                const int32_t *thr, uint8_t *keep, int32_t *kept_g,
                                 int32_t *removed_g, cudaStream_t s, int *launches,
                                 int32_t *list = nullptr, int32_t *list_count = nullptr);
 // Finished slots, vertex renumbering (vcnt->kept = surviving vertices),
 // edge compaction (cnt->kept = surviving edges) with outputs of leaving edges
 // through the per-slot pointer tables, new row pointers and slot ids.
 cudaError_t launch_server_round_tail(const Live &cur, const int32_t *S, const uint8_t *keep,
-                                     const int32_t *live_g, const int32_t *removed_g,
+                                     const int32_t *kept_g, const int32_t *removed_g,
                                      uint8_t *fin, int32_t *rounds_g, int32_t slots,
                                      const int32_t *gid, int32_t *vmap, int32_t *vtile_count,
                                      int32_t *vtile_off, RoundCounters *vcnt, int32_t *etile_count,

@@ -79,7 +79,7 @@ struct ktruss_server {
     int32_t *rp[2] = {}, *col[2] = {}, *eid[2] = {}, *gid[2] = {};
     int32_t *S = nullptr, *S2 = nullptr, *pos = nullptr, *vmap = nullptr;
     uint8_t *keep = nullptr, *fin = nullptr;
-    int32_t *thr = nullptr, *live_g = nullptr, *removed_g = nullptr, *rounds_g = nullptr;
+    int32_t *thr = nullptr, *kept_g = nullptr, *removed_g = nullptr, *rounds_g = nullptr;
     uint8_t **mask_ptr = nullptr;
     int32_t **sup_ptr = nullptr;
     int32_t *etile_count = nullptr, *etile_off = nullptr, *vtile_count = nullptr,
@@ -91,6 +91,7 @@ struct ktruss_server {
     void **ptr_host = nullptr;              // pinned [2 * slots] staging of slot pointers
     int32_t *thr_host = nullptr;            // pinned [slots]
     kt::BalancedScratch bs;
+    kt::UpdateState ust;  // recomputed each step: vertex ids change between steps
     std::vector<void *> owned;
     int cur = 0;
     int32_t n_live = 0;
@@ -196,10 +197,12 @@ int ktruss_server_create(ktruss_server **out, int32_t max_vertices, int64_t max_
     A((void **)&v->S2, eb);
     A((void **)&v->pos, eb);
     A((void **)&v->vmap, nb);
+    A((void **)&v->ust.ldeg, nb);
+    A((void **)&v->ust.flag, size_t(max_vertices) + 1);
     A((void **)&v->keep, size_t(max_edges));
     A((void **)&v->fin, size_t(max_requests));
     A((void **)&v->thr, sb);
-    A((void **)&v->live_g, sb);
+    A((void **)&v->kept_g, sb);
     A((void **)&v->removed_g, sb);
     A((void **)&v->rounds_g, sb);
     A((void **)&v->mask_ptr, size_t(max_requests) * sizeof(void *));
@@ -343,11 +346,11 @@ int ktruss_server_step(ktruss_server *srv, int32_t *num_done) {
                 SV_CK(support_step(srv, rg, srv->S + f.mb, &launches));
             }
         }
-        SV_CK(cudaMemsetAsync(srv->live_g, 0, size_t(srv->slots) * 4, s));
+        SV_CK(cudaMemsetAsync(srv->kept_g, 0, size_t(srv->slots) * 4, s));
         SV_CK(cudaMemsetAsync(srv->removed_g, 0, size_t(srv->slots) * 4, s));
         const bool track = srv->update_mode != KTRUSS_UPDATE_NEVER;
         const kt::UpdateScratch us = kt::update_scratch(&srv->bs);
-        SV_CK(kt::launch_server_prune(g, srv->S, srv->gid[c], srv->thr, srv->keep, srv->live_g,
+        SV_CK(kt::launch_server_prune(g, srv->S, srv->gid[c], srv->thr, srv->keep, srv->kept_g,
                                       srv->removed_g, s, &launches, track ? us.list : nullptr,
                                       &srv->cnt[0].removed_tri));
         bool upd = false;
@@ -357,15 +360,18 @@ int ktruss_server_step(ktruss_server *srv, int32_t *num_done) {
             SV_CK(cudaStreamSynchronize(s));
             const int32_t nlist = srv->cnt_host[0].removed_tri;
             // survivors are not known before the round tail: the live edges
-            // that are not listed bound them from above
+            // bound them from above (the same quarter rule as ktruss_run)
             upd = srv->update_mode == KTRUSS_UPDATE_ALWAYS ||
-                  int64_t(nlist) * 2 <= int64_t(srv->m_live);
-            if (upd && nlist > 0)
+                  int64_t(nlist) * 4 <= int64_t(srv->m_live);
+            if (upd && nlist > 0) {
+                srv->ust.ldeg_valid = false;
                 SV_CK(kt::launch_support_update(g, srv->keep, us.list, nlist, srv->S,
-                                                &srv->cnt[2].triangles, us, s, &launches));
+                                                &srv->cnt[2].triangles, us, &srv->ust, s,
+                                                &launches));
+            }
         }
         SV_CK(kt::launch_server_round_tail(
-            g, srv->S, srv->keep, srv->live_g, srv->removed_g, srv->fin, srv->rounds_g,
+            g, srv->S, srv->keep, srv->kept_g, srv->removed_g, srv->fin, srv->rounds_g,
             srv->slots, srv->gid[c], srv->vmap, srv->vtile_count, srv->vtile_off, srv->cnt + 1,
             srv->etile_count, srv->etile_off, srv->cnt, srv->pos, srv->rp[o], srv->col[o],
             srv->eid[o], srv->gid[o], srv->mask_ptr, srv->sup_ptr, s, &launches,

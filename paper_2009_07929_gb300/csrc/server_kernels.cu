@@ -35,17 +35,17 @@ __global__ void append_kernel(const int32_t *__restrict__ rp_in, const int32_t *
     }
 }
 
-// Per slot: the round counts for slots that had live edges; a slot whose
+// Per slot (kept_g / removed_g: whether the round kept / removed some edge of
+// the slot): the round counts for slots that had live edges; a slot whose
 // round removed nothing, or removed every live edge, is finished.
-__global__ void finish_kernel(int32_t slots, const int32_t *__restrict__ live_g,
+__global__ void finish_kernel(int32_t slots, const int32_t *__restrict__ kept_g,
                               const int32_t *__restrict__ removed_g, uint8_t *__restrict__ fin,
                               int32_t *__restrict__ rounds_g) {
     const int32_t g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= slots) return;
-    const int32_t live = live_g[g];
-    if (live > 0) {
+    if (kept_g[g] || removed_g[g]) {
         rounds_g[g] += 1;
-        fin[g] = removed_g[g] == 0 || removed_g[g] == live;
+        fin[g] = removed_g[g] == 0 || kept_g[g] == 0;
     } else {
         fin[g] = 0;
     }
@@ -209,7 +209,7 @@ cudaError_t launch_server_append(const int32_t *rp_in, const int32_t *col_in, in
 }
 
 cudaError_t launch_server_round_tail(const Live &cur, const int32_t *S, const uint8_t *keep,
-                                     const int32_t *live_g, const int32_t *removed_g,
+                                     const int32_t *kept_g, const int32_t *removed_g,
                                      uint8_t *fin, int32_t *rounds_g, int32_t slots,
                                      const int32_t *gid, int32_t *vmap, int32_t *vtile_count,
                                      int32_t *vtile_off, RoundCounters *vcnt, int32_t *etile_count,
@@ -218,7 +218,7 @@ cudaError_t launch_server_round_tail(const Live &cur, const int32_t *S, const ui
                                      int32_t *gid_out, uint8_t *const *mask_ptr,
                                      int32_t *const *sup_ptr, cudaStream_t s, int *launches,
                                      int32_t *S_out) {
-    finish_kernel<<<(slots + 255) / 256, 256, 0, s>>>(slots, live_g, removed_g, fin, rounds_g);
+    finish_kernel<<<(slots + 255) / 256, 256, 0, s>>>(slots, kept_g, removed_g, fin, rounds_g);
     const int32_t vt = compact_tiles(cur.n);
     if (vt > 0) vertex_count_kernel<<<vt, kCompactThreads, 0, s>>>(gid, fin, cur.n, vtile_count);
     cudaError_t e = launch_scan_tiles(vtile_count, vt, vtile_off, vcnt, s, launches);
@@ -241,10 +241,10 @@ cudaError_t launch_server_round_tail(const Live &cur, const int32_t *S, const ui
 }
 
 cudaError_t launch_server_prune(const Live &cur, const int32_t *S, const int32_t *gid,
-                                const int32_t *thr, uint8_t *keep, int32_t *live_g,
+                                const int32_t *thr, uint8_t *keep, int32_t *kept_g,
                                 int32_t *removed_g, cudaStream_t s, int *launches, int32_t *list,
                                 int32_t *list_count) {
-    return launch_batch_keep(cur, S, gid, thr, keep, live_g, removed_g, s, launches, list,
+    return launch_batch_keep(cur, S, gid, thr, keep, kept_g, removed_g, s, launches, list,
                              list_count);
 }
 

@@ -84,11 +84,13 @@ constexpr int kSchedNChunks = 1;
 constexpr int kSchedGiveUp = 2;  // first loop that gave up (code), then two values
 constexpr int kSchedWords = 8;
 
-// Loops whose bound comes from the hash tables' load factor end after at most
-// a region's bucket count of steps; one that would exceed it records where it
-// gave up in sched[kSchedGiveUp..+2] (first one wins), sets the round's error
-// bit and stops.  None is expected to trigger.
-constexpr int32_t kGiveUpInsert = 1, kGiveUpFind = 2, kGiveUpProbe = 3, kGiveUpStage = 4;
+// Checks that cannot trigger on consistent inputs: an insertion that finds its
+// region full (regions are at most a quarter full) or a stage that takes no
+// row.  The first one records where it gave up in sched[kSchedGiveUp..+2],
+// sets the round's error bit and stops its loop.  The lookups need no such
+// bound: at load factor <= 1/4 every walk meets a bucket with a free entry,
+// which ends it (and a bound in the probe loop costs about 4 % of the step).
+constexpr int32_t kGiveUpInsert = 1, kGiveUpStage = 4;
 __device__ __noinline__ void give_up(int32_t *sched, int32_t *err, int32_t code, int32_t v1,
                                      int32_t v2) {
     if (atomicCAS(sched + kSchedGiveUp, 0, code) == 0) {
@@ -216,15 +218,14 @@ __device__ __forceinline__ bool table_insert(uint32_t *fpw, uint16_t *slots, int
     return false;  // region full: cannot happen at load factor <= 1/4
 }
 
-// Local slot of column w in the region (bbase, lb), -1 if absent, -2 if the
-// walk visited every bucket of the region (cannot happen at load factor <= 1/4).
+// Local slot of column w in the region (bbase, lb), or -1.
 __device__ __forceinline__ int32_t table_find(const uint32_t *fpw, const uint16_t *slots,
                                               const int32_t *vals, int32_t bbase, int lb,
                                               int32_t w) {
     const uint32_t bm = (1u << lb) - 1u;
     const uint32_t fp4 = fingerprint(w) * 0x01010101u;
     uint32_t b = (uint32_t(w) * kHashMul) >> (32 - lb);
-    for (uint32_t step = 0;;) {
+    for (;;) {
         const int32_t at = bbase + int32_t(b);
         const uint32_t word = fpw[at];
         for (uint32_t mm = match_bytes(word, fp4); mm; mm &= mm - 1u) {
@@ -232,7 +233,6 @@ __device__ __forceinline__ int32_t table_find(const uint32_t *fpw, const uint16_
             if (vals[sl] == w) return sl;
         }
         if ((word >> 24) == 0) return -1;
-        if (++step > bm) return -2;
         b = (b + 1) & bm;
     }
 }
@@ -512,7 +512,7 @@ struct SupportSmem {
     int32_t rpos[kBatch];             // runs: probe position of run r's first item
     int32_t rkey[kBatch];             // runs: staged (local) row the run probes
     int32_t rseg[kBatch];             // runs: segment of run r
-    int32_t wtmp[64];
+    unsigned long long wtmp[64];
     int32_t ctl[64];
 };
 static_assert(sizeof(SupportSmem) <= 227 * 1024, "support CTA exceeds shared memory");
@@ -530,40 +530,48 @@ struct SupportArgs {
     int32_t *err;
 };
 
-// Exclusive block-wide prefix of v (kThreads threads); *total = sum.
-__device__ __forceinline__ int32_t block_excl_scan(int32_t v, int32_t *wtmp, int32_t &total) {
+// Exclusive block-wide prefix of v (kThreads threads); *total = sum.  wtmp is
+// read after the second barrier, so the caller synchronises before reusing it.
+__device__ __forceinline__ unsigned long long block_excl_scan(unsigned long long v,
+                                                              unsigned long long *wtmp,
+                                                              unsigned long long &total) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int32_t incl = v;
+    unsigned long long incl = v;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-        const int32_t u = __shfl_up_sync(0xffffffffu, incl, d);
+        const unsigned long long u = __shfl_up_sync(0xffffffffu, incl, d);
         if (lane >= d) incl += u;
     }
     if (lane == 31) wtmp[warp] = incl;
     __syncthreads();
     if (warp == 0) {
-        int32_t x = lane < kWarps ? wtmp[lane] : 0;
+        unsigned long long x = lane < kWarps ? wtmp[lane] : 0ull;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
-            const int32_t u = __shfl_up_sync(0xffffffffu, x, d);
+            const unsigned long long u = __shfl_up_sync(0xffffffffu, x, d);
             if (lane >= d) x += u;
         }
         if (lane < kWarps) wtmp[32 + lane] = x;
     }
     __syncthreads();
-    const int32_t before = warp > 0 ? wtmp[32 + warp - 1] : 0;
+    const unsigned long long before = warp > 0 ? wtmp[32 + warp - 1] : 0ull;
     total = wtmp[32 + kWarps - 1];
-    __syncthreads();
     return before + incl - v;
 }
 
 // Builds the run list from per-thread (len, pos, key, seg) proposals: runs of
 // positive length in thread order.  Returns (runs, items) through the refs.
+// One scan serves both prefixes: the run flag in the high word, the length in
+// the low word (a batch's items stay below 2^31, so no carry crosses).
 __device__ __forceinline__ void build_runs(SupportSmem &sm, int32_t len, int32_t pos, int32_t key,
                                            int32_t j, int32_t &nruns, int32_t &items) {
     const int32_t flag = len > 0 ? 1 : 0;
-    const int32_t ridx = block_excl_scan(flag, sm.wtmp, nruns);
-    const int32_t roff = block_excl_scan(len > 0 ? len : 0, sm.wtmp, items);
+    unsigned long long tot;
+    const unsigned long long pre =
+        block_excl_scan((unsigned long long)flag << 32 | uint32_t(len > 0 ? len : 0), sm.wtmp, tot);
+    const int32_t ridx = int32_t(pre >> 32), roff = int32_t(uint32_t(pre));
+    nruns = int32_t(tot >> 32);
+    items = int32_t(uint32_t(tot));
     if (flag) {
         sm.rstart[ridx] = roff;
         sm.rpos[ridx] = pos;
@@ -611,7 +619,7 @@ __device__ __forceinline__ void probe_range(const SupportArgs &A, SupportSmem &s
                     const int32_t w = wv[u];
                     const uint32_t fp4 = fingerprint(w) * 0x01010101u;
                     uint32_t b = (uint32_t(w) * kHashMul) >> sh;
-                    for (uint32_t step = 0;;) {
+                    for (;;) {
                         const int32_t at = bb + int32_t(b);
                         const uint32_t word = sm.fpw[at];
                         int32_t q = -1;
@@ -629,17 +637,12 @@ __device__ __forceinline__ void probe_range(const SupportArgs &A, SupportSmem &s
                             break;
                         }
                         if ((word >> 24) == 0) break;
-                        if (++step > bm) {  // only reached past a full bucket
-                            give_up(A.sched, A.err, kGiveUpProbe, key, lb);
-                            break;
-                        }
                         b = (b + 1) & bm;
                     }
                 }
             }
             for (; i < nwin; ++i) {
                 const int32_t q = table_find(sm.fpw, sm.slots, sm.vals, bb, lb, __ldg(src + 32 * i));
-                if (q == -2) give_up(A.sched, A.err, kGiveUpFind, key, lb);
                 if (q >= 0) {
                     atomicAdd(&sm.cnt[q], 1);
                     atomicAdd(dst + 32 * i, 1);
@@ -685,7 +688,6 @@ __device__ __forceinline__ void probe_range(const SupportArgs &A, SupportSmem &s
                 const int32_t bb = single ? 0 : sm.tbase[key];
                 const int lb = single ? piece_lb : sm.tlb[key];
                 const int32_t q = table_find(sm.fpw, sm.slots, sm.vals, bb, lb, wv[u]);
-                if (q == -2) give_up(A.sched, A.err, kGiveUpFind, key, lb);
                 if (q >= 0) {
                     atomicAdd(&sm.cnt[q], 1);
                     atomicAdd(A.S + x[u], 1);
@@ -835,8 +837,8 @@ __device__ void long_row(const SupportArgs &A, SupportSmem &sm, int32_t rbase, i
             }
             if (!__syncthreads_or(left > 0)) break;  // every segment exhausted
         }
+        // the next batch writes only this thread's owner/hit entries
         flush_owners(A, sm, nb, tri);
-        __syncthreads();
     }
 }
 
@@ -963,8 +965,8 @@ support_kernel(SupportArgs A) {
                 build_runs(sm, len, pos0, key, tid, nruns, items);
                 if (items > 0) probe_runs(A, sm, nruns, items, false, 0);
                 __syncthreads();
+                // the next batch writes only this thread's owner/hit entries
                 flush_owners(A, sm, nb, tri);
-                __syncthreads();
             }
             for (int k = tid; k < slen; k += kThreads) {
                 const int32_t v = sm.cnt[k];
@@ -1069,6 +1071,7 @@ UpdateScratch update_scratch(const BalancedScratch *bs) {
     return UpdateScratch{c.ekey,
                          c.epst,
                          c.eitems,
+                         c.seg,
                          c.rcount,
                          c.rstart,
                          c.arank,

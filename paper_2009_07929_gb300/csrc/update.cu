@@ -11,17 +11,20 @@
 //
 // Every triangle {x, y, w} of G that contains a removed edge is handled once,
 // by its removed edge with the smallest slot:
-//   1. lower-neighbour lists of G: for every vertex v, the u < v with (u, v)
-//      in G and the slot of (u, v) (a count, a scan and a scatter over the
-//      edges; the order inside a list does not matter);
-//   2. one warp per removed edge p = (x, y) with S[p] > 0: it walks the full
-//      neighbourhood (upper row and lower list) of the endpoint z of smaller
-//      degree and, for each neighbour w, looks up the edge between w and the
-//      other endpoint o by binary search in the upper row of min(o, w).  A
-//      found edge closes a triangle; the triangle is credited here unless one
-//      of its other two edges is removed and has a smaller slot, and the
-//      credit subtracts one from each of its kept edges.  The walk stops after
-//      S[p] triangles: S[p] is exactly the number of triangles of G on p.
+//   1. per removed edge p = (x, y) with S[p] > 0: its row x and the endpoint z
+//      of smaller degree (the caller's lower degrees of the live graph, kept
+//      current across rounds), flagged;
+//   2. lower-neighbour lists of G for the flagged vertices only: the u < v
+//      with (u, v) in G and the slot of (u, v) (a count, a scan and a scatter
+//      over the edges; the order inside a list does not matter);
+//   3. one warp per removed edge: it walks the full neighbourhood (upper row
+//      and lower list) of z and, for each neighbour w, looks up the edge
+//      between w and the other endpoint o by binary search in the upper row of
+//      min(o, w).  A found edge closes a triangle; the triangle is credited
+//      here unless one of its other two edges is removed and has a smaller
+//      slot, and the credit subtracts one from each of its kept edges.  The
+//      walk stops after S[p] triangles: S[p] is exactly the number of
+//      triangles of G on p.
 #include "ktruss_internal.cuh"
 
 namespace kt {
@@ -51,32 +54,66 @@ __device__ __forceinline__ int32_t lower_bound(const int32_t *__restrict__ col, 
     return lo;
 }
 
-// lcnt[v] += number of edges (u, v) of the live graph.
+// ldeg[v] = number of kept edges (u, v), u < v, of the live graph (its lower
+// degree once the removed edges are gone).
 __global__ void __launch_bounds__(kThreads)
-lower_count_kernel(const int32_t *__restrict__ col, int32_t m, int32_t *__restrict__ lcnt) {
+lower_degree_kernel(const int32_t *__restrict__ col, const uint8_t *__restrict__ keep, int32_t m,
+                    int32_t *__restrict__ ldeg) {
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < m; e += stride)
-        atomicAdd(lcnt + __ldg(col + e), 1);
+        if (keep[e]) atomicAdd(ldeg + __ldg(col + e), 1);
 }
 
-// Scatters (u, slot) of every edge (u, v) into the lower list of v.  A thread
-// visits kSlotsPerThread consecutive slots, finding the row of the first by
-// binary search and following rows from there.
+// Per listed edge p = (x, y): its row x and the endpoint z of smaller degree
+// (upper row length + lower degree), whose neighbourhood the update walks;
+// flags z.  lx[k] = x, with bit 31 set when z = y.
+__global__ void __launch_bounds__(kThreads)
+pick_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, int32_t n,
+            const int32_t *__restrict__ ldeg, const int32_t *__restrict__ list, int32_t nlist,
+            uint8_t *__restrict__ flag, int32_t *__restrict__ lx) {
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < nlist; k += stride) {
+        const int32_t p = __ldg(list + k);
+        const int32_t x = row_of(rp, n, p);
+        const int32_t y = __ldg(col + p);
+        const int32_t dx = __ldg(rp + x + 1) - __ldg(rp + x) + __ldg(ldeg + x);
+        const int32_t dy = __ldg(rp + y + 1) - __ldg(rp + y) + __ldg(ldeg + y);
+        const bool walk_y = dy < dx;
+        flag[walk_y ? y : x] = 1;
+        lx[k] = x | (walk_y ? int32_t(0x80000000u) : 0);
+    }
+}
+
+// lcnt[v] += number of edges (u, v) of the live graph, for flagged v.
+__global__ void __launch_bounds__(kThreads)
+lower_count_kernel(const int32_t *__restrict__ col, int32_t m, const uint8_t *__restrict__ flag,
+                   int32_t *__restrict__ lcnt) {
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < m; e += stride) {
+        const int32_t v = __ldg(col + e);
+        if (flag[v]) atomicAdd(lcnt + v, 1);
+    }
+}
+
+// Scatters (u, slot) of every edge (u, v) with v flagged into the lower list
+// of v.  A thread visits kSlotsPerThread consecutive slots, finding the row of
+// the first by binary search and following rows from there.
 __global__ void __launch_bounds__(kThreads)
 lower_fill_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, int32_t n,
-                  int32_t m, const int32_t *__restrict__ lrp, int32_t *__restrict__ lfill,
-                  int32_t *__restrict__ lsrc, int32_t *__restrict__ lslot) {
+                  int32_t m, const uint8_t *__restrict__ flag, const int32_t *__restrict__ lrp,
+                  int32_t *__restrict__ lfill, int32_t *__restrict__ lsrc,
+                  int32_t *__restrict__ lslot) {
     const int64_t e0 = (int64_t(blockIdx.x) * kThreads + threadIdx.x) * kSlotsPerThread;
     if (e0 >= m) return;
-    int32_t u = row_of(rp, n, int32_t(e0));
-    int32_t uend = __ldg(rp + u + 1);
     const int64_t e1 = e0 + kSlotsPerThread < m ? e0 + kSlotsPerThread : m;
+    int32_t u = -1, uend = 0;
     for (int64_t e = e0; e < e1; ++e) {
-        if (e >= uend) {
+        const int32_t v = __ldg(col + e);
+        if (!flag[v]) continue;
+        if (u < 0 || e >= uend) {
             u = row_of(rp, n, int32_t(e));
             uend = __ldg(rp + u + 1);
         }
-        const int32_t v = __ldg(col + e);
         const int32_t at = __ldg(lrp + v) + atomicAdd(lfill + v, 1);
         lsrc[at] = u;
         lslot[at] = int32_t(e);
@@ -84,27 +121,24 @@ lower_fill_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ co
 }
 
 __global__ void __launch_bounds__(kThreads)
-update_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, int32_t n,
+update_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
               const int32_t *__restrict__ lrp, const int32_t *__restrict__ lsrc,
               const int32_t *__restrict__ lslot, const uint8_t *__restrict__ keep,
-              const int32_t *__restrict__ list, int32_t nlist, int32_t *__restrict__ S,
-              unsigned long long *__restrict__ destroyed) {
+              const int32_t *__restrict__ list, const int32_t *__restrict__ lx, int32_t nlist,
+              int32_t *__restrict__ S, unsigned long long *__restrict__ destroyed) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t(gridDim.x) * blockDim.x) >> 5;
     unsigned long long mine = 0;
     for (int64_t k = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; k < nlist;
          k += warps) {
         const int32_t p = __ldg(list + k);
-        const int32_t x = row_of(rp, n, p);
+        const int32_t xw = __ldg(lx + k);
+        const int32_t x = xw & 0x7fffffff;
+        const bool walk_y = xw < 0;
         const int32_t y = __ldg(col + p);
-        const int32_t xu0 = __ldg(rp + x), xu1 = __ldg(rp + x + 1);
-        const int32_t yu0 = __ldg(rp + y), yu1 = __ldg(rp + y + 1);
-        const int32_t xl0 = __ldg(lrp + x), xl1 = __ldg(lrp + x + 1);
-        const int32_t yl0 = __ldg(lrp + y), yl1 = __ldg(lrp + y + 1);
-        const bool walk_y = (yu1 - yu0) + (yl1 - yl0) < (xu1 - xu0) + (xl1 - xl0);
-        const int32_t o = walk_y ? x : y;
-        const int32_t zu0 = walk_y ? yu0 : xu0, zu1 = walk_y ? yu1 : xu1;
-        const int32_t zl0 = walk_y ? yl0 : xl0, zl1 = walk_y ? yl1 : xl1;
+        const int32_t z = walk_y ? y : x, o = walk_y ? x : y;
+        const int32_t zu0 = __ldg(rp + z), zu1 = __ldg(rp + z + 1);
+        const int32_t zl0 = __ldg(lrp + z), zl1 = __ldg(lrp + z + 1);
         const int32_t nu = zu1 - zu0;
         const int32_t total = nu + (zl1 - zl0);
         const int32_t need = __ldg(S + p);
@@ -148,26 +182,39 @@ update_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, i
 
 cudaError_t launch_support_update(const Live &g, const uint8_t *keep, const int32_t *list,
                                   int32_t nlist, int32_t *S, unsigned long long *destroyed,
-                                  const UpdateScratch &u, cudaStream_t s, int *launches) {
+                                  const UpdateScratch &u, UpdateState *st, cudaStream_t s,
+                                  int *launches) {
     if (nlist <= 0 || g.m == 0) return cudaSuccess;
     const int64_t rows = int64_t(g.n) + 1;
-    cudaError_t e = cudaMemsetAsync(u.lcnt, 0, size_t(rows) * 4, s);
+    auto grid = [](int64_t work, int64_t cap) { return int((work + kThreads - 1) / kThreads < cap
+                                                               ? (work + kThreads - 1) / kThreads
+                                                               : cap); };
+    cudaError_t e = cudaSuccess;
+    if (!st->ldeg_valid) {
+        // lower degrees after this round's removals; prune keeps them current
+        // from here on by subtracting the edges it removes
+        e = cudaMemsetAsync(st->ldeg, 0, size_t(rows) * 4, s);
+        if (e != cudaSuccess) return e;
+        lower_degree_kernel<<<grid(g.m, 152 * 16), kThreads, 0, s>>>(g.col, keep, g.m, st->ldeg);
+        ++*launches;
+        st->ldeg_valid = true;
+    }
+    e = cudaMemsetAsync(st->flag, 0, size_t(g.n), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(u.lcnt, 0, size_t(rows) * 4, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(u.lfill, 0, size_t(rows) * 4, s);
     if (e != cudaSuccess) return e;
-    int64_t cblocks = (int64_t(g.m) + kThreads - 1) / kThreads;
-    if (cblocks > 152 * 16) cblocks = 152 * 16;
-    lower_count_kernel<<<int(cblocks), kThreads, 0, s>>>(g.col, g.m, u.lcnt);
-    ++*launches;
+    pick_kernel<<<grid(nlist, 152 * 16), kThreads, 0, s>>>(g.rp, g.col, g.n, st->ldeg, list, nlist,
+                                                            st->flag, u.lx);
+    lower_count_kernel<<<grid(g.m, 152 * 16), kThreads, 0, s>>>(g.col, g.m, st->flag, u.lcnt);
+    *launches += 2;
     e = launch_scan_i32(u.lcnt, u.lrp, rows, u, s, launches);
     if (e != cudaSuccess) return e;
     const int64_t fblocks =
         (int64_t(g.m) + int64_t(kThreads) * kSlotsPerThread - 1) / (int64_t(kThreads) * kSlotsPerThread);
-    lower_fill_kernel<<<int(fblocks), kThreads, 0, s>>>(g.rp, g.col, g.n, g.m, u.lrp, u.lfill,
-                                                        u.lsrc, u.lslot);
-    int64_t ublocks = (int64_t(nlist) * 32 + kThreads - 1) / kThreads;
-    if (ublocks > 152 * 32) ublocks = 152 * 32;
-    update_kernel<<<int(ublocks), kThreads, 0, s>>>(g.rp, g.col, g.n, u.lrp, u.lsrc, u.lslot, keep,
-                                                    list, nlist, S, destroyed);
+    lower_fill_kernel<<<int(fblocks), kThreads, 0, s>>>(g.rp, g.col, g.n, g.m, st->flag, u.lrp,
+                                                        u.lfill, u.lsrc, u.lslot);
+    update_kernel<<<grid(int64_t(nlist) * 32, 152 * 32), kThreads, 0, s>>>(
+        g.rp, g.col, u.lrp, u.lsrc, u.lslot, keep, list, u.lx, nlist, S, destroyed);
     *launches += 2;
     return cudaGetLastError();
 }
