@@ -30,6 +30,10 @@
 //    every probe is still read once.  Credits to staged slots are gathered in
 //    shared memory and flushed once per stage or piece.
 //
+// Light tasks (t + d <= kLight) skip all of the above: one thread merges the
+// two short lists (support_light_kernel), which costs less than giving them a
+// segment.  Which tasks are light is decided by the same test in both kernels.
+//
 // All credits are integer additions, so the result does not depend on the
 // order in which CTAs, warps or the counting sort place the work.
 #include <cstdint>
@@ -75,6 +79,15 @@ constexpr int kScanPer = 16;
 constexpr int kScanTile = kScanThreads * kScanPer;
 constexpr int kEdgeThreads = 256;
 constexpr int kEdgesPerThread = 16;
+#ifndef KT_SUPPORT_LIGHT
+#define KT_SUPPORT_LIGHT 64
+#endif
+// Tasks whose two lists hold at most kLight columns together are merged by one
+// thread (support_light_kernel) instead of being staged and probed.
+constexpr int32_t kLight = KT_SUPPORT_LIGHT;
+constexpr int kLightPerThread = 4;
+
+__device__ __forceinline__ bool light_task(int32_t t, int32_t d) { return t + d <= kLight; }
 
 constexpr int32_t kIntMax = 0x7fffffff;
 
@@ -364,7 +377,7 @@ classify_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
             const int32_t d = __ldg(rp + kappa + 1) - kb;
             const int32_t t = rw.rend - int32_t(e) - 1;
             merge += (long long)t + d;
-            const int32_t items = min(t, d);
+            const int32_t items = light_task(t, d) ? 0 : min(t, d);
             if (items > 0) {
                 const bool stage_kappa = t < d;
                 key = stage_kappa ? kappa : rw.row;
@@ -384,6 +397,51 @@ classify_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
         for (int k = 0; k < kEdgeThreads / 32; ++k) t += part[k];
         if (t) atomicAdd(merge_work, (unsigned long long)t);
     }
+}
+
+// Light tasks: a thread walks kLightPerThread consecutive slots and merges the
+// tail of row i after each light task's slot with row kappa (Listing 1's
+// two-pointer loop), crediting both matching slots and, once, its own slot.
+__global__ void __launch_bounds__(kEdgeThreads)
+support_light_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, int32_t n,
+                     int32_t m, int32_t *__restrict__ S, unsigned long long *__restrict__ tri) {
+    const int64_t e0 = (int64_t(blockIdx.x) * kEdgeThreads + threadIdx.x) * kLightPerThread;
+    int32_t found = 0;
+    if (e0 < m) {
+        RowWalk rw{0, 0, 0};
+        rw.start(rp, n, int32_t(e0));
+#pragma unroll 1
+        for (int j = 0; j < kLightPerThread; ++j) {
+            const int64_t e = e0 + j;
+            if (e >= m) break;
+            rw.advance(rp, n, int32_t(e));
+            const int32_t kappa = __ldg(col + e);
+            int32_t y = __ldg(rp + kappa);
+            const int32_t ye = __ldg(rp + kappa + 1);
+            int32_t x = int32_t(e) + 1;
+            const int32_t xe = rw.rend;
+            if (x >= xe || y >= ye || !light_task(xe - x, ye - y)) continue;
+            int32_t own = 0;
+            while (x < xe && y < ye) {
+                const int32_t a = __ldg(col + x), b = __ldg(col + y);
+                if (a == b) {
+                    atomicAdd(S + x, 1);
+                    atomicAdd(S + y, 1);
+                    ++own;
+                    ++x;
+                    ++y;
+                } else if (a < b) {
+                    ++x;
+                } else {
+                    ++y;
+                }
+            }
+            if (own) atomicAdd(S + e, own);
+            found += own;
+        }
+    }
+    const int32_t tot = __reduce_add_sync(0xffffffffu, found);
+    if ((threadIdx.x & 31) == 0 && tot) atomicAdd(tri, (unsigned long long)tot);
 }
 
 struct RowCountLoad {
@@ -509,8 +567,8 @@ struct SupportSmem {
     int32_t owner[kBatch];            // batch: owner edge slot of segment j
     int32_t hit[kBatch];              // batch: hits credited to segment j's owner
     int32_t rstart[kBatch + 1];       // runs: batch-local item offset of run r
-    int32_t rpos[kBatch];             // runs: probe position of run r's first item
-    int32_t rkey[kBatch];             // runs: staged (local) row the run probes
+    int32_t rdel[kBatch];             // runs: probe position of item i of run r is rdel[r] + i
+    int32_t rreg[kBatch];             // runs: region probed (first bucket | log2 buckets << 24)
     int32_t rseg[kBatch];             // runs: segment of run r
     unsigned long long wtmp[64];
     int32_t ctl[64];
@@ -559,11 +617,17 @@ __device__ __forceinline__ unsigned long long block_excl_scan(unsigned long long
     return before + incl - v;
 }
 
-// Builds the run list from per-thread (len, pos, key, seg) proposals: runs of
-// positive length in thread order.  Returns (runs, items) through the refs.
-// One scan serves both prefixes: the run flag in the high word, the length in
-// the low word (a batch's items stay below 2^31, so no carry crosses).
-__device__ __forceinline__ void build_runs(SupportSmem &sm, int32_t len, int32_t pos, int32_t key,
+// Region word of a staged row: first bucket in the low 24 bits, log2 of the
+// bucket count above.
+__device__ __forceinline__ int32_t region_word(int32_t bbase, int lb) { return bbase | (lb << 24); }
+
+// Builds the run list from per-thread (len, pos, reg, seg) proposals: runs of
+// positive length in thread order, each with its position offset and the
+// region word of the staged row it probes.  Returns (runs, items) through the
+// refs.  One scan serves both prefixes: the run flag in the high word, the
+// length in the low word (a batch's items stay below 2^31, so no carry
+// crosses).
+__device__ __forceinline__ void build_runs(SupportSmem &sm, int32_t len, int32_t pos, int32_t reg,
                                            int32_t j, int32_t &nruns, int32_t &items) {
     const int32_t flag = len > 0 ? 1 : 0;
     unsigned long long tot;
@@ -574,8 +638,8 @@ __device__ __forceinline__ void build_runs(SupportSmem &sm, int32_t len, int32_t
     items = int32_t(uint32_t(tot));
     if (flag) {
         sm.rstart[ridx] = roff;
-        sm.rpos[ridx] = pos;
-        sm.rkey[ridx] = key;
+        sm.rdel[ridx] = pos - roff;
+        sm.rreg[ridx] = reg;
         sm.rseg[ridx] = j;
     }
     if (threadIdx.x == 0) {
@@ -590,10 +654,9 @@ __device__ __forceinline__ void build_runs(SupportSmem &sm, int32_t len, int32_t
 // warp-uniform and a tight loop streams its windows (kUnroll loads in flight
 // per lane), counting the owner's hits in a register; a window that crosses
 // run boundaries maps each lane to its run with a bitmask of the run starts
-// inside the window.  single = true: one staged piece, region (0, piece_lb).
+// inside the window.
 __device__ __forceinline__ void probe_range(const SupportArgs &A, SupportSmem &sm, int32_t nruns,
-                                            int32_t items, int32_t E, int32_t p, int32_t pe,
-                                            bool single, int piece_lb) {
+                                            int32_t items, int32_t E, int32_t p, int32_t pe) {
     const int lane = threadIdx.x & 31;
     while (p < pe) {
         while (E + 1 < nruns && sm.rstart[E + 1] <= p) ++E;
@@ -601,12 +664,12 @@ __device__ __forceinline__ void probe_range(const SupportArgs &A, SupportSmem &s
         if (rend - p >= 32) {
             // ---- whole windows of run E: warp-uniform parameters
             const int32_t nwin = (rend - p) >> 5;
-            const int32_t key = single ? 0 : sm.rkey[E];
-            const int32_t bb = single ? 0 : sm.tbase[key];
-            const int lb = single ? piece_lb : sm.tlb[key];
+            const int32_t reg = sm.rreg[E];
+            const int32_t bb = reg & 0xffffff;
+            const int lb = reg >> 24;
             const uint32_t bm = (1u << lb) - 1u;
             const int sh = 32 - lb;
-            const int32_t *__restrict__ src = A.col + sm.rpos[E] + (p - sm.rstart[E]) + lane;
+            const int32_t *__restrict__ src = A.col + sm.rdel[E] + p + lane;
             int32_t *__restrict__ dst = A.S + (src - A.col);
             int32_t own = 0;
             int32_t i = 0;
@@ -675,7 +738,7 @@ __device__ __forceinline__ void probe_range(const SupportArgs &A, SupportSmem &s
                 const int32_t item = p + lane;
                 ok[u] = item < pe;
                 rr[u] = r;
-                x[u] = sm.rpos[r] + (item - sm.rstart[r]);
+                x[u] = sm.rdel[r] + item;
                 E = __shfl_sync(0xffffffffu, r, 31);
                 p += 32;
             }
@@ -684,9 +747,9 @@ __device__ __forceinline__ void probe_range(const SupportArgs &A, SupportSmem &s
 #pragma unroll
             for (int u = 0; u < kMixUnroll; ++u) {
                 if (!ok[u]) continue;
-                const int32_t key = single ? 0 : sm.rkey[rr[u]];
-                const int32_t bb = single ? 0 : sm.tbase[key];
-                const int lb = single ? piece_lb : sm.tlb[key];
+                const int32_t reg = sm.rreg[rr[u]];
+                const int32_t bb = reg & 0xffffff;
+                const int lb = reg >> 24;
                 const int32_t q = table_find(sm.fpw, sm.slots, sm.vals, bb, lb, wv[u]);
                 if (q >= 0) {
                     atomicAdd(&sm.cnt[q], 1);
@@ -702,15 +765,14 @@ __device__ __forceinline__ void probe_range(const SupportArgs &A, SupportSmem &s
 // (kGrain == 0), or grains of kGrain items taken from a shared counter
 // (sm.ctl[4], zero on entry) until the batch is exhausted.
 __device__ __forceinline__ void probe_runs(const SupportArgs &A, SupportSmem &sm, int32_t nruns,
-                                           int32_t items, bool single, int piece_lb) {
+                                           int32_t items) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if constexpr (kGrain == 0) {
         const int32_t per = ((items + kWarps - 1) / kWarps + 31) & ~31;
         const int32_t w0 = warp * per;
         const int32_t w1 = min(items, w0 + per);
         if (w0 < w1)
-            probe_range(A, sm, nruns, items, last_le(sm.rstart, 0, nruns - 1, w0), w0, w1,
-                        single, piece_lb);
+            probe_range(A, sm, nruns, items, last_le(sm.rstart, 0, nruns - 1, w0), w0, w1);
     } else {
         for (;;) {
             int32_t g = 0;
@@ -718,7 +780,7 @@ __device__ __forceinline__ void probe_runs(const SupportArgs &A, SupportSmem &sm
             g = __shfl_sync(0xffffffffu, g, 0);
             if (g >= items) break;
             const int32_t E = last_le(sm.rstart, 0, nruns - 1, g);
-            probe_range(A, sm, nruns, items, E, g, min(items, g + kGrain), single, piece_lb);
+            probe_range(A, sm, nruns, items, E, g, min(items, g + kGrain));
         }
     }
 }
@@ -815,9 +877,9 @@ __device__ void long_row(const SupportArgs &A, SupportSmem &sm, int32_t rbase, i
                 left = ke - lo;
             }
             int32_t nruns, items;
-            build_runs(sm, cnt_in, k, 0, tid, nruns, items);
+            const int lb = region_lb(plen);
+            build_runs(sm, cnt_in, k, region_word(0, lb), tid, nruns, items);
             if (items > 0) {
-                const int lb = region_lb(plen);
                 clear_table(sm, 1 << lb, plen, tid);
                 __syncthreads();
                 for (int q = tid; q < plen; q += kThreads) {
@@ -827,7 +889,7 @@ __device__ void long_row(const SupportArgs &A, SupportSmem &sm, int32_t rbase, i
                         give_up(A.sched, A.err, kGiveUpInsert, plen, lb);
                 }
                 __syncthreads();
-                probe_runs(A, sm, nruns, items, true, lb);
+                probe_runs(A, sm, nruns, items);
                 __syncthreads();
                 for (int q = tid; q < plen; q += kThreads) {
                     const int32_t v = sm.cnt[q];
@@ -962,8 +1024,9 @@ support_kernel(SupportArgs A) {
                     sm.hit[tid] = 0;
                 }
                 int32_t nruns, items;
-                build_runs(sm, len, pos0, key, tid, nruns, items);
-                if (items > 0) probe_runs(A, sm, nruns, items, false, 0);
+                build_runs(sm, len, pos0, tid < nb ? region_word(sm.tbase[key], sm.tlb[key]) : 0,
+                           tid, nruns, items);
+                if (items > 0) probe_runs(A, sm, nruns, items);
                 __syncthreads();
                 // the next batch writes only this thread's owner/hit entries
                 flush_owners(A, sm, nb, tri);
@@ -1180,6 +1243,11 @@ cudaError_t launch_support_balanced(const Live &g, int32_t *S, RoundCounters *cn
         e = cudaEventRecord(ev[1], s);
         if (e != cudaSuccess) return e;
     }
+    const int64_t lblocks = (int64_t(m) + int64_t(kEdgeThreads) * kLightPerThread - 1) /
+                            (int64_t(kEdgeThreads) * kLightPerThread);
+    support_light_kernel<<<int(lblocks), kEdgeThreads, 0, s>>>(g.rp, g.col, n, m, S,
+                                                              &cnt->triangles);
+    *launches += 1;
     SupportArgs A{g.rp, g.col, c.seg, c.pst, c.sact, c.wp, c.arow, c.aseg, c.plan, c.bound,
                   c.sched, S, &cnt->triangles, &cnt->error};
     support_kernel<<<g_support_blocks, kThreads, sizeof(SupportSmem), s>>>(A);
