@@ -16,6 +16,7 @@ namespace {
 
 constexpr int kWarpsPerTile = kCompactThreads / 32;
 constexpr int kWarpSpan = kCompactTile / kWarpsPerTile;
+constexpr int32_t kRecomputeMinListed = 1 << 16;
 
 // gid[v] = graph owning vertex v (largest g with vo[g] <= v).
 __global__ void graph_of_vertex_kernel(const int32_t *__restrict__ vo, int32_t G, int32_t n,
@@ -49,13 +50,14 @@ __global__ void batch_validate_kernel(const int32_t *__restrict__ rp, const int3
 // round kept some edge (kept_g) and removed some edge (removed_g): both are
 // 0/1 flags set with a plain store after a read shows them unset.  Removed
 // edges with S > 0 are appended to list (when given) at positions taken from
-// *list_count; when ldeg is given, each removed edge (u, v) subtracts one from
-// ldeg[v].
+// *list_count (and, when listed_g is given, counted per graph); when ldeg is
+// given, each removed edge (u, v) subtracts one from ldeg[v].
 __global__ void __launch_bounds__(256)
 batch_prune_kernel(const int32_t *__restrict__ S, const int32_t *__restrict__ col, int32_t m,
                    const int32_t *__restrict__ gid, const int32_t *__restrict__ thr,
                    uint8_t *__restrict__ keep, int32_t *kept_g, int32_t *removed_g,
-                   int32_t *__restrict__ list, int32_t *list_count, int32_t *__restrict__ ldeg) {
+                   int32_t *__restrict__ list, int32_t *list_count, int32_t *__restrict__ ldeg,
+                   int32_t *__restrict__ listed_g) {
     const int lane = threadIdx.x & 31;
     const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     int32_t g = -1;
@@ -78,6 +80,11 @@ batch_prune_kernel(const int32_t *__restrict__ S, const int32_t *__restrict__ co
             if (lane == __ffs(b) - 1) at = atomicAdd(list_count, __popc(b));
             at = __shfl_sync(0xffffffffu, at, __ffs(b) - 1);
             if ((b >> lane) & 1u) list[at + __popc(b & ((1u << lane) - 1u))] = int32_t(e);
+            if (listed_g) {
+                const bool mine = (b >> lane) & 1u;
+                const uint32_t peers = __match_any_sync(0xffffffffu, mine ? g : -1);
+                if (mine && lane == __ffs(peers) - 1) atomicAdd(listed_g + g, __popc(peers));
+            }
         }
     }
 }
@@ -93,6 +100,42 @@ __global__ void batch_done_kernel(int32_t G, const int32_t *__restrict__ kept_g,
         rounds_g[g] += 1;
         done[g] = removed_g[g] == 0;
     }
+}
+
+// Per graph after a round's compaction (rp_new: the new row pointers, graph g
+// owns vertices [vo[g], vo[g+1])): its surviving edges, and whether its next
+// supports come from the update of this round (upd_g = 1) or from a support
+// step (0).  mode: 0 never update, 1 always, 2 update while the listed edges
+// (removed, in triangles) are at most a quarter of the survivors, or fewer than
+// kRecomputeMinListed: a support step for a few graphs still classifies every
+// live edge of the batch, which only pays off for a graph that would otherwise
+// update a large number of edges.  Counts the graphs that stay live
+// (cnt->kept) and those that need a support step (cnt->removed_tri).
+__global__ void batch_decide_kernel(int32_t G, const int32_t *__restrict__ vo,
+                                    const int32_t *__restrict__ rp_new,
+                                    const int32_t *__restrict__ listed_g, int32_t mode,
+                                    uint8_t *__restrict__ upd_g, RoundCounters *cnt) {
+    const int32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= G) return;
+    const int32_t kept = rp_new[vo[g + 1]] - rp_new[vo[g]];
+    const int32_t listed = listed_g[g];
+    const bool upd = kept > 0 && (mode == 1 || (mode == 2 && (int64_t(listed) * 4 <= kept ||
+                                                             listed < kRecomputeMinListed)));
+    upd_g[g] = upd ? 1 : 0;
+    if (kept > 0) {
+        atomicAdd(&cnt->kept, 1);
+        if (!upd) atomicAdd(&cnt->removed_tri, 1);
+    }
+}
+
+// S[e] = 0 for the live edges of graphs whose next supports come from a
+// support step (upd_g == 0).
+__global__ void batch_zero_kernel(const int32_t *__restrict__ col, int32_t m,
+                                  const int32_t *__restrict__ gid,
+                                  const uint8_t *__restrict__ upd_g, int32_t *__restrict__ S) {
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < m; e += stride)
+        if (!upd_g[gid[col[e]]]) S[e] = 0;
 }
 
 __device__ __forceinline__ bool stays(const uint8_t *keep, const uint8_t *done, const int32_t *gid,
@@ -194,7 +237,8 @@ cudaError_t launch_batch_keep(const Live &g, const int32_t *S, const int32_t *gi
                               int32_t *list_count) {
     if (g.m == 0) return cudaSuccess;
     batch_prune_kernel<<<(g.m + 255) / 256, 256, 0, s>>>(S, g.col, g.m, gid, thr, keep, kept_g,
-                                                         removed_g, list, list_count, nullptr);
+                                                         removed_g, list, list_count, nullptr,
+                                                         nullptr);
     ++*launches;
     return cudaGetLastError();
 }
@@ -203,13 +247,15 @@ cudaError_t launch_batch_prune(const Live &g, const int32_t *S, const int32_t *g
                                const int32_t *thr, uint8_t *keep, int32_t *kept_g,
                                int32_t *removed_g, uint8_t *done, int32_t *rounds_g, int32_t G,
                                int32_t *tile_count, int32_t *tile_off, RoundCounters *cnt,
-                               cudaStream_t s, int *launches, int32_t *list, int32_t *ldeg) {
+                               cudaStream_t s, int *launches, int32_t *list, int32_t *ldeg,
+                               int32_t *listed_g) {
     if (list) {
         cudaError_t e = cudaMemsetAsync(&cnt->removed_tri, 0, sizeof(int32_t), s);
         if (e != cudaSuccess) return e;
     }
     batch_prune_kernel<<<(g.m + 255) / 256, 256, 0, s>>>(S, g.col, g.m, gid, thr, keep, kept_g,
-                                                         removed_g, list, &cnt->removed_tri, ldeg);
+                                                         removed_g, list, &cnt->removed_tri, ldeg,
+                                                         listed_g);
     batch_done_kernel<<<(G + 255) / 256, 256, 0, s>>>(G, kept_g, removed_g, done, rounds_g);
     const int32_t tiles = compact_tiles(g.m);
     batch_count_kernel<<<tiles, kCompactThreads, 0, s>>>(keep, done, gid, g.col, g.m, tile_count);
@@ -219,6 +265,26 @@ cudaError_t launch_batch_prune(const Live &g, const int32_t *S, const int32_t *g
     // scan of the tile counts (the single-graph kernels' scan, which ignores S
     // when given tile counts directly)
     return launch_scan_tiles(tile_count, tiles, tile_off, cnt, s, launches);
+}
+
+cudaError_t launch_batch_decide(int32_t G, const int32_t *vo, const int32_t *rp_new,
+                                const int32_t *listed_g, int32_t mode, uint8_t *upd_g,
+                                RoundCounters *cnt, cudaStream_t s, int *launches) {
+    cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(RoundCounters), s);
+    if (e != cudaSuccess) return e;
+    batch_decide_kernel<<<(G + 255) / 256, 256, 0, s>>>(G, vo, rp_new, listed_g, mode, upd_g, cnt);
+    ++*launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_zero(const Live &g, const int32_t *gid, const uint8_t *upd_g, int32_t *S,
+                              cudaStream_t s, int *launches) {
+    if (g.m == 0) return cudaSuccess;
+    int64_t blocks = (int64_t(g.m) + 255) / 256;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    batch_zero_kernel<<<int(blocks), 256, 0, s>>>(g.col, g.m, gid, upd_g, S);
+    ++*launches;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_batch_compact(const Live &in, const int32_t *S, const uint8_t *keep,

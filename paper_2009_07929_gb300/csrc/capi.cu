@@ -83,7 +83,8 @@ struct ktruss_graph {
     int32_t G = 0;
     int32_t *vo = nullptr, *gid = nullptr, *thr = nullptr, *kept_g = nullptr,
             *removed_g = nullptr, *rounds_g = nullptr;
-    uint8_t *keep = nullptr, *done = nullptr;
+    uint8_t *keep = nullptr, *done = nullptr, *upd_g = nullptr;
+    int32_t *listed_g = nullptr;
     kt::UpdateState ust;  // lower degrees and vertex flags of the support update
     std::vector<void *> owned;
     std::atomic<int> busy{0};
@@ -347,14 +348,16 @@ static int load_impl(ktruss_graph **out, int32_t n, int64_t m, const int32_t *ro
               A((void **)&g->pos, eb) && A((void **)&g->tile_count, (tiles + 1) * 4) &&
               A((void **)&g->tile_off, (tiles + 1) * 4) &&
               A((void **)&g->keep, size_t(m) + 1) &&
-              A((void **)&g->ust.ldeg, rpb) && A((void **)&g->ust.flag, size_t(n) + 1) &&
+              A((void **)&g->ust.ldeg, rpb) && A((void **)&g->ust.flag, rpb) &&
+              A((void **)&g->ust.nz, 16) &&
               A((void **)&g->cnt, 2 * sizeof(kt::RoundCounters));
     if (ok && G > 0) {
         const size_t gb = (size_t(G) + 1) * 4;
         ok = A((void **)&g->vo, gb) && A((void **)&g->gid, (size_t(n) + 1) * 4) &&
              A((void **)&g->thr, gb) && A((void **)&g->kept_g, gb) &&
              A((void **)&g->removed_g, gb) && A((void **)&g->rounds_g, gb) &&
-             A((void **)&g->done, size_t(G) + 1);
+             A((void **)&g->done, size_t(G) + 1) && A((void **)&g->upd_g, size_t(G) + 1) &&
+             A((void **)&g->listed_g, gb);
         g->G = G;
     }
     g->owned = al.owned;
@@ -375,6 +378,7 @@ static int load_impl(ktruss_graph **out, int32_t n, int64_t m, const int32_t *ro
     if (e == cudaSuccess) e = cudaMemcpyAsync(g->rp0, row_ptr, rpb, kind, s);
     if (e == cudaSuccess && m > 0) e = cudaMemcpyAsync(g->col0, col, eb, kind, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(g->cnt, 0, 2 * sizeof(kt::RoundCounters), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->ust.flag, 0, rpb, s);
     if (e == cudaSuccess) e = kt::launch_validate(g->rp0, g->col0, n, m, &g->cnt->error, s);
     if (e == cudaSuccess && G > 0) {
         e = cudaMemcpyAsync(g->vo, vertex_offsets, (size_t(G) + 1) * 4, cudaMemcpyHostToDevice, s);
@@ -458,53 +462,81 @@ int ktruss_run_batch(ktruss_graph *g, const int32_t *K, uint8_t *mask_out, int32
     kt::Live cur{g->rp0, g->col0, nullptr, n, m};
     int buf = 0;
     int32_t *S = g->S, *S_next = g->S2;
-    bool have_s = false;
-    int64_t tri_cur = 0;
+    // Each graph takes its own choice between the update and a support step
+    // (batch_decide_kernel): upd_g[g] = 1 when graph g's supports in S are
+    // current.  any_valid: some graph's are; need_graphs: live graphs whose
+    // supports a support step must compute (tasks of the others are skipped).
+    bool any_valid = false;
+    int32_t need_graphs = 0;
     while (cur.m > 0) {
         ++rounds;
-        const bool updated = have_s;
-        if (!have_s) {
+        const bool partial = any_valid;
+        KT_CK(cudaMemsetAsync(g->cnt, 0, sizeof(kt::RoundCounters), s));
+        if (!any_valid) {
             KT_CK(cudaMemsetAsync(S, 0, size_t(cur.m) * 4, s));
-            KT_CK(cudaMemsetAsync(g->cnt, 0, sizeof(kt::RoundCounters), s));
             KT_CK(support_step(g, cur, S, s, &launches, nullptr));
             ++support_launches;
-            kt::trace_phase(s, "batch support step");
+        } else if (need_graphs > 0) {
+            KT_CK(kt::launch_batch_zero(cur, g->gid, g->upd_g, S, s, &launches));
+            kt::Live masked = cur;
+            masked.gid = g->gid;
+            masked.skip = g->upd_g;
+            KT_CK(support_step(g, masked, S, s, &launches, nullptr));
+            ++support_launches;
         }
+        kt::trace_phase(s, "batch support step");
         KT_CK(cudaMemsetAsync(g->kept_g, 0, size_t(G) * 4, s));
         KT_CK(cudaMemsetAsync(g->removed_g, 0, size_t(G) * 4, s));
+        if (track) KT_CK(cudaMemsetAsync(g->listed_g, 0, size_t(G) * 4, s));
         KT_CK(kt::launch_batch_prune(cur, S, g->gid, g->thr, g->keep, g->kept_g, g->removed_g,
                                      g->done, g->rounds_g, G, g->tile_count, g->tile_off, g->cnt,
                                      s, &launches, track ? us.list : nullptr,
-                                     g->ust.ldeg_valid ? g->ust.ldeg : nullptr));
-        KT_CK(cudaMemcpyAsync(g->cnt_host, g->cnt, 2 * sizeof(kt::RoundCounters),
+                                     g->ust.ldeg_valid ? g->ust.ldeg : nullptr,
+                                     track ? g->listed_g : nullptr));
+        KT_CK(cudaMemcpyAsync(g->cnt_host, g->cnt, sizeof(kt::RoundCounters),
                               cudaMemcpyDeviceToHost, s));
         KT_CK(cudaStreamSynchronize(s));
         const kt::RoundCounters c = g->cnt_host[0];
         if (c.error) return (c.error & kt::kDevErrTimeout) ? KTRUSS_ETIMEOUT : KTRUSS_ECUDA;
-        tri_cur = updated ? tri_cur - int64_t(g->cnt_host[1].triangles) : int64_t(c.triangles);
+        // per-round triangles of a batch: those counted by the round's support
+        // step (the graphs whose supports were recomputed)
         g->live.push_back(cur.m);
-        g->tris.push_back(tri_cur);
-        g->merge.push_back(updated ? 0 : int64_t(c.merge_work));
+        g->tris.push_back(int64_t(c.triangles));
+        g->merge.push_back(int64_t(c.merge_work));
         g->removed.push_back(int64_t(cur.m) - c.kept);
         g->ms_sup.push_back(0.f);
-        g->upd.push_back(updated ? 1 : 0);
-        trace.round(rounds, cur.m, int64_t(cur.m) - c.kept, c.removed_tri, updated);
+        g->upd.push_back(partial ? 1 : 0);
+        trace.round(rounds, cur.m, int64_t(cur.m) - c.kept, c.removed_tri, partial);
         // kept = edges that stay live (kept edges of unfinished graphs); the
-        // finished graphs leave at this compaction with their outputs
-        const bool upd = track && use_update(g->update_mode, c.removed_tri, c.kept);
-        if (upd) {
-            KT_CK(cudaMemsetAsync(g->cnt + 1, 0, sizeof(kt::RoundCounters), s));
-            KT_CK(kt::launch_support_update(cur, g->keep, us.list, c.removed_tri, S,
-                                            &g->cnt[1].triangles, us, &g->ust, s, &launches));
-        }
+        // finished graphs leave at this compaction with their outputs; the
+        // supports ride along so that updated graphs keep theirs
         const int nb = buf;
         KT_CK(kt::launch_batch_compact(cur, S, g->keep, g->done, g->gid, g->tile_off, g->cnt,
                                        g->pos, g->rp[nb], g->col[nb], g->eid[nb], mask_d, sup_d,
-                                       s, &launches, upd ? S_next : nullptr));
+                                       s, &launches, track ? S_next : nullptr));
+        any_valid = false;
+        if (track && c.kept > 0) {
+            // per graph: update or support step next round; the update runs on
+            // this round's graph and subtracts into the compacted supports
+            KT_CK(kt::launch_batch_decide(G, g->vo, g->rp[nb], g->listed_g, g->update_mode,
+                                          g->upd_g, g->cnt + 1, s, &launches));
+            if (c.removed_tri > 0) {
+                kt::Live old = cur;
+                old.gid = g->gid;
+                KT_CK(kt::launch_support_update(old, g->keep, us.list, c.removed_tri, S,
+                                                &g->cnt[1].triangles, us, &g->ust, s, &launches,
+                                                g->pos, S_next, g->upd_g));
+            }
+            KT_CK(cudaMemcpyAsync(g->cnt_host + 1, g->cnt + 1, sizeof(kt::RoundCounters),
+                                  cudaMemcpyDeviceToHost, s));
+            KT_CK(cudaStreamSynchronize(s));
+            const int32_t live_graphs = g->cnt_host[1].kept;
+            need_graphs = g->cnt_host[1].removed_tri;
+            any_valid = need_graphs < live_graphs;
+        }
         cur = kt::Live{g->rp[nb], g->col[nb], g->eid[nb], n, c.kept};
         buf ^= 1;
-        if (upd) std::swap(S, S_next);
-        have_s = upd;
+        if (track) std::swap(S, S_next);
     }
     if (timing) KT_CK(cudaEventRecord(g->events[1], s));
     if (mem_kind == KTRUSS_HOST && m > 0) {

@@ -16,7 +16,17 @@ struct Live {
     const int32_t *eid;  // [m] or nullptr
     int32_t n;
     int32_t m;
+    // Batches only (both null otherwise): gid[v] = graph of vertex v, and a
+    // support step skips every task of a graph g with skip[g] != 0 (its
+    // supports are current), leaving that graph's S untouched.
+    const int32_t *gid = nullptr;
+    const uint8_t *skip = nullptr;
 };
+
+// True when the task of an edge in row i belongs to a skipped graph.
+__device__ __forceinline__ bool skipped_row(const Live &g, int32_t i) {
+    return g.skip && g.skip[g.gid[i]];
+}
 
 // Device-side counters of one round, written by kernels, read once per round
 // by the host through a pinned mirror.
@@ -73,26 +83,29 @@ cudaError_t balanced_scratch_alloc(BalancedScratch *bs, int32_t n, int64_t m);
 void balanced_scratch_free(BalancedScratch *bs);
 
 // Views of the balanced scratch used by the support update (which never runs
-// at the same time as the balanced support step): lower-neighbour lists of
-// the live graph (lcnt, lrp, lfill over n+1 vertices; lsrc, lslot over m
-// edges), the list of removed edges that lie in triangles (m), and the tile
-// arrays of an int32 scan over n+1 entries.
+// at the same time as the balanced support step), all sized by the edge
+// count m: lower-neighbour lists of the flagged vertices (lsrc, lslot; lcnt,
+// lrp, lfill by compact vertex index), the list of removed edges that lie in
+// triangles and per-entry data (list, lx), the flagged vertices (zlist), and
+// the tile arrays of an int32 scan over up to m + 1 entries.
 struct UpdateScratch {
-    int32_t *lsrc, *lslot, *list, *lx, *lcnt, *lrp, *lfill;
+    int32_t *lsrc, *lslot, *list, *lx, *zlist, *lcnt, *lrp, *lfill;
     int32_t *scan_sum, *scan_off, *scan_tot;
 };
 
 // State of the update that lives across rounds (owned by the caller): the
 // lower degree of every vertex in the live graph (ldeg, n+1 ints; valid once
-// ldeg_valid, after which prune subtracts the edges it removes) and one flag
-// byte per vertex.
+// ldeg_valid, after which prune subtracts the edges it removes), one flag
+// word per vertex (n+1 ints, zero on entry and on return of every update)
+// and a counter word (nz).
 struct UpdateState {
     int32_t *ldeg = nullptr;
-    uint8_t *flag = nullptr;
+    int32_t *flag = nullptr;
+    int32_t *nz = nullptr;
     bool ldeg_valid = false;
 };
 UpdateScratch update_scratch(const BalancedScratch *bs);
-// out[i] = in[0] + ... + in[i-1] for i in [0, count) (int32, count <= cap_n + 1).
+// out[i] = in[0] + ... + in[i-1] for i in [0, count) (int32, count <= cap_m + 1).
 cudaError_t launch_scan_i32(const int32_t *in, int32_t *out, int64_t count,
                             const UpdateScratch &u, cudaStream_t s, int *launches);
 
@@ -112,10 +125,15 @@ cudaError_t launch_support_balanced(const Live &g, int32_t *S, RoundCounters *cn
 // removed edges with S > 0 (removed edges with S = 0 lie in no triangle).
 // Afterwards the kept edges' S are their supports in g minus the removed edges.
 // st->ldeg is computed here the first time (st->ldeg_valid false).
+// When pos is given (the slot map of a compaction that already ran, old slot
+// -> new slot), the subtractions go to S_out[pos[q]] instead of S[q] (S is
+// then only read).  When upd_g is given (batches: g.gid set), only listed
+// edges of graphs with upd_g[graph] != 0 are processed.
 cudaError_t launch_support_update(const Live &g, const uint8_t *keep, const int32_t *list,
                                   int32_t nlist, int32_t *S, unsigned long long *destroyed,
                                   const UpdateScratch &u, UpdateState *st, cudaStream_t s,
-                                  int *launches);
+                                  int *launches, const int32_t *pos = nullptr,
+                                  int32_t *S_out = nullptr, const uint8_t *upd_g = nullptr);
 
 // ---- prune + compaction + finalize (compact.cu) ---------------------------
 // Tile geometry of the compaction kernels.
@@ -177,7 +195,17 @@ cudaError_t launch_batch_prune(const Live &g, const int32_t *S, const int32_t *g
                                int32_t *removed_g, uint8_t *done, int32_t *rounds_g, int32_t G,
                                int32_t *tile_count, int32_t *tile_off, RoundCounters *cnt,
                                cudaStream_t s, int *launches, int32_t *list = nullptr,
-                               int32_t *ldeg = nullptr);
+                               int32_t *ldeg = nullptr, int32_t *listed_g = nullptr);
+// After a round's compaction (rp_new), per graph: surviving edges and the
+// choice of update (upd_g = 1) or support step for its next supports (mode:
+// KTRUSS_UPDATE_* values); cnt (cleared here): kept = graphs that stay live,
+// removed_tri = those that need a support step.
+cudaError_t launch_batch_decide(int32_t G, const int32_t *vo, const int32_t *rp_new,
+                                const int32_t *listed_g, int32_t mode, uint8_t *upd_g,
+                                RoundCounters *cnt, cudaStream_t s, int *launches);
+// S[e] = 0 for the live edges of graphs with upd_g == 0.
+cudaError_t launch_batch_zero(const Live &g, const int32_t *gid, const uint8_t *upd_g, int32_t *S,
+                              cudaStream_t s, int *launches);
 // Keep flags (support >= threshold of the edge's graph) and the per-graph
 // kept_g / removed_g flags (zero on entry) only.
 cudaError_t launch_batch_keep(const Live &g, const int32_t *S, const int32_t *gid,

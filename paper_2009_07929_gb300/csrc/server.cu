@@ -198,7 +198,8 @@ int ktruss_server_create(ktruss_server **out, int32_t max_vertices, int64_t max_
     A((void **)&v->pos, eb);
     A((void **)&v->vmap, nb);
     A((void **)&v->ust.ldeg, nb);
-    A((void **)&v->ust.flag, size_t(max_vertices) + 1);
+    A((void **)&v->ust.flag, nb);
+    A((void **)&v->ust.nz, 16);
     A((void **)&v->keep, size_t(max_edges));
     A((void **)&v->fin, size_t(max_requests));
     A((void **)&v->thr, sb);
@@ -219,6 +220,7 @@ int ktruss_server_create(ktruss_server **out, int32_t max_vertices, int64_t max_
     if (e == cudaSuccess) e = cudaMallocHost((void **)&v->ptr_host, 2 * size_t(max_requests) * sizeof(void *));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&v->thr_host, sb);
     if (e == cudaSuccess) e = cudaMemsetAsync(v->rp[0], 0, 4, v->s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v->ust.flag, 0, nb, v->s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(v->s);
     if (e != cudaSuccess) {
         const int rc = map_err(e);

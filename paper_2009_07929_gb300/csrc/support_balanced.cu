@@ -359,7 +359,8 @@ __global__ void __launch_bounds__(kEdgeThreads)
 classify_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, int32_t n,
                 int32_t m, int32_t *__restrict__ ekey, int32_t *__restrict__ epst,
                 int32_t *__restrict__ eitems, int32_t *__restrict__ rcount,
-                unsigned long long *__restrict__ merge_work) {
+                unsigned long long *__restrict__ merge_work, const int32_t *__restrict__ gid,
+                const uint8_t *__restrict__ skip) {
     __shared__ long long part[kEdgeThreads / 32];
     const int lane = threadIdx.x & 31;
     const int64_t e0 = (int64_t(blockIdx.x) * kEdgeThreads + threadIdx.x) * kEdgesPerThread;
@@ -376,8 +377,9 @@ classify_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
             const int32_t kb = __ldg(rp + kappa);
             const int32_t d = __ldg(rp + kappa + 1) - kb;
             const int32_t t = rw.rend - int32_t(e) - 1;
-            merge += (long long)t + d;
-            const int32_t items = light_task(t, d) ? 0 : min(t, d);
+            const bool skipped = skip && skip[gid[rw.row]];
+            if (!skipped) merge += (long long)t + d;
+            const int32_t items = (skipped || light_task(t, d)) ? 0 : min(t, d);
             if (items > 0) {
                 const bool stage_kappa = t < d;
                 key = stage_kappa ? kappa : rw.row;
@@ -404,7 +406,8 @@ classify_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
 // two-pointer loop), crediting both matching slots and, once, its own slot.
 __global__ void __launch_bounds__(kEdgeThreads)
 support_light_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, int32_t n,
-                     int32_t m, int32_t *__restrict__ S, unsigned long long *__restrict__ tri) {
+                     int32_t m, int32_t *__restrict__ S, unsigned long long *__restrict__ tri,
+                     const int32_t *__restrict__ gid, const uint8_t *__restrict__ skip) {
     const int64_t e0 = (int64_t(blockIdx.x) * kEdgeThreads + threadIdx.x) * kLightPerThread;
     int32_t found = 0;
     if (e0 < m) {
@@ -421,6 +424,7 @@ support_light_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__
             int32_t x = int32_t(e) + 1;
             const int32_t xe = rw.rend;
             if (x >= xe || y >= ye || !light_task(xe - x, ye - y)) continue;
+            if (skip && skip[gid[rw.row]]) continue;
             int32_t own = 0;
             while (x < xe && y < ye) {
                 const int32_t a = __ldg(col + x), b = __ldg(col + y);
@@ -1135,12 +1139,13 @@ UpdateScratch update_scratch(const BalancedScratch *bs) {
                          c.epst,
                          c.eitems,
                          c.seg,
-                         c.rcount,
-                         c.rstart,
-                         c.arank,
-                         reinterpret_cast<int32_t *>(c.rtile_sum),
-                         reinterpret_cast<int32_t *>(c.rtile_off),
-                         reinterpret_cast<int32_t *>(c.rtot)};
+                         c.pst,
+                         c.sitems,
+                         reinterpret_cast<int32_t *>(c.wp),
+                         c.sact,
+                         reinterpret_cast<int32_t *>(c.itile_sum),
+                         reinterpret_cast<int32_t *>(c.itile_off),
+                         reinterpret_cast<int32_t *>(c.itot)};
 }
 
 cudaError_t launch_scan_i32(const int32_t *in, int32_t *out, int64_t count,
@@ -1196,7 +1201,7 @@ cudaError_t launch_support_balanced(const Live &g, int32_t *S, RoundCounters *cn
     const int eblocks = int((int64_t(m) + kEdgeThreads * kEdgesPerThread - 1) /
                             (kEdgeThreads * kEdgesPerThread));
     classify_kernel<<<eblocks, kEdgeThreads, 0, s>>>(g.rp, g.col, n, m, c.ekey, c.epst, c.eitems,
-                                                     c.rcount, &cnt->merge_work);
+                                                     c.rcount, &cnt->merge_work, g.gid, g.skip);
     trace_phase(s, "classify");
     // row scan: segment starts and active-row ranks (row n has count 0, so the
     // entries at n are the totals)
@@ -1246,7 +1251,7 @@ cudaError_t launch_support_balanced(const Live &g, int32_t *S, RoundCounters *cn
     const int64_t lblocks = (int64_t(m) + int64_t(kEdgeThreads) * kLightPerThread - 1) /
                             (int64_t(kEdgeThreads) * kLightPerThread);
     support_light_kernel<<<int(lblocks), kEdgeThreads, 0, s>>>(g.rp, g.col, n, m, S,
-                                                              &cnt->triangles);
+                                                              &cnt->triangles, g.gid, g.skip);
     *launches += 1;
     SupportArgs A{g.rp, g.col, c.seg, c.pst, c.sact, c.wp, c.arow, c.aseg, c.plan, c.bound,
                   c.sched, S, &cnt->triangles, &cnt->error};

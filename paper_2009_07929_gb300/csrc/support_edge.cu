@@ -23,11 +23,12 @@ __device__ __forceinline__ int32_t row_of_slot(const int32_t *__restrict__ rp, i
 
 __global__ void __launch_bounds__(256)
 support_edge_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, int32_t n,
-                    int32_t m, int32_t *__restrict__ S, unsigned long long *__restrict__ tri) {
+                    int32_t m, int32_t *__restrict__ S, unsigned long long *__restrict__ tri,
+                    const int32_t *__restrict__ gid, const uint8_t *__restrict__ skip) {
     const int32_t e = blockIdx.x * blockDim.x + threadIdx.x;
     int32_t own = 0;
-    if (e < m) {
-        const int32_t i = row_of_slot(rp, n, e);
+    const int32_t i = e < m ? row_of_slot(rp, n, e) : 0;
+    if (e < m && !(skip && skip[gid[i]])) {
         const int32_t kappa = __ldg(col + e);
         int32_t x = e + 1;
         const int32_t xe = __ldg(rp + i + 1);
@@ -60,10 +61,11 @@ support_edge_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ 
 // another in the same thread, which is the load imbalance Sec. III-A describes.
 __global__ void __launch_bounds__(256)
 support_coarse_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, int32_t n,
-                      int32_t *__restrict__ S, unsigned long long *__restrict__ tri) {
+                      int32_t *__restrict__ S, unsigned long long *__restrict__ tri,
+                      const int32_t *__restrict__ gid, const uint8_t *__restrict__ skip) {
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     long long found = 0;
-    if (i < n) {
+    if (i < n && !(skip && skip[gid[i]])) {
         const int32_t rb = __ldg(rp + i), re = __ldg(rp + i + 1);
         for (int32_t e = rb; e < re; ++e) {
             const int32_t kappa = __ldg(col + e);
@@ -99,7 +101,8 @@ cudaError_t launch_support_coarse(const Live &g, int32_t *S, RoundCounters *cnt,
     if (g.m == 0) return cudaSuccess;
     const int threads = 256;
     const int blocks = (g.n + threads - 1) / threads;
-    support_coarse_kernel<<<blocks, threads, 0, s>>>(g.rp, g.col, g.n, S, &cnt->triangles);
+    support_coarse_kernel<<<blocks, threads, 0, s>>>(g.rp, g.col, g.n, S, &cnt->triangles, g.gid,
+                                                     g.skip);
     return cudaGetLastError();
 }
 
@@ -107,7 +110,8 @@ cudaError_t launch_support_edge(const Live &g, int32_t *S, RoundCounters *cnt, c
     if (g.m == 0) return cudaSuccess;
     const int threads = 256;
     const int blocks = (g.m + threads - 1) / threads;
-    support_edge_kernel<<<blocks, threads, 0, s>>>(g.rp, g.col, g.n, g.m, S, &cnt->triangles);
+    support_edge_kernel<<<blocks, threads, 0, s>>>(g.rp, g.col, g.n, g.m, S, &cnt->triangles,
+                                                   g.gid, g.skip);
     return cudaGetLastError();
 }
 

@@ -13,7 +13,8 @@
 // by its removed edge with the smallest slot:
 //   1. per removed edge p = (x, y) with S[p] > 0: its row x and the endpoint z
 //      of smaller degree (the caller's lower degrees of the live graph, kept
-//      current across rounds), flagged;
+//      current across rounds), flagged; each flagged vertex then gets a
+//      compact index, so that nothing below is sized by the vertex count;
 //   2. lower-neighbour lists of G for the flagged vertices only: the u < v
 //      with (u, v) in G and the slot of (u, v) (a count, a scan and a scatter
 //      over the edges; the order inside a list does not matter);
@@ -66,16 +67,22 @@ lower_degree_kernel(const int32_t *__restrict__ col, const uint8_t *__restrict__
 
 // Per listed edge p = (x, y): its row x and the endpoint z of smaller degree
 // (upper row length + lower degree), whose neighbourhood the update walks;
-// flags z.  lx[k] = x, with bit 31 set when z = y.
+// flags z.  lx[k] = x, with bit 31 set when z = y; lx[k] = -1 when the edge's
+// graph is not updated (upd_g given and upd_g[graph] == 0).
 __global__ void __launch_bounds__(kThreads)
 pick_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, int32_t n,
             const int32_t *__restrict__ ldeg, const int32_t *__restrict__ list, int32_t nlist,
-            uint8_t *__restrict__ flag, int32_t *__restrict__ lx) {
+            int32_t *__restrict__ flag, int32_t *__restrict__ lx, const int32_t *__restrict__ gid,
+            const uint8_t *__restrict__ upd_g) {
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < nlist; k += stride) {
         const int32_t p = __ldg(list + k);
-        const int32_t x = row_of(rp, n, p);
         const int32_t y = __ldg(col + p);
+        if (upd_g && !upd_g[gid[y]]) {
+            lx[k] = -1;
+            continue;
+        }
+        const int32_t x = row_of(rp, n, p);
         const int32_t dx = __ldg(rp + x + 1) - __ldg(rp + x) + __ldg(ldeg + x);
         const int32_t dy = __ldg(rp + y + 1) - __ldg(rp + y) + __ldg(ldeg + y);
         const bool walk_y = dy < dx;
@@ -84,14 +91,45 @@ pick_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, int
     }
 }
 
-// lcnt[v] += number of edges (u, v) of the live graph, for flagged v.
+// flag[v]: 0 = not flagged, 1 = flagged by pick_kernel, c + 2 = flagged with
+// compact index c.  Each flagged vertex of the list is claimed once: it gets
+// the next index and zlist[c] = v.
 __global__ void __launch_bounds__(kThreads)
-lower_count_kernel(const int32_t *__restrict__ col, int32_t m, const uint8_t *__restrict__ flag,
+claim_kernel(const int32_t *__restrict__ col, const int32_t *__restrict__ list,
+             const int32_t *__restrict__ lx, int32_t nlist, int32_t *__restrict__ flag,
+             int32_t *__restrict__ zlist, int32_t *__restrict__ nz) {
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < nlist; k += stride) {
+        const int32_t xw = __ldg(lx + k);
+        if (xw == -1) continue;
+        const int32_t z = xw < 0 ? __ldg(col + __ldg(list + k)) : xw;
+        if (atomicCAS(flag + z, 1, 0x7fffffff) == 1) {
+            const int32_t c = atomicAdd(nz, 1);
+            zlist[c] = z;
+            flag[z] = c + 2;
+        }
+    }
+}
+
+// flag[zlist[c]] = 0 for every claimed vertex (c < *nz).
+__global__ void __launch_bounds__(kThreads)
+unflag_kernel(const int32_t *__restrict__ zlist, const int32_t *__restrict__ nz, int32_t cap,
+              int32_t *__restrict__ flag) {
+    const int32_t count = *nz;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; c < count && c < cap;
+         c += stride)
+        flag[zlist[c]] = 0;
+}
+
+// lcnt[c] += number of edges (u, v) of the live graph, for v with compact index c.
+__global__ void __launch_bounds__(kThreads)
+lower_count_kernel(const int32_t *__restrict__ col, int32_t m, const int32_t *__restrict__ flag,
                    int32_t *__restrict__ lcnt) {
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < m; e += stride) {
-        const int32_t v = __ldg(col + e);
-        if (flag[v]) atomicAdd(lcnt + v, 1);
+        const int32_t f = flag[__ldg(col + e)];
+        if (f >= 2) atomicAdd(lcnt + (f - 2), 1);
     }
 }
 
@@ -100,7 +138,7 @@ lower_count_kernel(const int32_t *__restrict__ col, int32_t m, const uint8_t *__
 // the first by binary search and following rows from there.
 __global__ void __launch_bounds__(kThreads)
 lower_fill_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, int32_t n,
-                  int32_t m, const uint8_t *__restrict__ flag, const int32_t *__restrict__ lrp,
+                  int32_t m, const int32_t *__restrict__ flag, const int32_t *__restrict__ lrp,
                   int32_t *__restrict__ lfill, int32_t *__restrict__ lsrc,
                   int32_t *__restrict__ lslot) {
     const int64_t e0 = (int64_t(blockIdx.x) * kThreads + threadIdx.x) * kSlotsPerThread;
@@ -108,13 +146,13 @@ lower_fill_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ co
     const int64_t e1 = e0 + kSlotsPerThread < m ? e0 + kSlotsPerThread : m;
     int32_t u = -1, uend = 0;
     for (int64_t e = e0; e < e1; ++e) {
-        const int32_t v = __ldg(col + e);
-        if (!flag[v]) continue;
+        const int32_t f = flag[__ldg(col + e)];
+        if (f < 2) continue;
         if (u < 0 || e >= uend) {
             u = row_of(rp, n, int32_t(e));
             uend = __ldg(rp + u + 1);
         }
-        const int32_t at = __ldg(lrp + v) + atomicAdd(lfill + v, 1);
+        const int32_t at = __ldg(lrp + (f - 2)) + atomicAdd(lfill + (f - 2), 1);
         lsrc[at] = u;
         lslot[at] = int32_t(e);
     }
@@ -122,23 +160,27 @@ lower_fill_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ co
 
 __global__ void __launch_bounds__(kThreads)
 update_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
-              const int32_t *__restrict__ lrp, const int32_t *__restrict__ lsrc,
+              const int32_t *__restrict__ flag, const int32_t *__restrict__ lrp,
+              const int32_t *__restrict__ lsrc,
               const int32_t *__restrict__ lslot, const uint8_t *__restrict__ keep,
               const int32_t *__restrict__ list, const int32_t *__restrict__ lx, int32_t nlist,
-              int32_t *__restrict__ S, unsigned long long *__restrict__ destroyed) {
+              const int32_t *__restrict__ S, int32_t *__restrict__ S_dec,
+              const int32_t *__restrict__ pos, unsigned long long *__restrict__ destroyed) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t(gridDim.x) * blockDim.x) >> 5;
     unsigned long long mine = 0;
     for (int64_t k = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; k < nlist;
          k += warps) {
-        const int32_t p = __ldg(list + k);
         const int32_t xw = __ldg(lx + k);
+        if (xw == -1) continue;  // graph not updated (warp-uniform: one edge per warp)
+        const int32_t p = __ldg(list + k);
         const int32_t x = xw & 0x7fffffff;
         const bool walk_y = xw < 0;
         const int32_t y = __ldg(col + p);
         const int32_t z = walk_y ? y : x, o = walk_y ? x : y;
         const int32_t zu0 = __ldg(rp + z), zu1 = __ldg(rp + z + 1);
-        const int32_t zl0 = __ldg(lrp + z), zl1 = __ldg(lrp + z + 1);
+        const int32_t zc = flag[z] - 2;  // compact index of the walked endpoint
+        const int32_t zl0 = __ldg(lrp + zc), zl1 = __ldg(lrp + zc + 1);
         const int32_t nu = zu1 - zu0;
         const int32_t total = nu + (zl1 - zl0);
         const int32_t need = __ldg(S + p);
@@ -164,8 +206,8 @@ update_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
                         hit = true;
                         const bool rz = keep[qz] == 0, ro = keep[qo] == 0;
                         if (!((rz && qz < p) || (ro && qo < p))) {
-                            if (!rz) atomicSub(S + qz, 1);
-                            if (!ro) atomicSub(S + qo, 1);
+                            if (!rz) atomicSub(S_dec + (pos ? pos[qz] : qz), 1);
+                            if (!ro) atomicSub(S_dec + (pos ? pos[qo] : qo), 1);
                             ++mine;
                         }
                     }
@@ -183,7 +225,8 @@ update_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
 cudaError_t launch_support_update(const Live &g, const uint8_t *keep, const int32_t *list,
                                   int32_t nlist, int32_t *S, unsigned long long *destroyed,
                                   const UpdateScratch &u, UpdateState *st, cudaStream_t s,
-                                  int *launches) {
+                                  int *launches, const int32_t *pos, int32_t *S_out,
+                                  const uint8_t *upd_g) {
     if (nlist <= 0 || g.m == 0) return cudaSuccess;
     const int64_t rows = int64_t(g.n) + 1;
     auto grid = [](int64_t work, int64_t cap) { return int((work + kThreads - 1) / kThreads < cap
@@ -199,23 +242,30 @@ cudaError_t launch_support_update(const Live &g, const uint8_t *keep, const int3
         ++*launches;
         st->ldeg_valid = true;
     }
-    e = cudaMemsetAsync(st->flag, 0, size_t(g.n), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(u.lcnt, 0, size_t(rows) * 4, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(u.lfill, 0, size_t(rows) * 4, s);
+    // per-list arrays: at most nlist flagged vertices (st->flag is all zero
+    // between calls; the claimed entries are reset at the end)
+    const int64_t zcap = int64_t(nlist) + 1;
+    e = cudaMemsetAsync(st->nz, 0, 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(u.lcnt, 0, size_t(zcap) * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(u.lfill, 0, size_t(zcap) * 4, s);
     if (e != cudaSuccess) return e;
     pick_kernel<<<grid(nlist, 152 * 16), kThreads, 0, s>>>(g.rp, g.col, g.n, st->ldeg, list, nlist,
-                                                            st->flag, u.lx);
+                                                            st->flag, u.lx, g.gid, upd_g);
+    claim_kernel<<<grid(nlist, 152 * 16), kThreads, 0, s>>>(g.col, list, u.lx, nlist, st->flag,
+                                                             u.zlist, st->nz);
     lower_count_kernel<<<grid(g.m, 152 * 16), kThreads, 0, s>>>(g.col, g.m, st->flag, u.lcnt);
-    *launches += 2;
-    e = launch_scan_i32(u.lcnt, u.lrp, rows, u, s, launches);
+    *launches += 3;
+    e = launch_scan_i32(u.lcnt, u.lrp, zcap, u, s, launches);
     if (e != cudaSuccess) return e;
     const int64_t fblocks =
         (int64_t(g.m) + int64_t(kThreads) * kSlotsPerThread - 1) / (int64_t(kThreads) * kSlotsPerThread);
     lower_fill_kernel<<<int(fblocks), kThreads, 0, s>>>(g.rp, g.col, g.n, g.m, st->flag, u.lrp,
                                                         u.lfill, u.lsrc, u.lslot);
     update_kernel<<<grid(int64_t(nlist) * 32, 152 * 32), kThreads, 0, s>>>(
-        g.rp, g.col, u.lrp, u.lsrc, u.lslot, keep, list, u.lx, nlist, S, destroyed);
-    *launches += 2;
+        g.rp, g.col, st->flag, u.lrp, u.lsrc, u.lslot, keep, list, u.lx, nlist, S,
+        pos ? S_out : S, pos, destroyed);
+    unflag_kernel<<<grid(nlist, 152 * 16), kThreads, 0, s>>>(u.zlist, st->nz, nlist, st->flag);
+    *launches += 3;
     return cudaGetLastError();
 }
 
