@@ -329,12 +329,12 @@ def main():
                          "recomputed every round (never, Alg. 1 as written)")
     ap.add_argument("--serve-requests", type=int, default=64,
                     help="requests of the serving measurement (0 = skip)")
-    ap.add_argument("--serve-mmax", type=float, default=1e6,
-                    help="largest request size (edges) of the serving measurement; the full "
-                         "serving workload uses 5e7")
-    ap.add_argument("--batch-mmax", type=float, default=1e5,
-                    help="largest graph size (edges) of that batch; the full batching "
-                         "workload uses 2e6")
+    ap.add_argument("--serve-mmax", type=float, default=5e7,
+                    help="largest request size (edges) of the serving measurement (the "
+                         "serving workload: 5e7)")
+    ap.add_argument("--batch-mmax", type=float, default=2e6,
+                    help="largest graph size (edges) of that batch (the batching workload: "
+                         "2e6)")
     ap.add_argument("--ref-scale", type=int, default=CPU_SAMPLE_SCALE,
                     help="R-MAT scale of the oracle sample timed by --impl reference")
     args = ap.parse_args()

@@ -76,6 +76,13 @@ extern "C" {
 #define KTRUSS_OPT_SUPPORT_KERNEL 1 /* KTRUSS_KERNEL_* */
 #define KTRUSS_OPT_TIMING 2         /* 1 = record per-phase CUDA events (default 1) */
 #define KTRUSS_OPT_UPDATE 3         /* KTRUSS_UPDATE_* */
+#define KTRUSS_OPT_LIGHT_MERGE 4    /* balanced step: tasks whose two lists (tail of row i,
+                                       row kappa) hold at most this many columns together
+                                       are merged by one thread instead of being staged
+                                       and probed; 0..1024, default 64 */
+#define KTRUSS_OPT_SMALL_EDGES 5    /* KTRUSS_KERNEL_AUTO: live graphs with fewer edges use
+                                       the one-thread-per-edge kernel; >= 0, default
+                                       131072 */
 
 typedef struct ktruss_graph ktruss_graph; /* opaque, library-owned */
 
@@ -265,6 +272,31 @@ int ktruss_stats(const ktruss_graph *g, ktruss_stats_t *out);
 /* Sets a KTRUSS_OPT_* option on a handle.  KTRUSS_EINVAL for an unknown key
  * or value. */
 int ktruss_set_option(ktruss_graph *g, int32_t key, int64_t value);
+
+/* Settings chosen by ktruss_autotune. */
+typedef struct {
+    int32_t light_merge;  /* KTRUSS_OPT_LIGHT_MERGE */
+    int64_t small_edges;  /* KTRUSS_OPT_SMALL_EDGES */
+    int32_t update_mode;  /* KTRUSS_OPT_UPDATE */
+    float ms;             /* device time of the best run (ms) */
+    int32_t trials;       /* runs timed */
+} ktruss_tune_t;
+
+/*
+ * Autotuner: picks KTRUSS_OPT_LIGHT_MERGE (merge or stage-and-probe, by list
+ * length), KTRUSS_OPT_SMALL_EDGES (per-edge or balanced kernel, by live size)
+ * and KTRUSS_OPT_UPDATE for this handle's graph by timing whole runs on it:
+ * ktruss_run with K[0] when num_K == 1, or ktruss_run_batch with K[0..G) when
+ * the handle is a batch of G graphs and num_K == G.  Candidates are tried one
+ * option at a time (coordinate descent from the current settings), each run
+ * reps times (best time counts); the best settings are left set on the
+ * handle and copied to *out (may be NULL).  Results of the runs are discarded
+ * (device buffers owned by the handle).  The support kernel choice
+ * (KTRUSS_OPT_SUPPORT_KERNEL) is left as set.  Errors as ktruss_run /
+ * ktruss_run_batch; KTRUSS_EINVAL for bad num_K or reps < 1.
+ */
+int ktruss_autotune(ktruss_graph *g, const int32_t *K, int32_t num_K, int32_t reps,
+                    ktruss_tune_t *out, void *cuda_stream);
 
 /* Vertex and edge counts of a loaded handle.  KTRUSS_EINVAL for NULL. */
 int ktruss_graph_size(const ktruss_graph *g, int32_t *n, int64_t *m);

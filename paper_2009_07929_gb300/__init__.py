@@ -29,7 +29,7 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBUSY = 0, -1, -2, -3, -4, -5
 HOST, DEVICE = 0, 1
 KERNEL_BALANCED, KERNEL_EDGE, KERNEL_COARSE, KERNEL_AUTO = 0, 1, 2, 3
 UPDATE_NEVER, UPDATE_ALWAYS, UPDATE_AUTO = 0, 1, 2
-OPT_SUPPORT_KERNEL, OPT_TIMING, OPT_UPDATE = 1, 2, 3
+OPT_SUPPORT_KERNEL, OPT_TIMING, OPT_UPDATE, OPT_LIGHT_MERGE, OPT_SMALL_EDGES = 1, 2, 3, 4, 5
 
 _lib = None
 
@@ -64,6 +64,16 @@ class _Stats(ctypes.Structure):
         ("kernel_launches", ctypes.c_int32),
         ("updated_per_round", ctypes.POINTER(ctypes.c_int32)),
         ("ms_update", ctypes.c_float),
+    ]
+
+
+class _Tune(ctypes.Structure):
+    _fields_ = [
+        ("light_merge", ctypes.c_int32),
+        ("small_edges", ctypes.c_int64),
+        ("update_mode", ctypes.c_int32),
+        ("ms", ctypes.c_float),
+        ("trials", ctypes.c_int32),
     ]
 
 
@@ -108,6 +118,8 @@ def lib():
         L.ktruss_decompose.restype = ctypes.c_int
         L.ktruss_stats.argtypes = [vp, ctypes.POINTER(_Stats)]
         L.ktruss_set_option.argtypes = [vp, i32, i64]
+        L.ktruss_autotune.argtypes = [vp, vp, i32, i32, ctypes.POINTER(_Tune), vp]
+        L.ktruss_autotune.restype = ctypes.c_int
         L.ktruss_graph_size.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i64)]
         L.ktruss_free.argtypes = [vp]
         L.ktruss_free.restype = None
@@ -202,6 +214,18 @@ class Graph:
 
     def set_kernel(self, kernel: int):
         self.set_option(OPT_SUPPORT_KERNEL, kernel)
+
+    def autotune(self, K, reps: int = 2, stream=None) -> dict:
+        """ktruss_autotune: times whole runs of this graph (K an int) or batch
+        (K one value per graph) with candidate light-merge thresholds, AUTO
+        kernel thresholds and update modes, leaves the fastest set on the
+        handle and returns them."""
+        Ks = np.ascontiguousarray(np.atleast_1d(np.asarray(K, dtype=np.int32)))
+        t = _Tune()
+        _check(lib().ktruss_autotune(self._h, Ks.ctypes.data, Ks.shape[0], reps, ctypes.byref(t),
+                                     _stream_ptr(stream)), "ktruss_autotune")
+        return {"light_merge": t.light_merge, "small_edges": t.small_edges,
+                "update_mode": t.update_mode, "ms": t.ms, "trials": t.trials}
 
     def set_update(self, mode: int):
         """UPDATE_NEVER (recompute S every round, Alg. 1 as written),

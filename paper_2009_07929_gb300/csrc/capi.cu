@@ -91,6 +91,10 @@ struct ktruss_graph {
     // options
     int support_kernel = KTRUSS_KERNEL_AUTO;
     int update_mode = KTRUSS_UPDATE_AUTO;
+    // KTRUSS_KERNEL_AUTO: live graphs below this many edges use the
+    // one-thread-per-edge kernel, whose single launch beats the balanced
+    // step's dozen small kernels there
+    int64_t small_edges = int64_t(1) << 17;
     int timing = 1;
     // events: [0] run start, [1] run end, then kEventsPerRound per round
     std::vector<cudaEvent_t> events;
@@ -134,11 +138,6 @@ cudaError_t ensure_events(ktruss_graph *g, size_t count) {
     }
     return cudaSuccess;
 }
-
-// Live graphs below this many edges use the one-thread-per-edge kernel under
-// KTRUSS_KERNEL_AUTO: the balanced step's fixed cost (a dozen small kernels
-// before the support kernel) dominates there.
-constexpr int32_t kAutoSmallEdges = 1 << 17;
 
 // Per-round events: [0] before the support step, [1] balance done, [2] support
 // done, [3] prune + counter read done, [4] update done, [5] compaction or
@@ -224,7 +223,7 @@ void clear_round_stats(ktruss_graph *g) {
 cudaError_t support_step(ktruss_graph *g, const kt::Live &cur, int32_t *S, cudaStream_t s,
                          int *launches, cudaEvent_t *ev) {
     int k = g->support_kernel;
-    if (k == KTRUSS_KERNEL_AUTO) k = cur.m < kAutoSmallEdges ? KTRUSS_KERNEL_EDGE : KTRUSS_KERNEL_BALANCED;
+    if (k == KTRUSS_KERNEL_AUTO) k = cur.m < g->small_edges ? KTRUSS_KERNEL_EDGE : KTRUSS_KERNEL_BALANCED;
     if (k == KTRUSS_KERNEL_BALANCED) {
         int l = 0;
         cudaError_t e = kt::launch_support_balanced(cur, S, g->cnt, &g->bs, s, &l, ev);
@@ -578,6 +577,14 @@ int ktruss_set_option(ktruss_graph *g, int32_t key, int64_t value) {
                 return KTRUSS_EINVAL;
             g->update_mode = int(value);
             return KTRUSS_OK;
+        case KTRUSS_OPT_LIGHT_MERGE:
+            if (value < 0 || value > kt::kMaxLight) return KTRUSS_EINVAL;
+            g->bs.light = int32_t(value);
+            return KTRUSS_OK;
+        case KTRUSS_OPT_SMALL_EDGES:
+            if (value < 0) return KTRUSS_EINVAL;
+            g->small_edges = value;
+            return KTRUSS_OK;
         default:
             return KTRUSS_EINVAL;
     }
@@ -820,6 +827,91 @@ int ktruss_decompose(ktruss_graph *g, int32_t *trussness_out, int32_t *kmax_out,
     if (kmax_out) *kmax_out = m == 0 ? 0 : K - 1;
     fill_stats(g, rounds, 0, 0, timing ? elapsed(g->events[0], g->events[1]) : 0.f, 0.f, 0.f,
                0.f, 0.f, 0.f, support_launches, launches);
+    return KTRUSS_OK;
+}
+
+int ktruss_autotune(ktruss_graph *g, const int32_t *K, int32_t num_K, int32_t reps,
+                    ktruss_tune_t *out, void *cuda_stream) {
+    if (!g || !K || reps < 1) return KTRUSS_EINVAL;
+    const bool batch = g->G > 0 && num_K == g->G;
+    if (!batch && num_K != 1) return KTRUSS_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    // device outputs owned by the handle
+    uint8_t *mask_d = nullptr;
+    int32_t *sup_d = nullptr;
+    KT_CK(host_outputs(g, KTRUSS_HOST, true, &mask_d, &sup_d));
+    KT_CK(ensure_events(g, 2));
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    KT_CK(cudaEventCreate(&t0));
+    cudaError_t ce = cudaEventCreate(&t1);
+    if (ce != cudaSuccess) {
+        cudaEventDestroy(t0);
+        return map_cuda(ce);
+    }
+    int32_t trials = 0;
+    int rc = KTRUSS_OK;
+    // best time of reps runs with the handle's current settings
+    auto measure = [&](float *best) -> int {
+        *best = 3.0e38f;
+        for (int32_t r = 0; r < reps; ++r) {
+            cudaError_t e = cudaEventRecord(t0, s);
+            if (e != cudaSuccess) return map_cuda(e);
+            const int code = batch ? ktruss_run_batch(g, K, mask_d, sup_d, nullptr,
+                                                      KTRUSS_DEVICE, cuda_stream)
+                                   : ktruss_run(g, K[0], mask_d, sup_d, KTRUSS_DEVICE,
+                                                cuda_stream);
+            if (code != KTRUSS_OK) return code;
+            e = cudaEventRecord(t1, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+            if (e != cudaSuccess) return map_cuda(e);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, t0, t1);
+            *best = ms < *best ? ms : *best;
+            ++trials;
+        }
+        return KTRUSS_OK;
+    };
+    float best = 0.f;
+    rc = measure(&best);  // first call also warms up
+    if (rc == KTRUSS_OK) rc = measure(&best);
+    // one option at a time, keeping the best value of each
+    const int64_t lights[] = {0, 32, 64, 128, 256};
+    const int64_t smalls[] = {int64_t(1) << 15, int64_t(1) << 17, int64_t(1) << 19,
+                              int64_t(1) << 21};
+    const int64_t updates[] = {KTRUSS_UPDATE_AUTO, KTRUSS_UPDATE_NEVER, KTRUSS_UPDATE_ALWAYS};
+    struct Axis {
+        int32_t key;
+        const int64_t *vals;
+        int count;
+        int64_t cur;
+    } axes[] = {{KTRUSS_OPT_LIGHT_MERGE, lights, 5, g->bs.light},
+                {KTRUSS_OPT_SMALL_EDGES, smalls, 4, g->small_edges},
+                {KTRUSS_OPT_UPDATE, updates, 3, g->update_mode}};
+    for (Axis &ax : axes) {
+        if (rc != KTRUSS_OK) break;
+        int64_t keep_val = ax.cur;
+        for (int i = 0; i < ax.count && rc == KTRUSS_OK; ++i) {
+            if (ax.vals[i] == ax.cur) continue;
+            ktruss_set_option(g, ax.key, ax.vals[i]);
+            float t = 0.f;
+            rc = measure(&t);
+            if (rc == KTRUSS_OK && t < best) {
+                best = t;
+                keep_val = ax.vals[i];
+            }
+        }
+        ktruss_set_option(g, ax.key, keep_val);
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    if (rc != KTRUSS_OK) return rc;
+    if (out) {
+        out->light_merge = g->bs.light;
+        out->small_edges = g->small_edges;
+        out->update_mode = g->update_mode;
+        out->ms = best;
+        out->trials = trials;
+    }
     return KTRUSS_OK;
 }
 

@@ -45,6 +45,11 @@ constexpr int32_t kDevErrInternal = 2;  // an internal consistency check failed
 
 constexpr int kWarp = 32;
 
+// Default light-task threshold of the balanced support step (see
+// BalancedScratch::light); chosen by a sweep on R-MAT and G(n,m) graphs.
+constexpr int32_t kDefaultLight = 64;
+constexpr int32_t kMaxLight = 1024;
+
 // KTRUSS_TRACE=2 (or more): the launchers synchronise the stream after each
 // phase and print its name and the time since the process loaded the library
 // on stderr (a debugging aid; off by default).
@@ -74,6 +79,9 @@ struct BalancedScratch {
     int64_t cap_m = 0;      // capacity in edges
     int64_t cap_tasks = 0;  // long-row task capacity
     int32_t cap_n = 0;
+    // tasks whose two lists hold at most `light` columns together are merged
+    // by one thread instead of being staged and probed (0 = none)
+    int32_t light = kDefaultLight;
 };
 
 // Bytes of device scratch BalancedScratch needs for a graph of n vertices and

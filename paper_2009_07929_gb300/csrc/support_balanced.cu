@@ -30,7 +30,7 @@
 //    every probe is still read once.  Credits to staged slots are gathered in
 //    shared memory and flushed once per stage or piece.
 //
-// Light tasks (t + d <= kLight) skip all of the above: one thread merges the
+// Light tasks (t + d <= light) skip all of the above: one thread merges the
 // two short lists (support_light_kernel), which costs less than giving them a
 // segment.  Which tasks are light is decided by the same test in both kernels.
 //
@@ -79,15 +79,13 @@ constexpr int kScanPer = 16;
 constexpr int kScanTile = kScanThreads * kScanPer;
 constexpr int kEdgeThreads = 256;
 constexpr int kEdgesPerThread = 16;
-#ifndef KT_SUPPORT_LIGHT
-#define KT_SUPPORT_LIGHT 64
-#endif
-// Tasks whose two lists hold at most kLight columns together are merged by one
-// thread (support_light_kernel) instead of being staged and probed.
-constexpr int32_t kLight = KT_SUPPORT_LIGHT;
 constexpr int kLightPerThread = 4;
 
-__device__ __forceinline__ bool light_task(int32_t t, int32_t d) { return t + d <= kLight; }
+// Tasks whose two lists hold at most `light` columns together are merged by
+// one thread (support_light_kernel) instead of being staged and probed.
+__device__ __forceinline__ bool light_task(int32_t t, int32_t d, int32_t light) {
+    return t + d <= light;
+}
 
 constexpr int32_t kIntMax = 0x7fffffff;
 
@@ -360,7 +358,7 @@ classify_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
                 int32_t m, int32_t *__restrict__ ekey, int32_t *__restrict__ epst,
                 int32_t *__restrict__ eitems, int32_t *__restrict__ rcount,
                 unsigned long long *__restrict__ merge_work, const int32_t *__restrict__ gid,
-                const uint8_t *__restrict__ skip) {
+                const uint8_t *__restrict__ skip, int32_t light) {
     __shared__ long long part[kEdgeThreads / 32];
     const int lane = threadIdx.x & 31;
     const int64_t e0 = (int64_t(blockIdx.x) * kEdgeThreads + threadIdx.x) * kEdgesPerThread;
@@ -379,7 +377,7 @@ classify_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
             const int32_t t = rw.rend - int32_t(e) - 1;
             const bool skipped = skip && skip[gid[rw.row]];
             if (!skipped) merge += (long long)t + d;
-            const int32_t items = (skipped || light_task(t, d)) ? 0 : min(t, d);
+            const int32_t items = (skipped || light_task(t, d, light)) ? 0 : min(t, d);
             if (items > 0) {
                 const bool stage_kappa = t < d;
                 key = stage_kappa ? kappa : rw.row;
@@ -407,7 +405,8 @@ classify_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
 __global__ void __launch_bounds__(kEdgeThreads)
 support_light_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, int32_t n,
                      int32_t m, int32_t *__restrict__ S, unsigned long long *__restrict__ tri,
-                     const int32_t *__restrict__ gid, const uint8_t *__restrict__ skip) {
+                     const int32_t *__restrict__ gid, const uint8_t *__restrict__ skip,
+                     int32_t light) {
     const int64_t e0 = (int64_t(blockIdx.x) * kEdgeThreads + threadIdx.x) * kLightPerThread;
     int32_t found = 0;
     if (e0 < m) {
@@ -423,7 +422,7 @@ support_light_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__
             const int32_t ye = __ldg(rp + kappa + 1);
             int32_t x = int32_t(e) + 1;
             const int32_t xe = rw.rend;
-            if (x >= xe || y >= ye || !light_task(xe - x, ye - y)) continue;
+            if (x >= xe || y >= ye || !light_task(xe - x, ye - y, light)) continue;
             if (skip && skip[gid[rw.row]]) continue;
             int32_t own = 0;
             while (x < xe && y < ye) {
@@ -1201,7 +1200,8 @@ cudaError_t launch_support_balanced(const Live &g, int32_t *S, RoundCounters *cn
     const int eblocks = int((int64_t(m) + kEdgeThreads * kEdgesPerThread - 1) /
                             (kEdgeThreads * kEdgesPerThread));
     classify_kernel<<<eblocks, kEdgeThreads, 0, s>>>(g.rp, g.col, n, m, c.ekey, c.epst, c.eitems,
-                                                     c.rcount, &cnt->merge_work, g.gid, g.skip);
+                                                     c.rcount, &cnt->merge_work, g.gid, g.skip,
+                                                     bs->light);
     trace_phase(s, "classify");
     // row scan: segment starts and active-row ranks (row n has count 0, so the
     // entries at n are the totals)
@@ -1248,11 +1248,13 @@ cudaError_t launch_support_balanced(const Live &g, int32_t *S, RoundCounters *cn
         e = cudaEventRecord(ev[1], s);
         if (e != cudaSuccess) return e;
     }
-    const int64_t lblocks = (int64_t(m) + int64_t(kEdgeThreads) * kLightPerThread - 1) /
-                            (int64_t(kEdgeThreads) * kLightPerThread);
-    support_light_kernel<<<int(lblocks), kEdgeThreads, 0, s>>>(g.rp, g.col, n, m, S,
-                                                              &cnt->triangles, g.gid, g.skip);
-    *launches += 1;
+    if (bs->light > 0) {
+        const int64_t lblocks = (int64_t(m) + int64_t(kEdgeThreads) * kLightPerThread - 1) /
+                                (int64_t(kEdgeThreads) * kLightPerThread);
+        support_light_kernel<<<int(lblocks), kEdgeThreads, 0, s>>>(
+            g.rp, g.col, n, m, S, &cnt->triangles, g.gid, g.skip, bs->light);
+        *launches += 1;
+    }
     SupportArgs A{g.rp, g.col, c.seg, c.pst, c.sact, c.wp, c.arow, c.aseg, c.plan, c.bound,
                   c.sched, S, &cnt->triangles, &cnt->error};
     support_kernel<<<g_support_blocks, kThreads, sizeof(SupportSmem), s>>>(A);

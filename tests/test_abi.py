@@ -50,6 +50,10 @@ def test_argument_checks_before_any_cuda_call():
     assert L.ktruss_run(None, 3, None, None, kt.DEVICE, None) == kt.EINVAL
     assert L.ktruss_stats(None, None) == kt.EINVAL
     assert L.ktruss_set_option(None, kt.OPT_TIMING, 1) == kt.EINVAL
+    assert L.ktruss_set_option(None, kt.OPT_LIGHT_MERGE, 64) == kt.EINVAL
+    assert L.ktruss_autotune(None, None, 1, 1, None, None) == kt.EINVAL
+    assert L.ktruss_server_set_option(None, kt.OPT_UPDATE, 2) == kt.EINVAL
+    assert L.ktruss_decompose(None, None, None, kt.DEVICE, None) == kt.EINVAL
     L.ktruss_free(None)
 
 

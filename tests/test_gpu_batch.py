@@ -99,6 +99,25 @@ def test_batch_handle_runs_single_K_and_decompose(kt):
     h.close()
 
 
+def test_batch_autotune(kt):
+    import torch
+    gs, Ks = mixed_small_graphs()
+    vo, rp, col, eo = kt.concat_graphs(gs)
+    h = kt.load_batch(vertex_offsets=vo, row_ptr=torch.from_numpy(rp).cuda(),
+                      col=torch.from_numpy(col).cuda())
+    t = h.autotune(Ks, reps=1)
+    assert t["trials"] >= 10
+    mask, sup, rounds = h.run_batch(Ks)
+    torch.cuda.synchronize()
+    mask, sup = mask.cpu().numpy(), sup.cpu().numpy()
+    for k, (g, K) in enumerate(zip(gs, Ks)):
+        r = oracle.ktruss(g.row_ptr, g.col, K)
+        assert np.array_equal(mask[eo[k]:eo[k + 1]], r.mask), k
+        assert np.array_equal(sup[eo[k]:eo[k + 1]], r.support), k
+        assert rounds[k] == r.rounds, k
+    h.close()
+
+
 def test_batch_rejects_edges_across_graphs(kt):
     g = gg.from_edges(4, [(0, 1), (1, 2), (0, 2), (2, 3)])
     # vertices {0,1} and {2,3} declared as two graphs: edge (1,2) crosses

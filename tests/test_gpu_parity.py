@@ -300,6 +300,40 @@ def test_support_optional(kt):
     h.close()
 
 
+# ------------------------------------------------ autotuner
+
+def test_autotune_picks_candidates_and_keeps_results(kt):
+    import torch
+    for g, K in ((gg.rmat(14, 16, 4), 4), (gg.er(20000, 300000, 2), 3)):
+        h = kt.load(torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col).cuda())
+        t = h.autotune(K, reps=1)
+        assert t["light_merge"] in (0, 32, 64, 128, 256)
+        assert t["small_edges"] in (1 << 15, 1 << 17, 1 << 19, 1 << 21)
+        assert t["update_mode"] in (0, 1, 2) and t["trials"] >= 10 and t["ms"] > 0
+        r = oracle.ktruss(g.row_ptr, g.col, K)
+        m_t, s_t = h.run(K)
+        torch.cuda.synchronize()
+        assert np.array_equal(m_t.cpu().numpy(), r.mask)
+        assert np.array_equal(s_t.cpu().numpy(), r.support)
+        assert h.stats().rounds == r.rounds
+        h.close()
+
+
+@pytest.mark.parametrize("light", [0, 16, 256, 1024])
+def test_light_merge_thresholds(kt, light):
+    import torch
+    for g, K in ((gg.rmat(13, 16, 6), 5), (gg.er(4000, 60000, 3), 3), (gg.book(300), 3)):
+        h = kt.load(torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col).cuda())
+        h.set_kernel(0)
+        h.set_option(kt.OPT_LIGHT_MERGE, light)
+        r = oracle.ktruss(g.row_ptr, g.col, K)
+        m_t, s_t = h.run(K)
+        torch.cuda.synchronize()
+        assert np.array_equal(m_t.cpu().numpy(), r.mask)
+        assert np.array_equal(s_t.cpu().numpy(), r.support)
+        h.close()
+
+
 # ------------------------------------------------ truss decomposition
 
 @pytest.mark.parametrize("kernel,update", [(k, None) for k in KERNELS] + [(3, u) for u in UPDATES])
