@@ -149,9 +149,10 @@ def algorithmic_bytes(n, live, merge, tris):
     return 4 * merge + 8 * live + 16 * tris + 8 * (n + 1)
 
 
-def traffic_record():
+def traffic_record(workload, K):
     """Per-launch DRAM traffic of the support step from the committed ncu
-    summary, if it was taken on the current kernel source (else None)."""
+    summary, if it was taken on the current kernel source and on this workload
+    and K (else None)."""
     p = os.path.join(ROOT, "profiles", "support_traffic.json")
     try:
         with open(p) as f:
@@ -161,7 +162,7 @@ def traffic_record():
     src = os.path.join(ROOT, "paper_2009_07929_gb300", "csrc", "support_balanced.cu")
     with open(src, "rb") as f:
         h = hashlib.sha256(f.read()).hexdigest()
-    if rec.get("source_sha256") != h:
+    if rec.get("source_sha256") != h or rec.get("workload") != f"{workload} K={K} round 1":
         return None
     return rec
 
@@ -483,7 +484,7 @@ def main():
     sup_avg_ms = sup_ms / max(sup_launches, 1)
     bytes_per_launch = bytes_alg / max(sup_launches, 1)
     achieved = bytes_per_launch / (sup_avg_ms / 1000.0) / 1e9 if sup_avg_ms > 0 else None
-    tr = traffic_record()
+    tr = traffic_record(args.workload, args.K)
     roofline = {
         "bound": "hbm", "achieved": round(achieved, 1) if achieved else None, "peak": peak,
         "unit": "GB/s", "frac": round(achieved / peak, 4) if achieved else None,
