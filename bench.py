@@ -500,6 +500,10 @@ def main():
     if tr:
         roofline["dram_frac"] = round(tr["dram_bytes_per_launch"] / (sup_avg_ms / 1e3) / 1e9 / peak, 4)
         roofline["traffic_workload"] = tr.get("workload")
+        if "sm_issue_active" in tr:
+            # what bounds the kernel: SM instruction issue (fraction of issue
+            # slots active, ncu), not HBM bandwidth (dram_frac)
+            roofline["sm_issue_active"] = tr["sm_issue_active"]
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tot_ms / args.steps, 4),
