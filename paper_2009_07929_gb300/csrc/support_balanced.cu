@@ -64,7 +64,10 @@ constexpr int kStageRows = 256;         // staged rows per stage
 constexpr int kWarps = kThreads / 32;
 constexpr int kBatch = kThreads;        // segments per batch (one per thread)
 constexpr int kUnroll = KT_SUPPORT_UNROLL;  // 32-item windows in flight per warp
-constexpr int kMixUnroll = 2;           // run-crossing windows in flight per warp
+#ifndef KT_SUPPORT_MIX_UNROLL
+#define KT_SUPPORT_MIX_UNROLL 2
+#endif
+constexpr int kMixUnroll = KT_SUPPORT_MIX_UNROLL;  // run-crossing windows in flight per warp
 #ifndef KT_SUPPORT_GRAIN
 #define KT_SUPPORT_GRAIN 0
 #endif

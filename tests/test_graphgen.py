@@ -57,3 +57,30 @@ def test_counter_rng_is_pure():
     assert gg.rand_u64(k, 5) != gg.rand_u64(k, 6)
     # SplitMix64 reference value: output function applied to state 0 + golden gamma
     assert gg.rand_u64(0, 0) == 0xE220A8397B1DCDAF
+
+
+def _digest(pairs):
+    import hashlib
+    h = hashlib.sha256()
+    for g, K in pairs:
+        h.update(np.ascontiguousarray(g.row_ptr, dtype="<i4").tobytes())
+        h.update(np.ascontiguousarray(g.col, dtype="<i4").tobytes())
+        h.update(int(K).to_bytes(4, "little"))
+    return h.hexdigest()
+
+
+def test_batch_and_serve_workloads_are_deterministic_and_in_range():
+    # the graphs are built on a thread pool: the result must not depend on it
+    b1 = gg.batch_config(48, seed=3, m_lo=1e3, m_hi=3e4)
+    b2 = gg.batch_config(48, seed=3, m_lo=1e3, m_hi=3e4)
+    assert _digest(b1) == _digest(b2)
+    for k, (g, K) in enumerate(b1):
+        assert 3 <= K <= 12
+        assert g.row_ptr[0] == 0 and g.row_ptr[-1] == g.m
+        if k % 2 == 0:  # G(n, m): exactly the drawn size
+            assert 1e3 <= g.m <= 3e4 + 1
+    s1 = gg.serve_config(12, seed=4, m_lo=1e4, m_hi=1e5)
+    s2 = gg.serve_config(12, seed=4, m_lo=1e4, m_hi=1e5)
+    assert _digest(s1) == _digest(s2)
+    assert all(3 <= K <= 16 for _, K in s1)
+    assert _digest(gg.batch_config(48, seed=5, m_lo=1e3, m_hi=3e4)) != _digest(b1)
