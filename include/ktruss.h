@@ -301,8 +301,15 @@ int ktruss_autotune(ktruss_graph *g, const int32_t *K, int32_t num_K, int32_t re
 /* Vertex and edge counts of a loaded handle.  KTRUSS_EINVAL for NULL. */
 int ktruss_graph_size(const ktruss_graph *g, int32_t *n, int64_t *m);
 
-/* Releases a handle and all device memory it owns (NULL is a no-op). */
+/* Releases a handle (NULL is a no-op).  Its device memory (one block per
+ * load, plus one for host-kind outputs) goes to a per-process cache of at most
+ * 16 GiB, reused by later loads that need between half and all of a cached
+ * block; an allocation that fails empties the cache and retries. */
 void ktruss_free(ktruss_graph *g);
+
+/* Frees every device block held by the cache of ktruss_free.  Returns
+ * KTRUSS_OK. */
+int ktruss_trim_cache(void);
 
 /* Static string naming a KTRUSS_* code. */
 const char *ktruss_strerror(int code);

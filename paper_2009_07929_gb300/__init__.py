@@ -120,6 +120,8 @@ def lib():
         L.ktruss_set_option.argtypes = [vp, i32, i64]
         L.ktruss_autotune.argtypes = [vp, vp, i32, i32, ctypes.POINTER(_Tune), vp]
         L.ktruss_autotune.restype = ctypes.c_int
+        L.ktruss_trim_cache.argtypes = []
+        L.ktruss_trim_cache.restype = ctypes.c_int
         L.ktruss_graph_size.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i64)]
         L.ktruss_free.argtypes = [vp]
         L.ktruss_free.restype = None
@@ -478,6 +480,12 @@ def serve_poisson(server, requests, rate, seed=0, clock=None):
             results[k] = (r, mask, sup)
             done += 1
     return latency, clock() - t0, results
+
+
+def trim_cache():
+    """ktruss_trim_cache: frees the device blocks that freed handles left in
+    the library's cache."""
+    _check(lib().ktruss_trim_cache(), "ktruss_trim_cache")
 
 
 NOALLOC_MAX_VERTICES = 1 << 19

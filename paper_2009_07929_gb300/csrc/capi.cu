@@ -15,6 +15,7 @@
 
 #include <atomic>
 #include <chrono>
+#include <mutex>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -43,24 +44,163 @@ int map_cuda(cudaError_t e) {
         if (e_ != cudaSuccess) return map_cuda(e_);  \
     } while (0)
 
-// Allocation with an optional simulated failure, for the out-of-memory tests:
-// KTRUSS_TEST_FAIL_ALLOC=N makes the (N+1)-th device allocation of a load fail.
+// Device blocks of freed handles, kept per device (at most kCacheBytes in
+// total) and handed to later loads that need between half and all of a
+// block, so that a load-run-free cycle does not pay cudaMalloc and cudaFree
+// each time.  A cudaMalloc that fails empties the cache and retries once;
+// ktruss_trim_cache empties it on request.
+class BlockCache {
+  public:
+    static constexpr size_t kCacheBytes = size_t(16) << 30;
+    cudaError_t get(size_t bytes, void **p) {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        {
+            std::lock_guard<std::mutex> lock(mu_);
+            size_t best = blocks_.size();
+            for (size_t i = 0; i < blocks_.size(); ++i) {
+                const Block &b = blocks_[i];
+                if (b.dev == dev && b.bytes >= bytes && b.bytes / 2 <= bytes &&
+                    (best == blocks_.size() || b.bytes < blocks_[best].bytes))
+                    best = i;
+            }
+            if (best < blocks_.size()) {
+                *p = blocks_[best].p;
+                held_ -= blocks_[best].bytes;
+                blocks_.erase(blocks_.begin() + long(best));
+                return cudaSuccess;
+            }
+        }
+        e = cudaMalloc(p, bytes);
+        if (e == cudaErrorMemoryAllocation) {
+            cudaGetLastError();
+            trim();
+            e = cudaMalloc(p, bytes);
+        }
+        return e;
+    }
+    // bytes: the size the block was obtained with (reused blocks keep theirs)
+    void put(void *p, size_t bytes) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess) {
+            std::lock_guard<std::mutex> lock(mu_);
+            if (held_ + bytes <= kCacheBytes) {
+                blocks_.push_back(Block{dev, bytes, p});
+                held_ += bytes;
+                return;
+            }
+        }
+        cudaFree(p);
+    }
+    void trim() {
+        std::vector<Block> out;
+        {
+            std::lock_guard<std::mutex> lock(mu_);
+            out.swap(blocks_);
+            held_ = 0;
+        }
+        for (const Block &b : out) cudaFree(b.p);
+    }
+
+  private:
+    struct Block {
+        int dev;
+        size_t bytes;
+        void *p;
+    };
+    std::mutex mu_;
+    std::vector<Block> blocks_;
+    size_t held_ = 0;
+};
+
+BlockCache &block_cache() {
+    static BlockCache *cache = new BlockCache();  // lives as long as the process
+    return *cache;
+}
+
+// A device block owned by a handle.
+struct Owned {
+    void *p;
+    size_t bytes;
+};
+
+// Device allocation with an optional simulated failure, for the
+// out-of-memory tests: KTRUSS_TEST_FAIL_ALLOC=N makes the (N+1)-th device
+// allocation of a load fail.  A load's buffers are requested one by one
+// (request) and carved out of a single cudaMalloc (commit), so that loading
+// and freeing a graph costs one allocation; alloc() is a request committed at
+// once.
 struct Allocator {
     long budget = -1;
-    std::vector<void *> owned;
+    std::vector<Owned> owned;
+    std::vector<std::pair<void **, size_t>> pending;
+    size_t total = 0;
     Allocator() {
         const char *v = std::getenv("KTRUSS_TEST_FAIL_ALLOC");
         if (v && *v) budget = std::atol(v);
     }
-    cudaError_t alloc(void **p, size_t bytes) {
+    static size_t aligned(size_t b) { return (b + 255) & ~size_t(255); }
+    cudaError_t request(void **p, size_t bytes) {
         *p = nullptr;
         if (budget == 0) return cudaErrorMemoryAllocation;
         if (budget > 0) --budget;
-        cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
-        if (e == cudaSuccess) owned.push_back(*p);
-        return e;
+        pending.emplace_back(p, total);
+        total += aligned(bytes ? bytes : 16);
+        return cudaSuccess;
+    }
+    cudaError_t commit() {
+        if (pending.empty()) return cudaSuccess;
+        void *base = nullptr;
+        cudaError_t e = block_cache().get(total, &base);
+        if (e != cudaSuccess) return e;
+        owned.push_back(Owned{base, total});
+        for (auto &q : pending) *q.first = static_cast<char *>(base) + q.second;
+        pending.clear();
+        total = 0;
+        return cudaSuccess;
+    }
+    cudaError_t alloc(void **p, size_t bytes) {
+        cudaError_t e = request(p, bytes);
+        return e == cudaSuccess ? commit() : e;
     }
 };
+
+// Page-locked host slots for the handles' round-counter mirrors, handed out
+// from blocks of 256 slots under a mutex, so that loading and freeing a graph
+// allocates no page-locked memory.  The blocks live as long as the process.
+class PinnedSlots {
+  public:
+    static constexpr size_t kSlot = 128;
+    void *get() {
+        std::lock_guard<std::mutex> lock(mu_);
+        if (free_.empty()) {
+            void *b = nullptr;
+            if (cudaHostAlloc(&b, kSlot * 256, cudaHostAllocPortable) != cudaSuccess) {
+                cudaGetLastError();
+                return nullptr;
+            }
+            for (int i = 0; i < 256; ++i) free_.push_back(static_cast<char *>(b) + i * kSlot);
+        }
+        void *p = free_.back();
+        free_.pop_back();
+        return p;
+    }
+    void put(void *p) {
+        std::lock_guard<std::mutex> lock(mu_);
+        free_.push_back(p);
+    }
+
+  private:
+    std::mutex mu_;
+    std::vector<void *> free_;
+};
+
+PinnedSlots &pinned_slots() {
+    static PinnedSlots *pool = new PinnedSlots();  // never destroyed: see above
+    return *pool;
+}
+static_assert(2 * sizeof(kt::RoundCounters) <= PinnedSlots::kSlot, "counter mirror slot");
 
 }  // namespace
 
@@ -86,7 +226,7 @@ struct ktruss_graph {
     uint8_t *keep = nullptr, *done = nullptr, *upd_g = nullptr;
     int32_t *listed_g = nullptr;
     kt::UpdateState ust;  // lower degrees and vertex flags of the support update
-    std::vector<void *> owned;
+    std::vector<Owned> owned;
     std::atomic<int> busy{0};
     // options
     int support_kernel = KTRUSS_KERNEL_AUTO;
@@ -122,9 +262,9 @@ struct BusyGuard {
 
 void release(ktruss_graph *g) {
     if (!g) return;
-    for (void *p : g->owned) cudaFree(p);
-    kt::balanced_scratch_free(&g->bs);
-    if (g->cnt_host) cudaFreeHost(g->cnt_host);
+    // device blocks (the balanced scratch is part of one) go back to the cache
+    for (const Owned &o : g->owned) block_cache().put(o.p, o.bytes);
+    if (g->cnt_host) pinned_slots().put(g->cnt_host);
     for (cudaEvent_t e : g->events) cudaEventDestroy(e);
     delete g;
 }
@@ -246,12 +386,15 @@ cudaError_t host_outputs(ktruss_graph *g, int mem_kind, bool want_support, uint8
     if (mem_kind != KTRUSS_HOST || g->m == 0) return cudaSuccess;
     if (!g->d_mask) {
         Allocator al;
-        cudaError_t e = al.alloc((void **)&g->d_mask, size_t(g->m));
-        if (e != cudaSuccess) return e;
-        g->owned.push_back(g->d_mask);
-        e = al.alloc((void **)&g->d_sup, size_t(g->m) * 4);
-        if (e != cudaSuccess) return e;
-        g->owned.push_back(g->d_sup);
+        cudaError_t e = al.request((void **)&g->d_mask, size_t(g->m));
+        if (e == cudaSuccess) e = al.request((void **)&g->d_sup, size_t(g->m) * 4);
+        if (e == cudaSuccess) e = al.commit();
+        if (e != cudaSuccess) {
+            g->d_mask = nullptr;
+            g->d_sup = nullptr;
+            return e;
+        }
+        g->owned.insert(g->owned.end(), al.owned.begin(), al.owned.end());
     }
     *mask_d = g->d_mask;
     *sup_d = want_support ? g->d_sup : nullptr;
@@ -330,7 +473,7 @@ static int load_impl(ktruss_graph **out, int32_t n, int64_t m, const int32_t *ro
     Allocator al;
     int rc = KTRUSS_OK;
     auto A = [&](void **p, size_t bytes) -> bool {
-        cudaError_t e = al.alloc(p, bytes);
+        cudaError_t e = al.request(p, bytes);
         if (e != cudaSuccess) {
             rc = map_cuda(e);
             return false;
@@ -359,18 +502,23 @@ static int load_impl(ktruss_graph **out, int32_t n, int64_t m, const int32_t *ro
              A((void **)&g->listed_g, gb);
         g->G = G;
     }
+    if (ok) ok = A(&g->bs.base, kt::balanced_scratch_bytes(n, m));
+    if (ok) {
+        const cudaError_t ce = al.commit();
+        if (ce != cudaSuccess) {
+            ok = false;
+            rc = map_cuda(ce);
+        }
+    }
     g->owned = al.owned;
     if (!ok) {
         release(g);
         return rc;
     }
-    if (al.budget == 0) {  // simulated failure of the scratch allocation
-        release(g);
-        return KTRUSS_ENOMEM;
-    }
-    cudaError_t e = kt::balanced_scratch_alloc(&g->bs, n, m);
-    if (e == cudaSuccess)
-        e = cudaMallocHost((void **)&g->cnt_host, 2 * sizeof(kt::RoundCounters));
+    g->bs.cap_m = m;
+    g->bs.cap_n = n;
+    g->cnt_host = static_cast<kt::RoundCounters *>(pinned_slots().get());
+    cudaError_t e = g->cnt_host ? cudaSuccess : cudaErrorMemoryAllocation;
     if (e == cudaSuccess) e = cudaGetDevice(&g->device);
     const cudaMemcpyKind kind =
         mem_kind == KTRUSS_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
@@ -548,6 +696,11 @@ int ktruss_run_batch(ktruss_graph *g, const int32_t *K, uint8_t *mask_out, int32
     KT_CK(cudaStreamSynchronize(s));
     fill_stats(g, rounds, 0, 0, timing ? elapsed(g->events[0], g->events[1]) : 0.f, 0.f, 0.f,
                0.f, 0.f, 0.f, support_launches, launches);
+    return KTRUSS_OK;
+}
+
+int ktruss_trim_cache(void) {
+    block_cache().trim();
     return KTRUSS_OK;
 }
 

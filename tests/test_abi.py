@@ -54,6 +54,7 @@ def test_argument_checks_before_any_cuda_call():
     assert L.ktruss_autotune(None, None, 1, 1, None, None) == kt.EINVAL
     assert L.ktruss_server_set_option(None, kt.OPT_UPDATE, 2) == kt.EINVAL
     assert L.ktruss_decompose(None, None, None, kt.DEVICE, None) == kt.EINVAL
+    assert L.ktruss_trim_cache() == kt.OK  # empty cache: no CUDA call
     L.ktruss_free(None)
 
 

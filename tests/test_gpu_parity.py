@@ -300,6 +300,25 @@ def test_support_optional(kt):
     h.close()
 
 
+# ------------------------------------------------ device block cache
+
+def test_freed_blocks_are_reused_and_trimmed(kt):
+    import torch
+    g = gg.rmat(15, 16, 1)
+    r = oracle.ktruss(g.row_ptr, g.col, 4)
+    kt.trim_cache()
+    torch.cuda.synchronize()
+    for cycle in range(3):  # load-run-free cycles reuse the cached block
+        h = kt.load(g.row_ptr, g.col)  # host arrays: no torch allocation
+        mask, sup = h.run_host(4)
+        assert np.array_equal(mask, r.mask) and np.array_equal(sup, r.support), cycle
+        h.close()
+    held = torch.cuda.mem_get_info()[0]
+    kt.trim_cache()
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] > held  # the cached blocks were freed
+
+
 # ------------------------------------------------ autotuner
 
 def test_autotune_picks_candidates_and_keeps_results(kt):
