@@ -70,15 +70,15 @@ cudaError_t launch_support_edge(const Live &g, int32_t *S, RoundCounters *cnt, c
 // Coarse-grained support step (Alg. 2): one thread per row.
 cudaError_t launch_support_coarse(const Live &g, int32_t *S, RoundCounters *cnt, cudaStream_t s);
 
-// Scratch owned by the handle for the balanced support kernel.
-// One device allocation carved into: the int64 work prefix [m+1], tile sums
-// and offsets of its scan, the chunk plan, the chunk boundary table, the
-// long-row task table and the scheduler counters.
+// Scratch owned by the handle for the balanced support step, one block of
+// balanced_scratch_bytes(n, m) carved into: per-edge classification and
+// segment arrays, the int64 item prefix and the tile sums and offsets of its
+// scans, per-row counts and active-row tables, the chunk plan, the chunk
+// boundary table and the scheduler words.
 struct BalancedScratch {
     void *base = nullptr;
-    int64_t cap_m = 0;      // capacity in edges
-    int64_t cap_tasks = 0;  // long-row task capacity
-    int32_t cap_n = 0;
+    int64_t cap_m = 0;  // capacity in edges
+    int32_t cap_n = 0;  // capacity in vertices
     // tasks whose two lists hold at most `light` columns together are merged
     // by one thread instead of being staged and probed (0 = none)
     int32_t light = kDefaultLight;

@@ -1176,7 +1176,6 @@ cudaError_t balanced_scratch_alloc(BalancedScratch *bs, int32_t n, int64_t m) {
     bs->base = p;
     bs->cap_m = m;
     bs->cap_n = n;
-    bs->cap_tasks = 0;
     return cudaSuccess;
 }
 

@@ -319,6 +319,27 @@ def test_freed_blocks_are_reused_and_trimmed(kt):
     assert torch.cuda.mem_get_info()[0] > held  # the cached blocks were freed
 
 
+# ------------------------------------------------ tracing
+
+def test_trace_prints_one_line_per_round():
+    import subprocess
+    import sys
+    code = ("import graphgen as gg, paper_2009_07929_gb300 as kt\n"
+            "g = gg.triangle_strip(60)\n"
+            "h = kt.load(g.row_ptr, g.col)\n"
+            "h.run_host(4)\n"
+            "print(h.stats().rounds)\n")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, KTRUSS_TRACE="1")
+    p = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True,
+                       text=True, timeout=300)
+    assert p.returncode == 0, p.stderr
+    rounds = int(p.stdout.strip().splitlines()[-1])
+    lines = [l for l in p.stderr.splitlines() if l.startswith("[ktruss run] round ")]
+    assert rounds == 2 and len(lines) == rounds
+    assert "round 1 live 117 removed 60" in lines[0]
+
+
 # ------------------------------------------------ autotuner
 
 def test_autotune_picks_candidates_and_keeps_results(kt):
