@@ -248,7 +248,9 @@ def measure_serving(kt, gg, count, m_hi, seed=0):
     """Serving workload (graphgen.serve_config: R-MAT or G(n,m) with p = 1/2,
     sizes log-uniform in [1e4, m_hi] edges, K uniform in 3..16) through the
     request server: first all requests at once (saturated graphs/s), then
-    Poisson arrivals at 70% of that rate (p50/p99 latency, graphs/s)."""
+    Poisson arrivals at 70% of that rate (p50/p99 latency, graphs/s).  For
+    comparison the same requests one after another through the plain path,
+    host arrays in and out as the server's are: load, run, free per request."""
     progress(f"serving: generating {count} requests, m up to {m_hi:g}")
     reqs = gg.serve_config(count, seed=seed, m_lo=1e4, m_hi=m_hi)
     edges = sum(g.m for g, _ in reqs)
@@ -271,9 +273,18 @@ def measure_serving(kt, gg, count, m_hi, seed=0):
     srv = server()
     lat, mk, _ = kt.serve_poisson(srv, reqs, rate=0.7 * sat, seed=seed + 1)
     srv.close()
+    progress("serving: plain path, one request after another")
+    t0 = time.perf_counter()
+    for g, K in reqs:
+        h = kt.load(g.row_ptr, g.col)
+        h.run_host(K)
+        h.close()
+    plain = count / (time.perf_counter() - t0)
     import numpy as np
     return {"requests": count, "edges": int(edges), "m_range": [10000, int(m_hi)],
-            "saturated_graphs_per_s": round(sat, 2), "arrival_rate": round(0.7 * sat, 2),
+            "saturated_graphs_per_s": round(sat, 2),
+            "plain_graphs_per_s": round(plain, 2), "saturated_vs_plain": round(sat / plain, 2),
+            "arrival_rate": round(0.7 * sat, 2),
             "graphs_per_s": round(count / mk, 2),
             "p50_latency_ms": round(float(np.percentile(lat, 50)) * 1e3, 3),
             "p99_latency_ms": round(float(np.percentile(lat, 99)) * 1e3, 3)}
