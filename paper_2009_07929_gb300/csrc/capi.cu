@@ -44,81 +44,6 @@ int map_cuda(cudaError_t e) {
         if (e_ != cudaSuccess) return map_cuda(e_);  \
     } while (0)
 
-// Device blocks of freed handles, kept per device (at most kCacheBytes in
-// total) and handed to later loads that need between half and all of a
-// block, so that a load-run-free cycle does not pay cudaMalloc and cudaFree
-// each time.  A cudaMalloc that fails empties the cache and retries once;
-// ktruss_trim_cache empties it on request.
-class BlockCache {
-  public:
-    static constexpr size_t kCacheBytes = size_t(16) << 30;
-    cudaError_t get(size_t bytes, void **p) {
-        int dev = 0;
-        cudaError_t e = cudaGetDevice(&dev);
-        if (e != cudaSuccess) return e;
-        {
-            std::lock_guard<std::mutex> lock(mu_);
-            size_t best = blocks_.size();
-            for (size_t i = 0; i < blocks_.size(); ++i) {
-                const Block &b = blocks_[i];
-                if (b.dev == dev && b.bytes >= bytes && b.bytes / 2 <= bytes &&
-                    (best == blocks_.size() || b.bytes < blocks_[best].bytes))
-                    best = i;
-            }
-            if (best < blocks_.size()) {
-                *p = blocks_[best].p;
-                held_ -= blocks_[best].bytes;
-                blocks_.erase(blocks_.begin() + long(best));
-                return cudaSuccess;
-            }
-        }
-        e = cudaMalloc(p, bytes);
-        if (e == cudaErrorMemoryAllocation) {
-            cudaGetLastError();
-            trim();
-            e = cudaMalloc(p, bytes);
-        }
-        return e;
-    }
-    // bytes: the size the block was obtained with (reused blocks keep theirs)
-    void put(void *p, size_t bytes) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) == cudaSuccess) {
-            std::lock_guard<std::mutex> lock(mu_);
-            if (held_ + bytes <= kCacheBytes) {
-                blocks_.push_back(Block{dev, bytes, p});
-                held_ += bytes;
-                return;
-            }
-        }
-        cudaFree(p);
-    }
-    void trim() {
-        std::vector<Block> out;
-        {
-            std::lock_guard<std::mutex> lock(mu_);
-            out.swap(blocks_);
-            held_ = 0;
-        }
-        for (const Block &b : out) cudaFree(b.p);
-    }
-
-  private:
-    struct Block {
-        int dev;
-        size_t bytes;
-        void *p;
-    };
-    std::mutex mu_;
-    std::vector<Block> blocks_;
-    size_t held_ = 0;
-};
-
-BlockCache &block_cache() {
-    static BlockCache *cache = new BlockCache();  // lives as long as the process
-    return *cache;
-}
-
 // A device block owned by a handle.
 struct Owned {
     void *p;
@@ -152,7 +77,7 @@ struct Allocator {
     cudaError_t commit() {
         if (pending.empty()) return cudaSuccess;
         void *base = nullptr;
-        cudaError_t e = block_cache().get(total, &base);
+        cudaError_t e = kt::cache_get(total, &base);
         if (e != cudaSuccess) return e;
         owned.push_back(Owned{base, total});
         for (auto &q : pending) *q.first = static_cast<char *>(base) + q.second;
@@ -263,7 +188,8 @@ struct BusyGuard {
 void release(ktruss_graph *g) {
     if (!g) return;
     // device blocks (the balanced scratch is part of one) go back to the cache
-    for (const Owned &o : g->owned) block_cache().put(o.p, o.bytes);
+    for (const Owned &o : g->owned) kt::cache_put(o.p, o.bytes);
+    kt::balanced_side_destroy(&g->bs);
     if (g->cnt_host) pinned_slots().put(g->cnt_host);
     for (cudaEvent_t e : g->events) cudaEventDestroy(e);
     delete g;
@@ -519,6 +445,7 @@ static int load_impl(ktruss_graph **out, int32_t n, int64_t m, const int32_t *ro
     g->bs.cap_n = n;
     g->cnt_host = static_cast<kt::RoundCounters *>(pinned_slots().get());
     cudaError_t e = g->cnt_host ? cudaSuccess : cudaErrorMemoryAllocation;
+    if (e == cudaSuccess) e = kt::balanced_side_create(&g->bs);
     if (e == cudaSuccess) e = cudaGetDevice(&g->device);
     const cudaMemcpyKind kind =
         mem_kind == KTRUSS_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
@@ -700,7 +627,7 @@ int ktruss_run_batch(ktruss_graph *g, const int32_t *K, uint8_t *mask_out, int32
 }
 
 int ktruss_trim_cache(void) {
-    block_cache().trim();
+    kt::cache_trim();
     return KTRUSS_OK;
 }
 

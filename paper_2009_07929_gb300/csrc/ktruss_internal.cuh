@@ -56,6 +56,15 @@ constexpr int32_t kMaxLight = 1024;
 bool trace_phases();
 void trace_phase(cudaStream_t s, const char *name);
 
+// ---- device memory cache (memory.cu) ---------------------------------------
+// cache_get: a block of at least `bytes` on the current device, reused from
+// the cache (blocks of half to all of its size) or newly allocated; give it
+// back with cache_put(p, bytes) using the same `bytes`.  cache_trim frees
+// every cached block.
+cudaError_t cache_get(size_t bytes, void **p);
+void cache_put(void *p, size_t bytes);
+void cache_trim();
+
 // ---- validation (validate.cu) ----------------------------------------------
 // Sets *err to a nonzero bit mask if (rp, col) violates the upper-triangular
 // CSR contract.  *err must be zero on entry.
@@ -82,7 +91,14 @@ struct BalancedScratch {
     // tasks whose two lists hold at most `light` columns together are merged
     // by one thread instead of being staged and probed (0 = none)
     int32_t light = kDefaultLight;
+    // optional: a second stream and two events on which the light merge runs
+    // alongside the balancing kernels (joined before the step returns)
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
 };
+// Creates / destroys the side stream and events of a BalancedScratch.
+cudaError_t balanced_side_create(BalancedScratch *bs);
+void balanced_side_destroy(BalancedScratch *bs);
 
 // Bytes of device scratch BalancedScratch needs for a graph of n vertices and
 // m edges (used for allocation at load time).

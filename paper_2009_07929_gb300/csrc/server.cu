@@ -22,9 +22,12 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <deque>
+#include <memory>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "ktruss.h"
@@ -37,9 +40,13 @@ struct Request {
     int32_t n;
     int64_t m;
     int32_t K;
-    std::vector<int32_t> rp, col;
+    std::unique_ptr<int32_t[]> rp, col;  // host copies (left uninitialised, then filled)
     uint8_t *mask_out;
     int32_t *support_out;
+    // staged at submit: the input already on the device (row_ptr then col)
+    // and the request's bytes already counted against the budget
+    int32_t *din = nullptr;
+    bool staged = false;
 };
 
 struct Slot {
@@ -53,7 +60,11 @@ struct Slot {
     uint8_t *dmask = nullptr;
     int32_t *dsup = nullptr;
     int32_t *din = nullptr;  // staged input: row_ptr then col
+    size_t din_bytes = 0;
 };
+
+// Device bytes of a request's staged input (row_ptr then col).
+size_t input_bytes(int32_t n, int64_t m) { return (size_t(n) + 1 + size_t(m)) * 4; }
 
 constexpr int32_t kAutoSmallEdges = 1 << 17;
 
@@ -80,6 +91,8 @@ struct ktruss_server {
     int32_t *S = nullptr, *S2 = nullptr, *pos = nullptr, *vmap = nullptr;
     uint8_t *keep = nullptr, *fin = nullptr;
     int32_t *thr = nullptr, *kept_g = nullptr, *removed_g = nullptr, *rounds_g = nullptr;
+    int32_t *verr = nullptr;       // device: validation error word of submit
+    int32_t *verr_host = nullptr;  // pinned mirror
     uint8_t **mask_ptr = nullptr;
     int32_t **sup_ptr = nullptr;
     int32_t *etile_count = nullptr, *etile_off = nullptr, *vtile_count = nullptr,
@@ -111,12 +124,16 @@ namespace {
 void server_release(ktruss_server *v) {
     if (!v) return;
     for (Slot &sl : v->slot) {
-        if (sl.dmask) cudaFree(sl.dmask);
-        if (sl.dsup) cudaFree(sl.dsup);
-        if (sl.din) cudaFree(sl.din);
+        if (sl.dmask) kt::cache_put(sl.dmask, size_t(sl.m));
+        if (sl.dsup) kt::cache_put(sl.dsup, size_t(sl.m) * 4);
+        if (sl.din) kt::cache_put(sl.din, sl.din_bytes);
     }
+    for (Request &r : v->queue)
+        if (r.din) kt::cache_put(r.din, input_bytes(r.n, r.m));
+    if (v->verr_host) cudaFreeHost(v->verr_host);
     for (void *p : v->owned) cudaFree(p);
     kt::balanced_scratch_free(&v->bs);
+    kt::balanced_side_destroy(&v->bs);
     if (v->cnt_host) cudaFreeHost(v->cnt_host);
     if (v->fin_host) cudaFreeHost(v->fin_host);
     if (v->rounds_host) cudaFreeHost(v->rounds_host);
@@ -125,16 +142,53 @@ void server_release(ktruss_server *v) {
     delete v;
 }
 
+// Runs body(lo, hi) on the parts of [0, count): one part per grain, at most
+// one per hardware thread, all in the calling thread when there is one part.
+template <typename F>
+void parallel_ranges(int64_t count, int64_t grain, F body) {
+    int64_t hw = int64_t(std::thread::hardware_concurrency());
+    if (hw < 1) hw = 1;
+    const int64_t parts = std::min<int64_t>(hw, std::max<int64_t>(1, count / grain));
+    if (parts <= 1) {
+        body(int64_t(0), count);
+        return;
+    }
+    std::vector<std::thread> ts;
+    ts.reserve(size_t(parts));
+    for (int64_t k = 0; k < parts; ++k)
+        ts.emplace_back(body, count * k / parts, count * (k + 1) / parts);
+    for (std::thread &t : ts) t.join();
+}
+
+// The CSR contract of ktruss_load_csr, checked on the host (rows split over
+// host threads for large requests).  Every row checks its own bounds before
+// it reads its columns, so no part reads outside col whatever the input.
 bool valid_csr(int32_t n, int64_t m, const int32_t *rp, const int32_t *col) {
     if (rp[0] != 0 || rp[n] != m) return false;
-    for (int32_t i = 0; i < n; ++i) {
-        if (rp[i + 1] < rp[i] || rp[i + 1] > m) return false;
-        for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
-            if (col[p] <= i || col[p] >= n) return false;
-            if (p > rp[i] && col[p] <= col[p - 1]) return false;
+    std::atomic<bool> ok{true};
+    parallel_ranges(int64_t(n), int64_t(1) << 16, [&](int64_t lo, int64_t hi) {
+        for (int64_t i = lo; i < hi && ok.load(std::memory_order_relaxed); ++i) {
+            const int64_t b = rp[i], e = rp[i + 1];
+            if (b < 0 || e < b || e > m) {
+                ok = false;
+                return;
+            }
+            for (int64_t p = b; p < e; ++p) {
+                if (col[p] <= i || col[p] >= n || (p > b && col[p] <= col[p - 1])) {
+                    ok = false;
+                    return;
+                }
+            }
         }
-    }
-    return true;
+    });
+    return ok;
+}
+
+// dst[0..count) = src[0..count), split over host threads for large copies.
+void parallel_copy(int32_t *dst, const int32_t *src, int64_t count) {
+    parallel_ranges(count, int64_t(1) << 22, [&](int64_t lo, int64_t hi) {
+        std::memcpy(dst + lo, src + lo, size_t(hi - lo) * sizeof(int32_t));
+    });
 }
 
 // Device bytes a request holds while active besides the shared live CSR:
@@ -213,8 +267,11 @@ int ktruss_server_create(ktruss_server **out, int32_t max_vertices, int64_t max_
     A((void **)&v->vtile_count, size_t(vt) * 4);
     A((void **)&v->vtile_off, size_t(vt) * 4);
     A((void **)&v->cnt, 3 * sizeof(kt::RoundCounters));
+    A((void **)&v->verr, 16);
     if (e == cudaSuccess) e = kt::balanced_scratch_alloc(&v->bs, max_vertices, max_edges);
+    if (e == cudaSuccess) e = kt::balanced_side_create(&v->bs);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&v->cnt_host, 3 * sizeof(kt::RoundCounters));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&v->verr_host, 16);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&v->fin_host, size_t(max_requests));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&v->rounds_host, sb);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&v->ptr_host, 2 * size_t(max_requests) * sizeof(void *));
@@ -251,14 +308,52 @@ int ktruss_server_submit(ktruss_server *srv, int32_t n, int64_t m, const int32_t
     if (n > srv->vcap || m > srv->ecap ||
         int64_t(request_bytes(n, m)) > srv->budget)
         return KTRUSS_EINVAL;  // could never be admitted
-    if (!valid_csr(n, m, row_ptr, col)) return KTRUSS_EINVAL;
     Request r;
-    r.ticket = srv->next_ticket++;
     r.n = n;
     r.m = m;
     r.K = K;
-    r.rp.assign(row_ptr, row_ptr + n + 1);
-    if (m > 0) r.col.assign(col, col + m);
+    const size_t bytes = request_bytes(n, m);
+    // Staged requests hold their budget while queued; staging only while no
+    // host-copied request waits keeps every staged request ahead of every
+    // host-copied one, so that admission in arrival order cannot stall on a
+    // budget that queued requests behind it hold.
+    if (m > 0 && srv->used + int64_t(bytes) <= srv->budget &&
+        (srv->queue.empty() || srv->queue.back().staged)) {
+        // room in the budget now: stage the input on the device straight from
+        // the caller's arrays and validate it there (no host copy)
+        void *p = nullptr;
+        if (kt::cache_get(input_bytes(n, m), &p) == cudaSuccess) {
+            cudaStream_t s = srv->s;
+            int32_t *din = static_cast<int32_t *>(p);
+            cudaError_t e = cudaMemcpyAsync(din, row_ptr, (size_t(n) + 1) * 4,
+                                            cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(din + n + 1, col, size_t(m) * 4, cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess) e = cudaMemsetAsync(srv->verr, 0, 4, s);
+            if (e == cudaSuccess) e = kt::launch_validate(din, din + n + 1, n, m, srv->verr, s);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(srv->verr_host, srv->verr, 4, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess || *srv->verr_host != 0) {
+                kt::cache_put(p, input_bytes(n, m));
+                return e != cudaSuccess ? map_err(e) : KTRUSS_EINVAL;
+            }
+            r.din = din;
+            r.staged = true;
+            srv->used += int64_t(bytes);
+        } else {
+            cudaGetLastError();  // no memory to stage now: keep a host copy
+        }
+    }
+    if (!r.staged) {
+        if (!valid_csr(n, m, row_ptr, col)) return KTRUSS_EINVAL;
+        r.rp.reset(new (std::nothrow) int32_t[size_t(n) + 1]);
+        if (m > 0) r.col.reset(new (std::nothrow) int32_t[size_t(m)]);
+        if (!r.rp || (m > 0 && !r.col)) return KTRUSS_ENOMEM;
+        parallel_copy(r.rp.get(), row_ptr, int64_t(n) + 1);
+        if (m > 0) parallel_copy(r.col.get(), col, m);
+    }
+    r.ticket = srv->next_ticket++;
     r.mask_out = mask_out;
     r.support_out = support_out;
     if (ticket_out) *ticket_out = r.ticket;
@@ -292,12 +387,28 @@ int ktruss_server_step(ktruss_server *srv, int32_t *num_done) {
             }
         const size_t bytes = request_bytes(r.n, r.m);
         if (sid < 0 || int64_t(srv->n_live) + r.n > srv->vcap ||
-            int64_t(srv->m_live) + r.m > srv->ecap || srv->used + int64_t(bytes) > srv->budget)
+            int64_t(srv->m_live) + r.m > srv->ecap ||
+            (!r.staged && srv->used + int64_t(bytes) > srv->budget))
             break;
         Slot &sl = srv->slot[size_t(sid)];
-        SV_CK(cudaMalloc((void **)&sl.din, (size_t(r.n) + 1 + size_t(r.m)) * 4));
-        SV_CK(cudaMalloc((void **)&sl.dmask, size_t(r.m)));
-        if (r.support_out) SV_CK(cudaMalloc((void **)&sl.dsup, size_t(r.m) * 4));
+        {
+            // take every buffer first, so that a failure leaves the request queued as it was
+            void *din = r.din, *dm = nullptr, *ds = nullptr;
+            cudaError_t e = din ? cudaSuccess : kt::cache_get(input_bytes(r.n, r.m), &din);
+            if (e == cudaSuccess) e = kt::cache_get(size_t(r.m), &dm);
+            if (e == cudaSuccess && r.support_out) e = kt::cache_get(size_t(r.m) * 4, &ds);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                if (dm) kt::cache_put(dm, size_t(r.m));
+                if (din && !r.staged) kt::cache_put(din, input_bytes(r.n, r.m));
+                return map_err(e);
+            }
+            sl.din = static_cast<int32_t *>(din);
+            sl.din_bytes = input_bytes(r.n, r.m);
+            sl.dmask = static_cast<uint8_t *>(dm);
+            sl.dsup = static_cast<int32_t *>(ds);
+            r.din = nullptr;
+        }
         sl.used = true;
         sl.ticket = r.ticket;
         sl.n = r.n;
@@ -305,10 +416,15 @@ int ktruss_server_step(ktruss_server *srv, int32_t *num_done) {
         sl.bytes = bytes;
         sl.host_mask = r.mask_out;
         sl.host_sup = r.support_out;
-        srv->used += int64_t(bytes);
         int32_t *drp = sl.din, *dcol = sl.din + r.n + 1;
-        SV_CK(cudaMemcpyAsync(drp, r.rp.data(), (size_t(r.n) + 1) * 4, cudaMemcpyHostToDevice, s));
-        SV_CK(cudaMemcpyAsync(dcol, r.col.data(), size_t(r.m) * 4, cudaMemcpyHostToDevice, s));
+        if (!r.staged) {
+            srv->used += int64_t(bytes);
+            SV_CK(cudaMemcpyAsync(drp, r.rp.get(), (size_t(r.n) + 1) * 4, cudaMemcpyHostToDevice,
+                                  s));
+            if (r.m > 0)
+                SV_CK(cudaMemcpyAsync(dcol, r.col.get(), size_t(r.m) * 4, cudaMemcpyHostToDevice,
+                                      s));
+        }
         SV_CK(kt::launch_server_append(drp, dcol, r.n, int32_t(r.m), srv->n_live, srv->m_live, sid,
                                        srv->rp[srv->cur], srv->col[srv->cur], srv->eid[srv->cur],
                                        srv->gid[srv->cur], s));
@@ -407,9 +523,9 @@ int ktruss_server_step(ktruss_server *srv, int32_t *num_done) {
             srv->done_tickets.push_back(sl.ticket);
             srv->done_rounds.push_back(srv->rounds_host[k]);
             ++finished;
-            cudaFree(sl.din);
-            cudaFree(sl.dmask);
-            if (sl.dsup) cudaFree(sl.dsup);
+            kt::cache_put(sl.din, sl.din_bytes);
+            kt::cache_put(sl.dmask, size_t(sl.m));
+            if (sl.dsup) kt::cache_put(sl.dsup, size_t(sl.m) * 4);
             srv->used -= int64_t(sl.bytes);
             sl = Slot{};
         }

@@ -1179,6 +1179,22 @@ cudaError_t balanced_scratch_alloc(BalancedScratch *bs, int32_t n, int64_t m) {
     return cudaSuccess;
 }
 
+cudaError_t balanced_side_create(BalancedScratch *bs) {
+    cudaError_t e = cudaStreamCreateWithFlags(&bs->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&bs->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&bs->join, cudaEventDisableTiming);
+    if (e != cudaSuccess) balanced_side_destroy(bs);
+    return e;
+}
+
+void balanced_side_destroy(BalancedScratch *bs) {
+    if (bs->fork) cudaEventDestroy(bs->fork);
+    if (bs->join) cudaEventDestroy(bs->join);
+    if (bs->side) cudaStreamDestroy(bs->side);
+    bs->side = nullptr;
+    bs->fork = bs->join = nullptr;
+}
+
 void balanced_scratch_free(BalancedScratch *bs) {
     if (bs->base) cudaFree(bs->base);
     bs->base = nullptr;
@@ -1196,6 +1212,27 @@ cudaError_t launch_support_balanced(const Live &g, int32_t *S, RoundCounters *cn
     Carve c;
     carve(bs->base, bs->cap_n, bs->cap_m, &c);
     const int32_t n = g.n, m = g.m;
+    // light tasks first: on the side stream they overlap the balancing
+    // kernels below (S is zero on entry in stream order, so the fork is safe)
+    const bool side = bs->side && bs->light > 0;
+    if (bs->light > 0) {
+        cudaStream_t ls = s;
+        if (side) {
+            e = cudaEventRecord(bs->fork, s);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(bs->side, bs->fork, 0);
+            if (e != cudaSuccess) return e;
+            ls = bs->side;
+        }
+        const int64_t lblocks = (int64_t(m) + int64_t(kEdgeThreads) * kLightPerThread - 1) /
+                                (int64_t(kEdgeThreads) * kLightPerThread);
+        support_light_kernel<<<int(lblocks), kEdgeThreads, 0, ls>>>(
+            g.rp, g.col, n, m, S, &cnt->triangles, g.gid, g.skip, bs->light);
+        *launches += 1;
+        if (side) {
+            e = cudaEventRecord(bs->join, bs->side);
+            if (e != cudaSuccess) return e;
+        }
+    }
     e = cudaMemsetAsync(c.rcount, 0, size_t(n + 1) * 4, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c.sched, 0, kSchedWords * 4, s);
     if (e != cudaSuccess) return e;
@@ -1250,16 +1287,13 @@ cudaError_t launch_support_balanced(const Live &g, int32_t *S, RoundCounters *cn
         e = cudaEventRecord(ev[1], s);
         if (e != cudaSuccess) return e;
     }
-    if (bs->light > 0) {
-        const int64_t lblocks = (int64_t(m) + int64_t(kEdgeThreads) * kLightPerThread - 1) /
-                                (int64_t(kEdgeThreads) * kLightPerThread);
-        support_light_kernel<<<int(lblocks), kEdgeThreads, 0, s>>>(
-            g.rp, g.col, n, m, S, &cnt->triangles, g.gid, g.skip, bs->light);
-        *launches += 1;
-    }
     SupportArgs A{g.rp, g.col, c.seg, c.pst, c.sact, c.wp, c.arow, c.aseg, c.plan, c.bound,
                   c.sched, S, &cnt->triangles, &cnt->error};
     support_kernel<<<g_support_blocks, kThreads, sizeof(SupportSmem), s>>>(A);
+    if (side) {
+        e = cudaStreamWaitEvent(s, bs->join, 0);
+        if (e != cudaSuccess) return e;
+    }
     trace_phase(s, "support_kernel");
     if (trace_phases()) {
         int32_t hs[kSchedWords] = {};
