@@ -408,12 +408,25 @@ class Server:
         except Exception:
             pass
 
-    def submit(self, row_ptr, col, K: int, support: bool = True) -> int:
+    def submit(self, row_ptr, col, K: int, support: bool = True, mask_out=None,
+               support_out=None) -> int:
+        """Queues one request.  mask_out / support_out: caller-owned host
+        arrays (uint8 / int32, at least m entries, C-contiguous) that receive
+        the outputs; allocated here when None."""
         rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
         c = np.ascontiguousarray(col, dtype=np.int32)
         m = c.shape[0]
-        mask = np.zeros(max(m, 1), dtype=np.uint8)
-        sup = np.zeros(max(m, 1), dtype=np.int32) if support else None
+
+        def out(a, dtype):
+            if a is None:
+                return np.zeros(max(m, 1), dtype=dtype)
+            if (not isinstance(a, np.ndarray) or a.dtype != dtype or a.ndim != 1
+                    or a.shape[0] < m or not a.flags.c_contiguous):
+                raise ValueError(f"output array must be C-contiguous {np.dtype(dtype).name}[>= {m}]")
+            return a
+
+        mask = out(mask_out, np.uint8)
+        sup = out(support_out, np.int32) if support else None
         t = ctypes.c_int64(0)
         rc = lib().ktruss_server_submit(self._h, rp.shape[0] - 1, m, rp.ctypes.data,
                                         c.ctypes.data if m else None, K, mask.ctypes.data,
@@ -446,11 +459,13 @@ class Server:
         return q.value, a.value, e.value
 
 
-def serve_poisson(server, requests, rate, seed=0, clock=None):
+def serve_poisson(server, requests, rate, seed=0, clock=None, outputs=None):
     """Feeds (csr, K) requests to a Server with Poisson arrivals of the given
     rate (requests/s; None = all at time 0) in real time and steps it until
-    every request is done.  Returns per-request latencies (s, arrival to
-    completion), the makespan and the results by request index."""
+    every request is done.  outputs: optional (mask, support) host arrays per
+    request (Server.submit's mask_out / support_out).  Returns per-request
+    latencies (s, arrival to completion), the makespan and the results by
+    request index."""
     import time
     clock = clock or time.perf_counter
     rng = np.random.default_rng(seed)
@@ -467,7 +482,8 @@ def serve_poisson(server, requests, rate, seed=0, clock=None):
         now = clock() - t0
         while i < N and arrivals[i] <= now:
             g, K = requests[i]
-            ticket_of[server.submit(g.row_ptr, g.col, K)] = i
+            mo, so = outputs[i] if outputs is not None else (None, None)
+            ticket_of[server.submit(g.row_ptr, g.col, K, mask_out=mo, support_out=so)] = i
             i += 1
         q, a, _ = server.status()
         if q == 0 and a == 0:

@@ -16,7 +16,6 @@ namespace {
 
 constexpr int kWarpsPerTile = kCompactThreads / 32;
 constexpr int kWarpSpan = kCompactTile / kWarpsPerTile;
-constexpr int32_t kRecomputeMinListed = 1 << 16;
 
 // gid[v] = graph owning vertex v (largest g with vo[g] <= v).
 __global__ void graph_of_vertex_kernel(const int32_t *__restrict__ vo, int32_t G, int32_t n,
@@ -105,11 +104,8 @@ __global__ void batch_done_kernel(int32_t G, const int32_t *__restrict__ kept_g,
 // Per graph after a round's compaction (rp_new: the new row pointers, graph g
 // owns vertices [vo[g], vo[g+1])): its surviving edges, and whether its next
 // supports come from the update of this round (upd_g = 1) or from a support
-// step (0).  mode: 0 never update, 1 always, 2 update while the listed edges
-// (removed, in triangles) are at most a quarter of the survivors, or fewer than
-// kRecomputeMinListed: a support step for a few graphs still classifies every
-// live edge of the batch, which only pays off for a graph that would otherwise
-// update a large number of edges.  Counts the graphs that stay live
+// step (0).  mode: 0 never update, 1 always, 2 the kRecomputeMinListed rule.
+// Counts the graphs that stay live
 // (cnt->kept) and those that need a support step (cnt->removed_tri).
 __global__ void batch_decide_kernel(int32_t G, const int32_t *__restrict__ vo,
                                     const int32_t *__restrict__ rp_new,
@@ -234,11 +230,11 @@ cudaError_t launch_batch_validate(const int32_t *rp, const int32_t *col, int32_t
 cudaError_t launch_batch_keep(const Live &g, const int32_t *S, const int32_t *gid,
                               const int32_t *thr, uint8_t *keep, int32_t *kept_g,
                               int32_t *removed_g, cudaStream_t s, int *launches, int32_t *list,
-                              int32_t *list_count) {
+                              int32_t *list_count, int32_t *listed_g) {
     if (g.m == 0) return cudaSuccess;
     batch_prune_kernel<<<(g.m + 255) / 256, 256, 0, s>>>(S, g.col, g.m, gid, thr, keep, kept_g,
                                                          removed_g, list, list_count, nullptr,
-                                                         nullptr);
+                                                         listed_g);
     ++*launches;
     return cudaGetLastError();
 }

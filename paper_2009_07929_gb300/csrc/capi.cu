@@ -258,6 +258,7 @@ int trace_level() {
 }
 }  // namespace
 
+bool trace_on() { return trace_level() >= 1; }
 bool trace_phases() { return trace_level() >= 2; }
 
 void trace_phase(cudaStream_t s, const char *name) {

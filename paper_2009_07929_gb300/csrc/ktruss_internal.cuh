@@ -49,10 +49,17 @@ constexpr int kWarp = 32;
 // BalancedScratch::light); chosen by a sweep on R-MAT and G(n,m) graphs.
 constexpr int32_t kDefaultLight = 64;
 constexpr int32_t kMaxLight = 1024;
+// Per-graph update rule of batches and the server: a graph's next supports
+// come from the decremental update while its listed edges (removed, in some
+// triangle) are at most a quarter of its surviving edges, or fewer than this:
+// a support step for a few graphs still classifies every live edge, which
+// only pays off for a graph that would otherwise update many edges.
+constexpr int32_t kRecomputeMinListed = 1 << 16;
 
 // KTRUSS_TRACE=2 (or more): the launchers synchronise the stream after each
 // phase and print its name and the time since the process loaded the library
 // on stderr (a debugging aid; off by default).
+bool trace_on();      // KTRUSS_TRACE >= 1
 bool trace_phases();
 void trace_phase(cudaStream_t s, const char *name);
 
@@ -235,7 +242,8 @@ cudaError_t launch_batch_zero(const Live &g, const int32_t *gid, const uint8_t *
 cudaError_t launch_batch_keep(const Live &g, const int32_t *S, const int32_t *gid,
                               const int32_t *thr, uint8_t *keep, int32_t *kept_g,
                               int32_t *removed_g, cudaStream_t s, int *launches,
-                              int32_t *list = nullptr, int32_t *list_count = nullptr);
+                              int32_t *list = nullptr, int32_t *list_count = nullptr,
+                              int32_t *listed_g = nullptr);
 
 // ---- request server (server_kernels.cu) --------------------------------------
 // Appends a request's device CSR at vertex base nb / edge base mb of the live CSR.
@@ -243,11 +251,20 @@ cudaError_t launch_server_append(const int32_t *rp_in, const int32_t *col_in, in
                                  int32_t nb, int32_t mb, int32_t slot, int32_t *rp, int32_t *col,
                                  int32_t *eid, int32_t *gid, cudaStream_t s);
 // Keep flags and per-slot kept / removed flags (= launch_batch_keep); removed edges with
-// S > 0 appended to list when given (count in *list_count, zero on entry).
+// S > 0 appended to list when given (count in *list_count, zero on entry) and
+// counted per slot in listed_s when given.
 cudaError_t launch_server_prune(const Live &cur, const int32_t *S, const int32_t *gid,
                                 const int32_t *thr, uint8_t *keep, int32_t *kept_g,
                                 int32_t *removed_g, cudaStream_t s, int *launches,
-                                int32_t *list = nullptr, int32_t *list_count = nullptr);
+                                int32_t *list = nullptr, int32_t *list_count = nullptr,
+                                int32_t *listed_s = nullptr);
+// Per slot after a round tail (kept_s: the slot's surviving edges, as
+// counted by the round tail): upd_s = 1 when its next supports come from the
+// update (mode 0 never, 1 always, 2 the kRecomputeMinListed rule), cnt->kept =
+// live slots, cnt->removed_tri = live slots that need a support step.
+cudaError_t launch_server_decide(int32_t slots, const int32_t *kept_s, const int32_t *listed_s,
+                                 int32_t mode, uint8_t *upd_s, RoundCounters *cnt, cudaStream_t s,
+                                 int *launches);
 // Finished slots, vertex renumbering (vcnt->kept = surviving vertices),
 // edge compaction (cnt->kept = surviving edges) with outputs of leaving edges
 // through the per-slot pointer tables, new row pointers and slot ids.
@@ -260,7 +277,7 @@ cudaError_t launch_server_round_tail(const Live &cur, const int32_t *S, const ui
                                      int32_t *rp_out, int32_t *col_out, int32_t *eid_out,
                                      int32_t *gid_out, uint8_t *const *mask_ptr,
                                      int32_t *const *sup_ptr, cudaStream_t s, int *launches,
-                                     int32_t *S_out = nullptr);
+                                     int32_t *S_out = nullptr, int32_t *kept_s = nullptr);
 
 // Compaction of the edges that stay live; outputs of the edges that leave.
 // When S_out is given, edges that stay carry their S into S_out.

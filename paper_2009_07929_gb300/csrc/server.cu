@@ -23,6 +23,8 @@
 
 #include <algorithm>
 #include <atomic>
+#include <chrono>
+#include <cstdio>
 #include <cstring>
 #include <deque>
 #include <memory>
@@ -109,7 +111,13 @@ struct ktruss_server {
     int cur = 0;
     int32_t n_live = 0;
     int32_t m_live = 0;
-    int32_t m_valid = 0;  // leading live edges whose S was carried from the last step
+    // per slot: upd_s = 1 when the slot's supports in S are current (carried
+    // and updated from the last step, or computed at admission); listed_s /
+    // kept_s: the round's listed and surviving edges of the slot
+    uint8_t *upd_s = nullptr;
+    int32_t *listed_s = nullptr, *kept_s = nullptr;
+    bool any_valid = false;  // some live slot has upd_s = 1
+    int32_t need_slots = 0;  // live slots with upd_s = 0
     int update_mode = KTRUSS_UPDATE_AUTO;
     int64_t next_ticket = 1;
     std::deque<Request> queue;
@@ -209,7 +217,7 @@ cudaError_t support_step(ktruss_server *v, const kt::Live &g, int32_t *S, int *l
 // (request-local vertex ids) and its first slot in the live CSR.
 struct Fresh {
     const int32_t *rp, *col;
-    int32_t n, m, mb;
+    int32_t n, m, nb, mb;
 };
 
 }  // namespace
@@ -260,6 +268,9 @@ int ktruss_server_create(ktruss_server **out, int32_t max_vertices, int64_t max_
     A((void **)&v->kept_g, sb);
     A((void **)&v->removed_g, sb);
     A((void **)&v->rounds_g, sb);
+    A((void **)&v->upd_s, size_t(max_requests));
+    A((void **)&v->listed_s, sb);
+    A((void **)&v->kept_s, sb);
     A((void **)&v->mask_ptr, size_t(max_requests) * sizeof(void *));
     A((void **)&v->sup_ptr, size_t(max_requests) * sizeof(void *));
     A((void **)&v->etile_count, size_t(et) * 4);
@@ -438,86 +449,133 @@ int ktruss_server_step(ktruss_server *srv, int32_t *num_done) {
                               cudaMemcpyHostToDevice, s));
         SV_CK(cudaMemcpyAsync(srv->thr + sid, &srv->thr_host[sid], 4, cudaMemcpyHostToDevice, s));
         SV_CK(cudaMemsetAsync(srv->rounds_g + sid, 0, 4, s));
-        fresh.push_back(Fresh{drp, dcol, r.n, int32_t(r.m), srv->m_live});
+        SV_CK(cudaMemsetAsync(srv->upd_s + sid, 1, 1, s));  // supports computed below
+        fresh.push_back(Fresh{drp, dcol, r.n, int32_t(r.m), srv->n_live, srv->m_live});
         srv->n_live += r.n;
         srv->m_live += int32_t(r.m);
         admitted.push_back(std::move(r));
         srv->queue.pop_front();
     }
+    kt::trace_phase(s, "server admission");
+    const auto t_step = std::chrono::steady_clock::now();
     // ---- 2. one peel round over every active request
     if (srv->m_live > 0) {
         const int c = srv->cur, o = c ^ 1;
         const kt::Live g{srv->rp[c], srv->col[c], srv->eid[c], srv->n_live, srv->m_live};
         SV_CK(cudaMemsetAsync(srv->cnt, 0, 3 * sizeof(kt::RoundCounters), s));
-        if (srv->m_valid == 0) {
-            // supports of the whole live CSR
-            SV_CK(cudaMemsetAsync(srv->S, 0, size_t(g.m) * 4, s));
-            SV_CK(support_step(srv, g, srv->S, &launches));
-        } else if (srv->m_live > srv->m_valid) {
-            // carried supports for the older requests; a support step per
-            // request admitted now, over its own CSR (its slots follow the
-            // live CSR's in order, so its supports land at its first slot)
-            SV_CK(cudaMemsetAsync(srv->S + srv->m_valid, 0,
-                                  size_t(srv->m_live - srv->m_valid) * 4, s));
+        // The requests admitted now follow the older ones in the live CSR:
+        // the older requests are the prefix [0, n_old) x [0, m_old), itself a
+        // valid CSR (the first admitted vertex's row starts at m_old).
+        const int32_t n_old = fresh.empty() ? g.n : fresh.front().nb;
+        const int32_t m_old = fresh.empty() ? g.m : fresh.front().mb;
+        // a support step per request admitted now, over its own CSR (its
+        // supports land at its first slot) ...
+        if (!fresh.empty()) {
+            SV_CK(cudaMemsetAsync(srv->S + m_old, 0, size_t(g.m - m_old) * 4, s));
             for (const Fresh &f : fresh) {
                 const kt::Live rg{f.rp, f.col, nullptr, f.n, f.m};
                 SV_CK(support_step(srv, rg, srv->S + f.mb, &launches));
             }
         }
+        // ... and one over the older requests: all of them when no supports
+        // were carried, else those whose own rule chose a support step (the
+        // tasks of every other slot skipped)
+        if (m_old > 0) {
+            const kt::Live prefix{g.rp, g.col, g.eid, n_old, m_old};
+            if (!srv->any_valid) {
+                SV_CK(cudaMemsetAsync(srv->S, 0, size_t(m_old) * 4, s));
+                SV_CK(support_step(srv, prefix, srv->S, &launches));
+            } else if (srv->need_slots > 0) {
+                SV_CK(kt::launch_batch_zero(prefix, srv->gid[c], srv->upd_s, srv->S, s,
+                                            &launches));
+                kt::Live masked = prefix;
+                masked.gid = srv->gid[c];
+                masked.skip = srv->upd_s;
+                SV_CK(support_step(srv, masked, srv->S, &launches));
+            }
+        }
+        kt::trace_phase(s, "server support steps");
         SV_CK(cudaMemsetAsync(srv->kept_g, 0, size_t(srv->slots) * 4, s));
         SV_CK(cudaMemsetAsync(srv->removed_g, 0, size_t(srv->slots) * 4, s));
         const bool track = srv->update_mode != KTRUSS_UPDATE_NEVER;
         const kt::UpdateScratch us = kt::update_scratch(&srv->bs);
+        if (track) {
+            SV_CK(cudaMemsetAsync(srv->listed_s, 0, size_t(srv->slots) * 4, s));
+            SV_CK(cudaMemsetAsync(srv->kept_s, 0, size_t(srv->slots) * 4, s));
+        }
         SV_CK(kt::launch_server_prune(g, srv->S, srv->gid[c], srv->thr, srv->keep, srv->kept_g,
                                       srv->removed_g, s, &launches, track ? us.list : nullptr,
-                                      &srv->cnt[0].removed_tri));
-        bool upd = false;
-        if (track) {
-            SV_CK(cudaMemcpyAsync(srv->cnt_host, srv->cnt, sizeof(kt::RoundCounters),
-                                  cudaMemcpyDeviceToHost, s));
-            SV_CK(cudaStreamSynchronize(s));
-            const int32_t nlist = srv->cnt_host[0].removed_tri;
-            // survivors are not known before the round tail: the live edges
-            // bound them from above (the same quarter rule as ktruss_run)
-            upd = srv->update_mode == KTRUSS_UPDATE_ALWAYS ||
-                  int64_t(nlist) * 4 <= int64_t(srv->m_live);
-            if (upd && nlist > 0) {
-                srv->ust.ldeg_valid = false;
-                SV_CK(kt::launch_support_update(g, srv->keep, us.list, nlist, srv->S,
-                                                &srv->cnt[2].triangles, us, &srv->ust, s,
-                                                &launches));
-            }
-        }
+                                      &srv->cnt[0].removed_tri, track ? srv->listed_s : nullptr));
+        // the round tail carries the supports of surviving edges into S2 when
+        // the update may run; each slot then takes its own choice
         SV_CK(kt::launch_server_round_tail(
             g, srv->S, srv->keep, srv->kept_g, srv->removed_g, srv->fin, srv->rounds_g,
             srv->slots, srv->gid[c], srv->vmap, srv->vtile_count, srv->vtile_off, srv->cnt + 1,
             srv->etile_count, srv->etile_off, srv->cnt, srv->pos, srv->rp[o], srv->col[o],
             srv->eid[o], srv->gid[o], srv->mask_ptr, srv->sup_ptr, s, &launches,
-            upd ? srv->S2 : nullptr));
-        SV_CK(cudaMemcpyAsync(srv->cnt_host, srv->cnt, 2 * sizeof(kt::RoundCounters),
+            track ? srv->S2 : nullptr, track ? srv->kept_s : nullptr));
+        kt::trace_phase(s, "server prune + round tail");
+        const int32_t mode = srv->update_mode == KTRUSS_UPDATE_ALWAYS ? 1 : 2;
+        if (track)
+            SV_CK(kt::launch_server_decide(srv->slots, srv->kept_s, srv->listed_s, mode, srv->upd_s,
+                                           srv->cnt + 2, s, &launches));
+        SV_CK(cudaMemcpyAsync(srv->cnt_host, srv->cnt, 3 * sizeof(kt::RoundCounters),
                               cudaMemcpyDeviceToHost, s));
         SV_CK(cudaMemcpyAsync(srv->fin_host, srv->fin, size_t(srv->slots), cudaMemcpyDeviceToHost, s));
         SV_CK(cudaMemcpyAsync(srv->rounds_host, srv->rounds_g, size_t(srv->slots) * 4,
                               cudaMemcpyDeviceToHost, s));
         SV_CK(cudaStreamSynchronize(s));
-        srv->m_live = srv->cnt_host[0].kept;
+        const kt::RoundCounters c0 = srv->cnt_host[0], c2 = srv->cnt_host[2];
+        if (c0.error) return (c0.error & kt::kDevErrTimeout) ? KTRUSS_ETIMEOUT : KTRUSS_ECUDA;
+        const int32_t nlist = c0.removed_tri;
+        srv->any_valid = track && c2.kept > c2.removed_tri;
+        srv->need_slots = track ? c2.removed_tri : 0;
+        if (srv->any_valid && nlist > 0) {
+            // the update of the updated slots runs on this step's graph and
+            // subtracts into the carried supports through the position map
+            kt::Live old = g;
+            old.gid = srv->gid[c];
+            srv->ust.ldeg_valid = false;
+            SV_CK(kt::launch_support_update(old, srv->keep, us.list, nlist, srv->S,
+                                            &srv->cnt[2].triangles, us, &srv->ust, s, &launches,
+                                            srv->pos, srv->S2, srv->upd_s));
+        }
+        kt::trace_phase(s, "server update");
+        if (kt::trace_on())
+            std::fprintf(stderr,
+                         "[ktruss server] step %lld admitted %d live %d -> %d edges, listed %d, "
+                         "recomputed slots next %d, %s, %.3f ms to the round tail\n",
+                         (long long)srv->steps, int(admitted.size()), int(g.m), int(c0.kept),
+                         int(nlist), int(srv->need_slots),
+                         srv->any_valid ? "update" : "support step next",
+                         std::chrono::duration<double, std::milli>(
+                             std::chrono::steady_clock::now() - t_step).count());
+        srv->m_live = c0.kept;
         srv->n_live = srv->cnt_host[1].kept;
         srv->cur = o;
-        if (upd) std::swap(srv->S, srv->S2);
-        srv->m_valid = upd ? srv->m_live : 0;
+        if (track) std::swap(srv->S, srv->S2);
         ++srv->steps;
         // ---- 3. finished requests: outputs to the caller, memory back
         std::vector<int32_t> fin_slots;
         for (int32_t k = 0; k < srv->slots; ++k) {
             Slot &sl = srv->slot[size_t(k)];
             if (!sl.used || !srv->fin_host[k]) continue;
+            const auto t_copy = std::chrono::steady_clock::now();
             SV_CK(cudaMemcpyAsync(sl.host_mask, sl.dmask, size_t(sl.m), cudaMemcpyDeviceToHost, s));
             if (sl.host_sup)
                 SV_CK(cudaMemcpyAsync(sl.host_sup, sl.dsup, size_t(sl.m) * 4,
                                       cudaMemcpyDeviceToHost, s));
+            if (kt::trace_phases()) {
+                SV_CK(cudaStreamSynchronize(s));
+                std::fprintf(stderr, "[ktruss server] outputs of slot %d: %d edges, %.3f ms\n",
+                             int(k), int(sl.m),
+                             std::chrono::duration<double, std::milli>(
+                                 std::chrono::steady_clock::now() - t_copy).count());
+            }
             fin_slots.push_back(k);
         }
         if (!fin_slots.empty()) SV_CK(cudaStreamSynchronize(s));
+        kt::trace_phase(s, "server finished outputs");
         for (int32_t k : fin_slots) {
             Slot &sl = srv->slot[size_t(k)];
             srv->done_tickets.push_back(sl.ticket);

@@ -179,21 +179,52 @@ edge_compact_kernel(const int32_t *__restrict__ col, const int32_t *__restrict__
     }
 }
 
-// New row pointers and slot ids of the surviving vertices.
+// New row pointers and slot ids of the surviving vertices.  A slot's
+// vertices are contiguous, so its surviving edges (kept_s, zero on entry,
+// when given) are the new row pointer after its last vertex minus the one of
+// its first: the two boundary vertices add them.
 __global__ void vertex_rewrite_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ gid,
                                       const uint8_t *__restrict__ fin,
                                       const int32_t *__restrict__ vmap,
                                       const int32_t *__restrict__ pos, int32_t n, int32_t m,
                                       const RoundCounters *__restrict__ cnt,
                                       const int32_t *__restrict__ vtotal,
-                                      int32_t *__restrict__ rp_out, int32_t *__restrict__ gid_out) {
+                                      int32_t *__restrict__ rp_out, int32_t *__restrict__ gid_out,
+                                      int32_t *__restrict__ kept_s) {
     const int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (v < n && !fin[gid[v]]) {
+        const int32_t g = gid[v];
         const int32_t r = rp[v];
-        rp_out[vmap[v]] = r < m ? pos[r] : cnt->kept;
-        gid_out[vmap[v]] = gid[v];
+        const int32_t nr = r < m ? pos[r] : cnt->kept;
+        rp_out[vmap[v]] = nr;
+        gid_out[vmap[v]] = g;
+        if (kept_s) {
+            if (v == 0 || gid[v - 1] != g) atomicSub(kept_s + g, nr);
+            if (v == n - 1 || gid[v + 1] != g) {
+                const int32_t r1 = rp[v + 1];
+                atomicAdd(kept_s + g, r1 < m ? pos[r1] : cnt->kept);
+            }
+        }
     }
     if (v == 0) rp_out[*vtotal] = cnt->kept;
+}
+
+// Per slot: update or support step next step (the rule of batch_decide_kernel
+// on the slot's surviving and listed edges).
+__global__ void server_decide_kernel(int32_t slots, const int32_t *__restrict__ kept_s,
+                                     const int32_t *__restrict__ listed_s, int32_t mode,
+                                     uint8_t *__restrict__ upd_s, RoundCounters *cnt) {
+    const int32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= slots) return;
+    const int32_t kept = kept_s[g];
+    const int32_t listed = listed_s[g];
+    const bool upd = kept > 0 && (mode == 1 || (mode == 2 && (int64_t(listed) * 4 <= kept ||
+                                                             listed < kRecomputeMinListed)));
+    upd_s[g] = upd ? 1 : 0;
+    if (kept > 0) {
+        atomicAdd(&cnt->kept, 1);
+        if (!upd) atomicAdd(&cnt->removed_tri, 1);
+    }
 }
 
 }  // namespace
@@ -217,7 +248,7 @@ cudaError_t launch_server_round_tail(const Live &cur, const int32_t *S, const ui
                                      int32_t *rp_out, int32_t *col_out, int32_t *eid_out,
                                      int32_t *gid_out, uint8_t *const *mask_ptr,
                                      int32_t *const *sup_ptr, cudaStream_t s, int *launches,
-                                     int32_t *S_out) {
+                                     int32_t *S_out, int32_t *kept_s) {
     finish_kernel<<<(slots + 255) / 256, 256, 0, s>>>(slots, kept_g, removed_g, fin, rounds_g);
     const int32_t vt = compact_tiles(cur.n);
     if (vt > 0) vertex_count_kernel<<<vt, kCompactThreads, 0, s>>>(gid, fin, cur.n, vtile_count);
@@ -235,7 +266,7 @@ cudaError_t launch_server_round_tail(const Live &cur, const int32_t *S, const ui
                                                            vmap, cur.m, etile_off, pos, col_out,
                                                            eid_out, mask_ptr, sup_ptr, S_out);
     vertex_rewrite_kernel<<<int((int64_t(cur.n) + 256) / 256), 256, 0, s>>>(
-        cur.rp, gid, fin, vmap, pos, cur.n, cur.m, cnt, &vcnt->kept, rp_out, gid_out);
+        cur.rp, gid, fin, vmap, pos, cur.n, cur.m, cnt, &vcnt->kept, rp_out, gid_out, kept_s);
     *launches += 6;
     return cudaGetLastError();
 }
@@ -243,9 +274,18 @@ cudaError_t launch_server_round_tail(const Live &cur, const int32_t *S, const ui
 cudaError_t launch_server_prune(const Live &cur, const int32_t *S, const int32_t *gid,
                                 const int32_t *thr, uint8_t *keep, int32_t *kept_g,
                                 int32_t *removed_g, cudaStream_t s, int *launches, int32_t *list,
-                                int32_t *list_count) {
+                                int32_t *list_count, int32_t *listed_s) {
     return launch_batch_keep(cur, S, gid, thr, keep, kept_g, removed_g, s, launches, list,
-                             list_count);
+                             list_count, listed_s);
+}
+
+cudaError_t launch_server_decide(int32_t slots, const int32_t *kept_s, const int32_t *listed_s,
+                                 int32_t mode, uint8_t *upd_s, RoundCounters *cnt, cudaStream_t s,
+                                 int *launches) {
+    server_decide_kernel<<<(slots + 255) / 256, 256, 0, s>>>(slots, kept_s, listed_s, mode, upd_s,
+                                                             cnt);
+    ++*launches;
+    return cudaGetLastError();
 }
 
 }  // namespace kt

@@ -116,3 +116,37 @@ def test_poisson_driver_completes_everything(kt):
         want = oracle.ktruss(g.row_ptr, g.col, K)
         assert np.array_equal(mask, want.mask) and np.array_equal(sup, want.support)
         assert r == want.rounds
+
+
+def test_budget_mix_of_staged_and_host_copied_requests(kt):
+    """A budget that holds about two requests: the first requests are staged on
+    the device at submit, later ones wait as host copies; every request still
+    completes in arrival order of admission with its solo result, into the
+    caller's own (larger than m) output arrays."""
+    reqs = [(gg.rmat(11, 8, seed=s), 3 + s % 4) for s in range(6)]
+    m_max = max(g.m for g, _ in reqs)
+    n_max = max(g.n for g, _ in reqs)
+    one = 4 * (n_max + 1 + m_max) + 5 * m_max + 768
+    srv = kt.Server(max_vertices=1 << 16, max_edges=1 << 20, max_requests=8,
+                    request_bytes=2 * one)
+    outs = [(np.full(g.m + 7, 9, np.uint8), np.full(g.m + 7, -5, np.int32)) for g, _ in reqs]
+    order = {}
+    for i, ((g, K), (mo, so)) in enumerate(zip(reqs, outs)):
+        order[srv.submit(g.row_ptr, g.col, K, mask_out=mo, support_out=so)] = i
+    results = {}
+    while len(results) < len(reqs):
+        for t, r, mask, sup in srv.step():
+            results[order[t]] = r
+    srv.close()
+    for k, ((g, K), (mo, so)) in enumerate(zip(reqs, outs)):
+        want = oracle.ktruss(g.row_ptr, g.col, K)
+        assert np.array_equal(mo[:g.m], want.mask) and np.array_equal(so[:g.m], want.support)
+        assert (mo[g.m:] == 9).all() and (so[g.m:] == -5).all()  # nothing past m written
+        assert results[k] == want.rounds
+    with pytest.raises(ValueError):
+        srv2 = kt.Server(max_vertices=100, max_edges=100, max_requests=2)
+        try:
+            g = gg.complete(6)
+            srv2.submit(g.row_ptr, g.col, 3, mask_out=np.zeros(3, np.uint8))  # too short
+        finally:
+            srv2.close()
