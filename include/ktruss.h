@@ -240,8 +240,9 @@ int ktruss_server_status(const ktruss_server *srv, int32_t *queued, int32_t *act
  * over its own CSR for each request it admits.  Each active request chooses
  * for itself: under AUTO it is recomputed (one support step over the live
  * CSR that skips every other request) when its removed edges that lie in
- * triangles number at least 65536 and exceed a quarter of its surviving
- * edges.  Results do not depend on it.  KTRUSS_EINVAL for another key or value. */
+ * triangles exceed a quarter of its surviving edges and either number at
+ * least 65536 or some other request is recomputed anyway.  Results do not
+ * depend on it.  KTRUSS_EINVAL for another key or value. */
 int ktruss_server_set_option(ktruss_server *srv, int32_t key, int64_t value);
 
 /* Releases the server and every buffer it holds (NULL is a no-op). */

@@ -101,11 +101,24 @@ __global__ void batch_done_kernel(int32_t G, const int32_t *__restrict__ kept_g,
     }
 }
 
+// First pass of the per-graph rule: cnt->forced = graphs whose listed edges
+// exceed a quarter of their survivors and number at least kRecomputeMinListed.
+__global__ void batch_force_kernel(int32_t G, const int32_t *__restrict__ vo,
+                                   const int32_t *__restrict__ rp_new,
+                                   const int32_t *__restrict__ listed_g, RoundCounters *cnt) {
+    const int32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= G) return;
+    const int32_t kept = rp_new[vo[g + 1]] - rp_new[vo[g]];
+    const int32_t listed = listed_g[g];
+    if (kept > 0 && listed >= kRecomputeMinListed && int64_t(listed) * 4 > kept)
+        atomicAdd(&cnt->forced, 1);
+}
+
 // Per graph after a round's compaction (rp_new: the new row pointers, graph g
 // owns vertices [vo[g], vo[g+1])): its surviving edges, and whether its next
 // supports come from the update of this round (upd_g = 1) or from a support
-// step (0).  mode: 0 never update, 1 always, 2 the kRecomputeMinListed rule.
-// Counts the graphs that stay live
+// step (0).  mode: 0 never update, 1 always, 2 the kRecomputeMinListed rule
+// (cnt->forced: the graphs of batch_force_kernel).  Counts the graphs that stay live
 // (cnt->kept) and those that need a support step (cnt->removed_tri).
 __global__ void batch_decide_kernel(int32_t G, const int32_t *__restrict__ vo,
                                     const int32_t *__restrict__ rp_new,
@@ -116,7 +129,8 @@ __global__ void batch_decide_kernel(int32_t G, const int32_t *__restrict__ vo,
     const int32_t kept = rp_new[vo[g + 1]] - rp_new[vo[g]];
     const int32_t listed = listed_g[g];
     const bool upd = kept > 0 && (mode == 1 || (mode == 2 && (int64_t(listed) * 4 <= kept ||
-                                                             listed < kRecomputeMinListed)));
+                                                             (listed < kRecomputeMinListed &&
+                                                              cnt->forced == 0))));
     upd_g[g] = upd ? 1 : 0;
     if (kept > 0) {
         atomicAdd(&cnt->kept, 1);
@@ -268,6 +282,10 @@ cudaError_t launch_batch_decide(int32_t G, const int32_t *vo, const int32_t *rp_
                                 RoundCounters *cnt, cudaStream_t s, int *launches) {
     cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(RoundCounters), s);
     if (e != cudaSuccess) return e;
+    if (mode == 2) {
+        batch_force_kernel<<<(G + 255) / 256, 256, 0, s>>>(G, vo, rp_new, listed_g, cnt);
+        ++*launches;
+    }
     batch_decide_kernel<<<(G + 255) / 256, 256, 0, s>>>(G, vo, rp_new, listed_g, mode, upd_g, cnt);
     ++*launches;
     return cudaGetLastError();

@@ -36,7 +36,8 @@ struct RoundCounters {
     int32_t kept;                  // edges with support >= K-2
     int32_t error;                 // nonzero: a kernel detected an inconsistency
     int32_t removed_tri;           // removed edges with support > 0 (listed by prune)
-    int32_t pad_;
+    int32_t forced;                // per-graph decisions: graphs that need a support step
+                                   // whatever the others do (first decision pass)
 };
 
 // Device error bits in RoundCounters::error during a run.
@@ -51,9 +52,11 @@ constexpr int32_t kDefaultLight = 64;
 constexpr int32_t kMaxLight = 1024;
 // Per-graph update rule of batches and the server: a graph's next supports
 // come from the decremental update while its listed edges (removed, in some
-// triangle) are at most a quarter of its surviving edges, or fewer than this:
-// a support step for a few graphs still classifies every live edge, which
-// only pays off for a graph that would otherwise update many edges.
+// triangle) are at most a quarter of its surviving edges.  A graph above that
+// with fewer than kRecomputeMinListed listed edges still takes the update
+// when no graph needs a support step otherwise: a support step for a few
+// small graphs classifies every live edge of the batch, which only pays off
+// once some graph needs one anyway.
 constexpr int32_t kRecomputeMinListed = 1 << 16;
 
 // KTRUSS_TRACE=2 (or more): the launchers synchronise the stream after each

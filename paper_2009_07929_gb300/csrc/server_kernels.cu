@@ -209,6 +209,16 @@ __global__ void vertex_rewrite_kernel(const int32_t *__restrict__ rp, const int3
     if (v == 0) rp_out[*vtotal] = cnt->kept;
 }
 
+// Per slot: its first decision pass (batch_force_kernel).
+__global__ void server_force_kernel(int32_t slots, const int32_t *__restrict__ kept_s,
+                                    const int32_t *__restrict__ listed_s, RoundCounters *cnt) {
+    const int32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= slots) return;
+    const int32_t kept = kept_s[g], listed = listed_s[g];
+    if (kept > 0 && listed >= kRecomputeMinListed && int64_t(listed) * 4 > kept)
+        atomicAdd(&cnt->forced, 1);
+}
+
 // Per slot: update or support step next step (the rule of batch_decide_kernel
 // on the slot's surviving and listed edges).
 __global__ void server_decide_kernel(int32_t slots, const int32_t *__restrict__ kept_s,
@@ -219,7 +229,8 @@ __global__ void server_decide_kernel(int32_t slots, const int32_t *__restrict__ 
     const int32_t kept = kept_s[g];
     const int32_t listed = listed_s[g];
     const bool upd = kept > 0 && (mode == 1 || (mode == 2 && (int64_t(listed) * 4 <= kept ||
-                                                             listed < kRecomputeMinListed)));
+                                                             (listed < kRecomputeMinListed &&
+                                                              cnt->forced == 0))));
     upd_s[g] = upd ? 1 : 0;
     if (kept > 0) {
         atomicAdd(&cnt->kept, 1);
@@ -282,6 +293,10 @@ cudaError_t launch_server_prune(const Live &cur, const int32_t *S, const int32_t
 cudaError_t launch_server_decide(int32_t slots, const int32_t *kept_s, const int32_t *listed_s,
                                  int32_t mode, uint8_t *upd_s, RoundCounters *cnt, cudaStream_t s,
                                  int *launches) {
+    if (mode == 2) {
+        server_force_kernel<<<(slots + 255) / 256, 256, 0, s>>>(slots, kept_s, listed_s, cnt);
+        ++*launches;
+    }
     server_decide_kernel<<<(slots + 255) / 256, 256, 0, s>>>(slots, kept_s, listed_s, mode, upd_s,
                                                              cnt);
     ++*launches;
