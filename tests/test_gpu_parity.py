@@ -494,9 +494,10 @@ def test_full_size_against_oracle_digests(kt, name):
 def test_rmat23_cliques_k3_sampled_and_kmax_sweep(kt):
     """Config 3 at full size: K=3 checked on sampled edges against per-edge
     oracle supports (for K=3 the kept edges are exactly those in a triangle and
-    keep their full-graph support); then K rises to the largest non-empty truss,
-    checking size-independent properties at every K and sampled supports inside
-    the truss for a few K."""
+    keep their full-graph support); then a ladder of K up to the largest
+    non-empty truss (from the decomposition) and one past it, checking
+    size-independent properties at every K and sampled supports inside the
+    truss for a few K."""
     import torch
     g = gg.cached_workload("rmat23c", 0)
     h = kt.load(torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col).cuda())
@@ -516,31 +517,27 @@ def test_rmat23_cliques_k3_sampled_and_kmax_sweep(kt):
     assert np.array_equal(sup3[q], full)
     assert np.array_equal(mask3[q], (full >= 1).astype(np.uint8))
     assert int(sup3.astype(np.int64).sum()) == 3 * st.triangles_out
+    assert np.array_equal(mask3, (tr >= 3).astype(np.uint8))
+    # a 200-clique was planted, so the 200-truss is non-empty
+    assert kmax_dec >= 200 and (tr == kmax_dec).any() and not (tr > kmax_dec).any()
+    ladder = sorted({4, 5, 6, 8, 12, 20, 50, 100, 200, (200 + kmax_dec) // 2, kmax_dec,
+                     kmax_dec + 1})
     prev = mask3
-    K = 4
-    kmax = 3
-    while True:
+    for K in ladder:
         m_t, s_t = h.run(K)
         torch.cuda.synchronize()
         mask, sup = m_t.cpu().numpy(), s_t.cpu().numpy()
         st = h.stats()
-        if not mask.any():
-            break
-        kmax = K
+        if K > kmax_dec:
+            assert not mask.any() and not sup.any()
+            continue
         assert np.array_equal(mask, (tr >= K).astype(np.uint8))
         assert (sup[mask == 1] >= K - 2).all() and (sup[mask == 0] == 0).all()
         assert not np.any((mask == 1) & (prev == 0))
         assert int(sup.astype(np.int64).sum()) == 3 * st.triangles_out
-        if K in (6, 20, 100, 199) or mask.sum() < 50000:
+        if K in (6, 100, 200, kmax_dec) or mask.sum() < 50000:
             kept = np.flatnonzero(mask)
             qs = kept if kept.size <= 3000 else rng.choice(kept, 3000, replace=False)
             assert np.array_equal(sup[qs], oracle.edge_support(g.row_ptr, g.col, qs, keep=mask))
         prev = mask
-        K += 1 if K < 20 or K > 190 else 10
-        if K > 400:
-            break
-    # a 200-clique was planted, so the 200-truss is non-empty
-    assert kmax >= 200
-    assert kmax_dec >= kmax and not (tr > kmax_dec).any()
-    assert np.array_equal(mask3, (tr >= 3).astype(np.uint8))
     h.close()
