@@ -214,8 +214,13 @@ int ktruss_server_create(ktruss_server **out, int32_t max_vertices, int64_t max_
  * mask_out (uint8[m]) and support_out (int32[m] or NULL) are HOST buffers the
  * caller keeps valid until the request is reported done; they are written
  * when it completes.  The request's device bytes are 4(n+1+m) + 5m + 768.
- * *ticket_out (may be NULL) identifies it.  KTRUSS_EINVAL for bad arguments,
- * a malformed CSR, or a graph that could never fit the server's capacities.
+ * While they fit in what the budget has left and no request waits as a host
+ * copy, the graph is copied straight to a device block and validated there
+ * (the call synchronises the server's stream), and the request holds its
+ * budget from then on; otherwise it is validated and copied on host threads
+ * and staged at admission.  *ticket_out (may be NULL) identifies it.
+ * KTRUSS_EINVAL for bad arguments, a malformed CSR, or a graph that could
+ * never fit the server's capacities; KTRUSS_ENOMEM, KTRUSS_ECUDA.
  */
 int ktruss_server_submit(ktruss_server *srv, int32_t n, int64_t m, const int32_t *row_ptr,
                          const int32_t *col, int32_t K, uint8_t *mask_out, int32_t *support_out,

@@ -1,22 +1,25 @@
 // K-truss request server: continuous batching of many K-truss queries.
 //
 // Requests (a graph in host memory and its K) are queued by
-// ktruss_server_submit.  Each ktruss_server_step:
+// ktruss_server_submit, which stages the graph on the device and validates
+// it there while the budget has room (else it keeps a validated host copy
+// until admission).  Each ktruss_server_step:
 //   1. admits queued requests in arrival order while they fit: a free slot,
 //      room in the live CSR (vertices, edges) and in the device budget for
 //      the request's own input staging and output buffers (its HBM
-//      footprint); an admitted request's graph is copied to the device and
-//      appended to the live CSR;
+//      footprint); an admitted request's graph is appended to the live CSR;
 //   2. runs one peel round (supports of every active request, then each
 //      request pruned with its own threshold) — the rounds of all active
-//      requests are one batched computation on the device.  Supports come
-//      from one support step over the whole live CSR, or (decremental update,
-//      the default) from the previous step's supports updated for the edges
-//      it removed, plus a support step of each request admitted in this step
-//      over its own CSR;
+//      requests are one batched computation on the device.  Each request
+//      admitted in this step gets a support step over its own CSR; the older
+//      requests keep the previous step's supports updated for the edges it
+//      removed (decremental update, the default), except those whose own
+//      rule chose a support step, which get one (masked) step over the older
+//      part of the live CSR;
 //   3. finishes the requests whose round removed nothing or removed every
 //      live edge (their outputs are already in their device buffers), copies
-//      their outputs to the caller's host buffers and frees their memory.
+//      their outputs to the caller's host buffers and returns their device
+//      blocks to the cache.
 // A request therefore goes through exactly the bulk rounds of its own
 // ktruss_run, whatever else is in flight (the paper's Alg. 1 per request).
 #include <cuda_runtime.h>
