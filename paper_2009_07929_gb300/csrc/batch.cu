@@ -93,8 +93,9 @@ batch_prune_kernel(const int32_t *__restrict__ S, const int32_t *__restrict__ co
 __global__ void batch_done_kernel(int32_t G, const int32_t *__restrict__ kept_g,
                                   const int32_t *__restrict__ removed_g,
                                   uint8_t *__restrict__ done, int32_t *__restrict__ rounds_g) {
-    const int32_t g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= G) return;
+    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t >= G) return;
+    const int32_t g = int32_t(t);
     if (kept_g[g] || removed_g[g]) {
         rounds_g[g] += 1;
         done[g] = removed_g[g] == 0;
@@ -106,8 +107,9 @@ __global__ void batch_done_kernel(int32_t G, const int32_t *__restrict__ kept_g,
 __global__ void batch_force_kernel(int32_t G, const int32_t *__restrict__ vo,
                                    const int32_t *__restrict__ rp_new,
                                    const int32_t *__restrict__ listed_g, RoundCounters *cnt) {
-    const int32_t g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= G) return;
+    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t >= G) return;
+    const int32_t g = int32_t(t);
     const int32_t kept = rp_new[vo[g + 1]] - rp_new[vo[g]];
     const int32_t listed = listed_g[g];
     if (kept > 0 && listed >= kRecomputeMinListed && int64_t(listed) * 4 > kept)
@@ -124,8 +126,9 @@ __global__ void batch_decide_kernel(int32_t G, const int32_t *__restrict__ vo,
                                     const int32_t *__restrict__ rp_new,
                                     const int32_t *__restrict__ listed_g, int32_t mode,
                                     uint8_t *__restrict__ upd_g, RoundCounters *cnt) {
-    const int32_t g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= G) return;
+    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t >= G) return;
+    const int32_t g = int32_t(t);
     const int32_t kept = rp_new[vo[g + 1]] - rp_new[vo[g]];
     const int32_t listed = listed_g[g];
     const bool upd = kept > 0 && (mode == 1 || (mode == 2 && (int64_t(listed) * 4 <= kept ||
@@ -228,7 +231,7 @@ batch_compact_kernel(const int32_t *__restrict__ col, const int32_t *__restrict_
 cudaError_t launch_graph_of_vertex(const int32_t *vo, int32_t G, int32_t n, int32_t *gid,
                                    cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    graph_of_vertex_kernel<<<(n + 255) / 256, 256, 0, s>>>(vo, G, n, gid);
+    graph_of_vertex_kernel<<<int((int64_t(n) + 255) / 256), 256, 0, s>>>(vo, G, n, gid);
     return cudaGetLastError();
 }
 
@@ -246,7 +249,7 @@ cudaError_t launch_batch_keep(const Live &g, const int32_t *S, const int32_t *gi
                               int32_t *removed_g, cudaStream_t s, int *launches, int32_t *list,
                               int32_t *list_count, int32_t *listed_g) {
     if (g.m == 0) return cudaSuccess;
-    batch_prune_kernel<<<(g.m + 255) / 256, 256, 0, s>>>(S, g.col, g.m, gid, thr, keep, kept_g,
+    batch_prune_kernel<<<int((int64_t(g.m) + 255) / 256), 256, 0, s>>>(S, g.col, g.m, gid, thr, keep, kept_g,
                                                          removed_g, list, list_count, nullptr,
                                                          listed_g);
     ++*launches;
@@ -263,10 +266,10 @@ cudaError_t launch_batch_prune(const Live &g, const int32_t *S, const int32_t *g
         cudaError_t e = cudaMemsetAsync(&cnt->removed_tri, 0, sizeof(int32_t), s);
         if (e != cudaSuccess) return e;
     }
-    batch_prune_kernel<<<(g.m + 255) / 256, 256, 0, s>>>(S, g.col, g.m, gid, thr, keep, kept_g,
+    batch_prune_kernel<<<int((int64_t(g.m) + 255) / 256), 256, 0, s>>>(S, g.col, g.m, gid, thr, keep, kept_g,
                                                          removed_g, list, &cnt->removed_tri, ldeg,
                                                          listed_g);
-    batch_done_kernel<<<(G + 255) / 256, 256, 0, s>>>(G, kept_g, removed_g, done, rounds_g);
+    batch_done_kernel<<<int((int64_t(G) + 255) / 256), 256, 0, s>>>(G, kept_g, removed_g, done, rounds_g);
     const int32_t tiles = compact_tiles(g.m);
     batch_count_kernel<<<tiles, kCompactThreads, 0, s>>>(keep, done, gid, g.col, g.m, tile_count);
     *launches += 3;
@@ -283,10 +286,10 @@ cudaError_t launch_batch_decide(int32_t G, const int32_t *vo, const int32_t *rp_
     cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(RoundCounters), s);
     if (e != cudaSuccess) return e;
     if (mode == 2) {
-        batch_force_kernel<<<(G + 255) / 256, 256, 0, s>>>(G, vo, rp_new, listed_g, cnt);
+        batch_force_kernel<<<int((int64_t(G) + 255) / 256), 256, 0, s>>>(G, vo, rp_new, listed_g, cnt);
         ++*launches;
     }
-    batch_decide_kernel<<<(G + 255) / 256, 256, 0, s>>>(G, vo, rp_new, listed_g, mode, upd_g, cnt);
+    batch_decide_kernel<<<int((int64_t(G) + 255) / 256), 256, 0, s>>>(G, vo, rp_new, listed_g, mode, upd_g, cnt);
     ++*launches;
     return cudaGetLastError();
 }

@@ -224,7 +224,7 @@ cudaError_t launch_rowptr(const Live &in, const int32_t *pos, const RoundCounter
 cudaError_t launch_finalize(const Live &g, const int32_t *S, uint8_t *mask_out,
                             int32_t *support_out, cudaStream_t s, int *launches) {
     if (g.m == 0) return cudaSuccess;
-    finalize_kernel<<<(g.m + 255) / 256, 256, 0, s>>>(g.eid, S, g.m, mask_out, support_out);
+    finalize_kernel<<<int((int64_t(g.m) + 255) / 256), 256, 0, s>>>(g.eid, S, g.m, mask_out, support_out);
     ++*launches;
     return cudaGetLastError();
 }

@@ -175,7 +175,9 @@ constexpr int kCompactThreads = 256;
 constexpr int kCompactItemsPerThread = 16;
 constexpr int kCompactTile = kCompactThreads * kCompactItemsPerThread;
 
-inline int32_t compact_tiles(int32_t m) { return (m + kCompactTile - 1) / kCompactTile; }
+inline int32_t compact_tiles(int32_t m) {
+    return int32_t((int64_t(m) + kCompactTile - 1) / kCompactTile);
+}
 
 // Counts edges with S >= thr per tile into tile_count[tiles], then scans the
 // tile counts into tile_off[tiles] and writes the total into cnt->kept.  When

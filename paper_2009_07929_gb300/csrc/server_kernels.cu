@@ -41,8 +41,9 @@ __global__ void append_kernel(const int32_t *__restrict__ rp_in, const int32_t *
 __global__ void finish_kernel(int32_t slots, const int32_t *__restrict__ kept_g,
                               const int32_t *__restrict__ removed_g, uint8_t *__restrict__ fin,
                               int32_t *__restrict__ rounds_g) {
-    const int32_t g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= slots) return;
+    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t >= slots) return;
+    const int32_t g = int32_t(t);
     if (kept_g[g] || removed_g[g]) {
         rounds_g[g] += 1;
         fin[g] = removed_g[g] == 0 || kept_g[g] == 0;
@@ -212,8 +213,9 @@ __global__ void vertex_rewrite_kernel(const int32_t *__restrict__ rp, const int3
 // Per slot: its first decision pass (batch_force_kernel).
 __global__ void server_force_kernel(int32_t slots, const int32_t *__restrict__ kept_s,
                                     const int32_t *__restrict__ listed_s, RoundCounters *cnt) {
-    const int32_t g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= slots) return;
+    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t >= slots) return;
+    const int32_t g = int32_t(t);
     const int32_t kept = kept_s[g], listed = listed_s[g];
     if (kept > 0 && listed >= kRecomputeMinListed && int64_t(listed) * 4 > kept)
         atomicAdd(&cnt->forced, 1);
@@ -224,8 +226,9 @@ __global__ void server_force_kernel(int32_t slots, const int32_t *__restrict__ k
 __global__ void server_decide_kernel(int32_t slots, const int32_t *__restrict__ kept_s,
                                      const int32_t *__restrict__ listed_s, int32_t mode,
                                      uint8_t *__restrict__ upd_s, RoundCounters *cnt) {
-    const int32_t g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= slots) return;
+    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t >= slots) return;
+    const int32_t g = int32_t(t);
     const int32_t kept = kept_s[g];
     const int32_t listed = listed_s[g];
     const bool upd = kept > 0 && (mode == 1 || (mode == 2 && (int64_t(listed) * 4 <= kept ||
@@ -260,7 +263,7 @@ cudaError_t launch_server_round_tail(const Live &cur, const int32_t *S, const ui
                                      int32_t *gid_out, uint8_t *const *mask_ptr,
                                      int32_t *const *sup_ptr, cudaStream_t s, int *launches,
                                      int32_t *S_out, int32_t *kept_s) {
-    finish_kernel<<<(slots + 255) / 256, 256, 0, s>>>(slots, kept_g, removed_g, fin, rounds_g);
+    finish_kernel<<<int((int64_t(slots) + 255) / 256), 256, 0, s>>>(slots, kept_g, removed_g, fin, rounds_g);
     const int32_t vt = compact_tiles(cur.n);
     if (vt > 0) vertex_count_kernel<<<vt, kCompactThreads, 0, s>>>(gid, fin, cur.n, vtile_count);
     cudaError_t e = launch_scan_tiles(vtile_count, vt, vtile_off, vcnt, s, launches);
@@ -294,10 +297,10 @@ cudaError_t launch_server_decide(int32_t slots, const int32_t *kept_s, const int
                                  int32_t mode, uint8_t *upd_s, RoundCounters *cnt, cudaStream_t s,
                                  int *launches) {
     if (mode == 2) {
-        server_force_kernel<<<(slots + 255) / 256, 256, 0, s>>>(slots, kept_s, listed_s, cnt);
+        server_force_kernel<<<int((int64_t(slots) + 255) / 256), 256, 0, s>>>(slots, kept_s, listed_s, cnt);
         ++*launches;
     }
-    server_decide_kernel<<<(slots + 255) / 256, 256, 0, s>>>(slots, kept_s, listed_s, mode, upd_s,
+    server_decide_kernel<<<int((int64_t(slots) + 255) / 256), 256, 0, s>>>(slots, kept_s, listed_s, mode, upd_s,
                                                              cnt);
     ++*launches;
     return cudaGetLastError();

@@ -25,10 +25,12 @@ __global__ void __launch_bounds__(256)
 support_edge_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, int32_t n,
                     int32_t m, int32_t *__restrict__ S, unsigned long long *__restrict__ tri,
                     const int32_t *__restrict__ gid, const uint8_t *__restrict__ skip) {
-    const int32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const bool live = t < m;
+    const int32_t e = live ? int32_t(t) : 0;
     int32_t own = 0;
-    const int32_t i = e < m ? row_of_slot(rp, n, e) : 0;
-    if (e < m && !(skip && skip[gid[i]])) {
+    const int32_t i = live ? row_of_slot(rp, n, e) : 0;
+    if (live && !(skip && skip[gid[i]])) {
         const int32_t kappa = __ldg(col + e);
         int32_t x = e + 1;
         const int32_t xe = __ldg(rp + i + 1);
@@ -63,9 +65,10 @@ __global__ void __launch_bounds__(256)
 support_coarse_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, int32_t n,
                       int32_t *__restrict__ S, unsigned long long *__restrict__ tri,
                       const int32_t *__restrict__ gid, const uint8_t *__restrict__ skip) {
-    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int32_t i = t < n ? int32_t(t) : 0;
     long long found = 0;
-    if (i < n && !(skip && skip[gid[i]])) {
+    if (t < n && !(skip && skip[gid[i]])) {
         const int32_t rb = __ldg(rp + i), re = __ldg(rp + i + 1);
         for (int32_t e = rb; e < re; ++e) {
             const int32_t kappa = __ldg(col + e);
@@ -100,7 +103,7 @@ support_coarse_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict_
 cudaError_t launch_support_coarse(const Live &g, int32_t *S, RoundCounters *cnt, cudaStream_t s) {
     if (g.m == 0) return cudaSuccess;
     const int threads = 256;
-    const int blocks = (g.n + threads - 1) / threads;
+    const int blocks = int((int64_t(g.n) + threads - 1) / threads);
     support_coarse_kernel<<<blocks, threads, 0, s>>>(g.rp, g.col, g.n, S, &cnt->triangles, g.gid,
                                                      g.skip);
     return cudaGetLastError();
@@ -109,7 +112,7 @@ cudaError_t launch_support_coarse(const Live &g, int32_t *S, RoundCounters *cnt,
 cudaError_t launch_support_edge(const Live &g, int32_t *S, RoundCounters *cnt, cudaStream_t s) {
     if (g.m == 0) return cudaSuccess;
     const int threads = 256;
-    const int blocks = (g.m + threads - 1) / threads;
+    const int blocks = int((int64_t(g.m) + threads - 1) / threads);
     support_edge_kernel<<<blocks, threads, 0, s>>>(g.rp, g.col, g.n, g.m, S, &cnt->triangles,
                                                    g.gid, g.skip);
     return cudaGetLastError();
