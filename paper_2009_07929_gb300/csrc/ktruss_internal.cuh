@@ -272,7 +272,9 @@ cudaError_t launch_server_decide(int32_t slots, const int32_t *kept_s, const int
                                  int *launches);
 // Finished slots, vertex renumbering (vcnt->kept = surviving vertices),
 // edge compaction (cnt->kept = surviving edges) with outputs of leaving edges
-// through the per-slot pointer tables, new row pointers and slot ids.
+// through the per-slot pointer tables, new row pointers and slot ids.  When
+// given, S_out receives the S of the surviving edges in their new order and
+// kept_s (zero on entry) each slot's surviving edges.
 cudaError_t launch_server_round_tail(const Live &cur, const int32_t *S, const uint8_t *keep,
                                      const int32_t *kept_g, const int32_t *removed_g,
                                      uint8_t *fin, int32_t *rounds_g, int32_t slots,
