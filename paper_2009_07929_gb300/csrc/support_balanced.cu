@@ -1255,7 +1255,7 @@ cudaError_t launch_support_balanced(const Live &g, int32_t *S, RoundCounters *cn
     active_rows_kernel<<<int((rows + 255) / 256), 256, 0, s>>>(c.rcount, c.rstart, c.arank,
                                                                c.rtot, n, c.arow, c.aseg);
     trace_phase(s, "row scan + active rows");
-    scatter_kernel<<<int((int64_t(m) + 255) / 256), 256, 0, s>>>(c.ekey, c.epst, c.eitems, m, c.rstart,
+    scatter_kernel<<<(m + 255) / 256, 256, 0, s>>>(c.ekey, c.epst, c.eitems, m, c.rstart,
                                                    c.arank, c.rcount, c.seg, c.pst, c.sitems,
                                                    c.sact);
     trace_phase(s, "scatter");
