@@ -75,3 +75,25 @@ def test_algorithmic_bytes_formula():
     import bench
     # 4 bytes per merge element, 8 per live edge, 16 per triangle, 8 per row pointer
     assert bench.algorithmic_bytes(n=3, live=2, merge=10, tris=1) == 40 + 16 + 16 + 32
+
+
+def test_traffic_record_is_bound_to_the_profiled_source_and_workload(tmp_path, monkeypatch):
+    """An ncu traffic record is used only for the kernel source it was captured
+    on (its sha256) and for its own workload and K."""
+    import hashlib
+    sys.path.insert(0, ROOT)
+    import bench
+    src = tmp_path / "paper_2009_07929_gb300" / "csrc" / "support_balanced.cu"
+    src.parent.mkdir(parents=True)
+    src.write_bytes(b"// kernel source as captured\n")
+    (tmp_path / "profiles").mkdir()
+    rec = {"kernel": "support_kernel", "workload": "rmat20 K=3 round 1",
+           "source_sha256": hashlib.sha256(src.read_bytes()).hexdigest(),
+           "dram_bytes_per_launch": 123456}
+    (tmp_path / "profiles" / "support_traffic.json").write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.traffic_record("rmat20", 3)["dram_bytes_per_launch"] == 123456
+    assert bench.traffic_record("rmat20", 4) is None
+    assert bench.traffic_record("rmat23c", 3) is None
+    src.write_bytes(b"// kernel source changed after the capture\n")
+    assert bench.traffic_record("rmat20", 3) is None
