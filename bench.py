@@ -78,6 +78,8 @@ class ClockSampler:
         self.proc = None
         self.lines = []
         self.t = None
+        self.first = threading.Event()
+        self.t_start = 0.0
 
     def __enter__(self):
         try:
@@ -87,13 +89,18 @@ class ClockSampler:
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            # nvidia-smi takes a moment to start: let its first sample arrive
+            # before the timed region begins, so that the region is sampled
+            self.first.wait(timeout=2.0)
         except OSError:
             self.proc = None
+        self.t_start = time.perf_counter()
         return self
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+            self.first.set()
 
     def __exit__(self, *a):
         if self.proc is not None:
@@ -105,9 +112,15 @@ class ClockSampler:
             self.t.join(timeout=2)
 
     def summary(self):
+        """Median SM clock, maximum clock and throttle reasons of the samples
+        taken inside the timed region (the last earlier sample when the region
+        was too short to hold one)."""
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        inside = [ln for t, ln in self.lines if t >= self.t_start]
+        if not inside:
+            inside = [ln for _, ln in self.lines][-1:]
+        for ln in inside:
             parts = [x.strip() for x in ln.split(",")]
             if len(parts) < 9:
                 continue

@@ -97,3 +97,19 @@ def test_traffic_record_is_bound_to_the_profiled_source_and_workload(tmp_path, m
     assert bench.traffic_record("rmat23c", 3) is None
     src.write_bytes(b"// kernel source changed after the capture\n")
     assert bench.traffic_record("rmat20", 3) is None
+
+
+def test_clock_summary_uses_samples_inside_the_timed_region():
+    sys.path.insert(0, ROOT)
+    import bench
+    c = bench.ClockSampler(0)
+    row = "0, {sm}, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, {cap}"
+    c.lines = [(1.0, row.format(sm=1200, cap="Not Active"))]  # before the region
+    c.t_start = 2.0
+    assert c.summary()["sm_mhz"] == 1200 and c.summary()["samples"] == 1  # only one: kept
+    c.lines += [(2.1, row.format(sm=2070, cap="Active")), (2.3, row.format(sm=2050, cap="Not Active"))]
+    s = c.summary()
+    assert s["sm_mhz"] == 2060 and s["sm_max_mhz"] == 2070 and s["samples"] == 2
+    assert s["reasons"] == ["sw_power_cap"]
+    c.lines = []
+    assert c.summary()["reasons"] == ["unsampled"]
