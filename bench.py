@@ -80,6 +80,7 @@ class ClockSampler:
         self.t = None
         self.first = threading.Event()
         self.t_start = 0.0
+        self.t_end = float("inf")
 
     def __enter__(self):
         try:
@@ -103,6 +104,7 @@ class ClockSampler:
             self.first.set()
 
     def __exit__(self, *a):
+        self.t_end = time.perf_counter()
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -117,9 +119,9 @@ class ClockSampler:
         was too short to hold one)."""
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        inside = [ln for t, ln in self.lines if t >= self.t_start]
+        inside = [ln for t, ln in self.lines if self.t_start <= t <= self.t_end]
         if not inside:
-            inside = [ln for _, ln in self.lines][-1:]
+            inside = [ln for t, ln in self.lines if t < self.t_start][-1:]
         for ln in inside:
             parts = [x.strip() for x in ln.split(",")]
             if len(parts) < 9:
@@ -537,6 +539,11 @@ def main():
             # what bounds the kernel: SM instruction issue (fraction of issue
             # slots active, ncu), not HBM bandwidth (dram_frac)
             roofline["sm_issue_active"] = tr["sm_issue_active"]
+        # L2 sector hit rate and warp execution efficiency (active threads per
+        # executed warp instruction / 32) of the same capture
+        for key in ("l2_hit_rate", "warp_exec_efficiency"):
+            if key in tr:
+                roofline[key] = tr[key]
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tot_ms / args.steps, 4),

@@ -111,5 +111,9 @@ def test_clock_summary_uses_samples_inside_the_timed_region():
     s = c.summary()
     assert s["sm_mhz"] == 2060 and s["sm_max_mhz"] == 2070 and s["samples"] == 2
     assert s["reasons"] == ["sw_power_cap"]
+    # a sample taken after the region ended is not part of it
+    c.t_end = 2.5
+    c.lines.append((2.7, row.format(sm=900, cap="Not Active")))
+    assert c.summary()["sm_mhz"] == 2060 and c.summary()["samples"] == 2
     c.lines = []
     assert c.summary()["reasons"] == ["unsampled"]
