@@ -266,6 +266,13 @@ def batch_config(count: int, seed: int = 0, m_lo: float = 1e3, m_hi: float = 2e6
     with scale clamp(ceil(log2(m/16)), 10, 17) and edge factor 16 (their size
     is what that scale gives).  Each graph has a K drawn uniformly from
     [k_lo, k_hi].  Returns a list of (CSR, K)."""
+    return _generate(batch_specs(count, seed, m_lo, m_hi, k_lo, k_hi))
+
+
+def batch_specs(count: int, seed: int = 0, m_lo: float = 1e3, m_hi: float = 2e6,
+                k_lo: int = 3, k_hi: int = 12):
+    """The (spec, K) pairs of batch_config without building the graphs; graph
+    g of the batch is from_spec(spec) of pair g."""
     import math
     key = stream_key(5, seed, count)
     specs = []
@@ -281,7 +288,14 @@ def batch_config(count: int, seed: int = 0, m_lo: float = 1e3, m_hi: float = 2e6
         else:
             scale = min(17, max(10, int(math.ceil(math.log2(max(mt, 1) / 16.0)))))
             specs.append((("rmat", scale, 16, sub_seed), K))
-    return _generate(specs)
+    return specs
+
+
+def from_spec(spec):
+    """The graph of one spec of batch_specs: ("er", n, m, seed) or
+    ("rmat", scale, edge_factor, seed)."""
+    kind, a, b, sd = spec
+    return er(a, b, sd) if kind == "er" else rmat(a, b, sd)
 
 
 def _generate(specs):
@@ -290,14 +304,10 @@ def _generate(specs):
     import os
     from concurrent.futures import ThreadPoolExecutor
 
-    def one(spec):
-        kind, a, b, sd = spec
-        return er(a, b, sd) if kind == "er" else rmat(a, b, sd)
-
     _load()
     workers = max(1, min(len(specs), os.cpu_count() or 1))
     with ThreadPoolExecutor(max_workers=workers) as ex:
-        graphs = list(ex.map(one, [sp for sp, _ in specs]))
+        graphs = list(ex.map(from_spec, [sp for sp, _ in specs]))
     return [(g, K) for g, (_, K) in zip(graphs, specs)]
 
 

@@ -9,6 +9,13 @@ large to rerun the oracle on in a test.
 
     python tests/golden/make_golden.py rmat20 rmat20r      # config 2
     python tests/golden/make_golden.py rmat23c --K 3       # config 3, K=3
+    python tests/golden/make_golden.py batch --jobs 8      # config 4, 4096 graphs
+
+The batching workload (graphgen.batch_config: 4096 graphs, 1e3..2e6 edges,
+K per graph in 3..12, seed 0) is stored per graph (K, rounds, kept edges) and
+as digests of digests: the SHA-256 of the concatenated hex SHA-256 digests of
+every graph's mask (resp. little-endian int32 supports, resp. CSR), in batch
+order.
 """
 from __future__ import annotations
 
@@ -61,6 +68,66 @@ def one(args):
     }
 
 
+BATCH = {"graphs": 4096, "seed": 0, "m_lo": 1e3, "m_hi": 2e6, "k_lo": 3, "k_hi": 12}
+
+
+def one_batch_graph(args):
+    k, spec, K = args
+    import numpy as np
+    import graphgen as gg
+    import oracle
+    g = gg.from_spec(spec)
+    t0 = time.time()
+    r = oracle.ktruss(g.row_ptr, g.col, K)
+    dt = time.time() - t0
+    return {"index": k, "K": K, "m": g.m, "graph_sha256": graph_digest(g), "rounds": r.rounds,
+            "edges_out": int(r.mask.sum()), "triangles_out": int(r.triangles),
+            "support_sum": int(r.support.astype(np.int64).sum()),
+            "mask_sha256": sha(np.ascontiguousarray(r.mask, dtype=np.uint8)),
+            "support_sha256": sha(np.ascontiguousarray(r.support, dtype="<i4")),
+            "seconds": dt}
+
+
+def digest_of_digests(hexes) -> str:
+    return hashlib.sha256("".join(hexes).encode("ascii")).hexdigest()
+
+
+def make_batch(jobs: int):
+    import graphgen as gg
+    specs = gg.batch_specs(BATCH["graphs"], BATCH["seed"], BATCH["m_lo"], BATCH["m_hi"],
+                           BATCH["k_lo"], BATCH["k_hi"])
+    tasks = [(k, sp, K) for k, (sp, K) in enumerate(specs)]
+    # largest graphs first, so that the pool ends evenly
+    tasks.sort(key=lambda t: -(t[1][2] if t[1][0] == "er" else t[1][2] << t[1][1]))
+    t0 = time.time()
+    with mp.get_context("spawn").Pool(jobs) as pool:
+        res = pool.map(one_batch_graph, tasks, chunksize=1)
+    res.sort(key=lambda r: r["index"])
+    out = dict(BATCH)
+    out.update({
+        "source": "oracle.ktruss (CPU) on every graph of graphgen.batch_config, "
+                  "tests/golden/make_golden.py",
+        "edges": sum(r["m"] for r in res),
+        "graphs_sha256": digest_of_digests(r["graph_sha256"] for r in res),
+        "mask_sha256": digest_of_digests(r["mask_sha256"] for r in res),
+        "support_sha256": digest_of_digests(r["support_sha256"] for r in res),
+        "edges_out_total": sum(r["edges_out"] for r in res),
+        "support_sum_total": sum(r["support_sum"] for r in res),
+        "triangles_out_total": sum(r["triangles_out"] for r in res),
+        "oracle_cpu_seconds": round(sum(r["seconds"] for r in res), 1),
+        "wall_seconds": round(time.time() - t0, 1),
+        "K": [r["K"] for r in res],
+        "rounds": [r["rounds"] for r in res],
+        "edges_out": [r["edges_out"] for r in res],
+    })
+    path = os.path.join(HERE, "batch4096.json")
+    with open(path, "w") as f:
+        # one key per line; the per-graph lists stay on one line each
+        f.write("{\n" + ",\n".join(f" {json.dumps(k)}: {json.dumps(v, separators=(',', ':'))}"
+                                   for k, v in out.items()) + "\n}\n")
+    print(f"wrote {path} ({len(res)} graphs, {out['wall_seconds']} s)")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("workloads", nargs="+")
@@ -73,6 +140,9 @@ def main():
     gg.build()
     oracle.build()
     for name in a.workloads:
+        if name == "batch":
+            make_batch(a.jobs)
+            continue
         seeds = a.seeds if a.seeds else DEFAULT_SEEDS[name]
         for s in seeds:
             gg.cached_workload(name, s)  # generate once, before the pool

@@ -128,3 +128,66 @@ def test_batch_rejects_edges_across_graphs(kt):
     with pytest.raises(kt.KtrussError):
         kt.load_batch(vertex_offsets=np.array([0, 3, 2], np.int32), row_ptr=g.row_ptr,
                       col=g.col)
+
+
+def test_full_batching_workload_against_oracle_digests(kt):
+    """The batching workload at full size (4096 graphs of 1e3..2e6 edges, 1.2e9
+    edges in all, K per graph uniform in 3..12, seed 0), run as one batch with
+    the default options, as the benchmark times it, then with the supports
+    recomputed every round.  Every graph's mask, supports and round count are
+    compared with the oracle's, stored as digests by tests/golden/make_golden.py
+    (oracle.ktruss on each graph; nothing from the CUDA library)."""
+    import hashlib
+    import json
+    import os
+
+    import torch
+    p = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "batch4096.json")
+    if not os.path.exists(p):
+        pytest.skip("no stored oracle digests for the batching workload")
+    with open(p) as f:
+        c = json.load(f)
+
+    def sha(b) -> str:
+        return hashlib.sha256(b).hexdigest()
+
+    def digest_of_digests(hexes) -> str:
+        return sha("".join(hexes).encode("ascii"))
+
+    batch = gg.batch_config(c["graphs"], seed=c["seed"], m_lo=c["m_lo"], m_hi=c["m_hi"],
+                            k_lo=c["k_lo"], k_hi=c["k_hi"])
+    graphs = [b[0] for b in batch]
+    Ks = [int(b[1]) for b in batch]
+    assert Ks == c["K"]
+    assert digest_of_digests(
+        sha(np.ascontiguousarray(g.row_ptr, dtype="<i4").tobytes()
+            + np.ascontiguousarray(g.col, dtype="<i4").tobytes()) for g in graphs
+    ) == c["graphs_sha256"], "generator output changed"
+    vo, rp, col, eo = kt.concat_graphs(graphs)
+    del batch, graphs
+    assert int(eo[-1]) == c["edges"]
+    h = kt.load_batch(vertex_offsets=vo, row_ptr=torch.from_numpy(rp).cuda(),
+                      col=torch.from_numpy(col).cuda())
+    del rp, col
+    lo, hi = eo[:-1].tolist(), eo[1:].tolist()
+    # the default options first (decremental update), then Alg. 1 as written
+    # (supports recomputed every round) on the same handle
+    for update in (None, 0):
+        if update is not None:
+            h.set_update(update)
+        mask_t, sup_t, rounds = h.run_batch(Ks)
+        torch.cuda.synchronize()
+        st = h.stats()
+        mask = mask_t.cpu().numpy()
+        sup = np.ascontiguousarray(sup_t.cpu().numpy(), dtype="<i4")
+        del mask_t, sup_t
+        assert [int(r) for r in rounds] == c["rounds"], update
+        assert st.rounds == max(c["rounds"]), update
+        csum = np.concatenate([[0], np.cumsum(mask, dtype=np.int64)])
+        assert (csum[eo[1:]] - csum[eo[:-1]]).tolist() == c["edges_out"], update
+        assert int(sup.sum(dtype=np.int64)) == c["support_sum_total"], update
+        assert digest_of_digests(sha(mask[a:b].tobytes())
+                                 for a, b in zip(lo, hi)) == c["mask_sha256"], update
+        assert digest_of_digests(sha(sup[a:b].tobytes())
+                                 for a, b in zip(lo, hi)) == c["support_sha256"], update
+    h.close()

@@ -150,3 +150,33 @@ def test_budget_mix_of_staged_and_host_copied_requests(kt):
             srv2.submit(g.row_ptr, g.col, 3, mask_out=np.zeros(3, np.uint8))  # too short
         finally:
             srv2.close()
+
+
+def test_full_serving_workload_served_equals_solo(kt):
+    """The serving workload at full size (64 requests, R-MAT or G(n,m) with
+    p = 1/2, 1e4..5e7 edges, K uniform in 3..16, seed 0: 5.2e8 edges), all
+    arriving at once and served together as in the benchmark's saturated run,
+    with the server sized as there.  Every request equals its solo run (Alg. 1
+    as written: supports recomputed every round) in mask, supports and rounds.
+    The oracle ties the results to the definition at this size: kept edges
+    have support >= K - 2, removed edges report 0, and the supports of 256
+    sampled kept edges per request are their triangle counts inside the kept
+    subgraph (oracle.edge_support, one edge at a time)."""
+    reqs = gg.serve_config(64, seed=0, m_lo=1e4, m_hi=5e7)
+    edges = sum(g.m for g, _ in reqs)
+    srv = kt.Server(max_vertices=sum(g.n for g, _ in reqs) + 1,
+                    max_edges=min(edges + 1, (1 << 31) - 1), max_requests=len(reqs))
+    _, _, results = kt.serve_poisson(srv, reqs, rate=None)
+    srv.close()
+    rng = np.random.default_rng(0)
+    for k, (g, K) in enumerate(reqs):
+        r, mask, sup = results[k]
+        sm, ss, sr = solo(kt, g, K)
+        assert np.array_equal(mask, sm) and np.array_equal(sup, ss) and r == sr, k
+        assert not sup[mask == 0].any(), k
+        assert (sup[mask == 1] >= K - 2).all(), k
+        kept = np.flatnonzero(mask)
+        if kept.size:
+            q = rng.choice(kept, size=min(256, kept.size), replace=False)
+            want = oracle.edge_support(g.row_ptr, g.col, q, keep=mask)
+            assert np.array_equal(sup[q].astype(np.int64), want), k

@@ -84,3 +84,35 @@ def test_batch_and_serve_workloads_are_deterministic_and_in_range():
     assert _digest(s1) == _digest(s2)
     assert all(3 <= K <= 16 for _, K in s1)
     assert _digest(gg.batch_config(48, seed=5, m_lo=1e3, m_hi=3e4)) != _digest(b1)
+
+
+def test_batch_workload_reproduces_the_stored_oracle_record():
+    """The full batching workload (4096 graphs, 1.2e9 edges) must still be the
+    one the oracle digests in tests/golden/batch4096.json were taken on: same
+    K per graph, edge count and graph digest.  The record must also be
+    consistent in itself: support sum = 3 x triangles (every triangle credits
+    its three edges), one entry per graph."""
+    import hashlib
+    import json
+    import os
+    p = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "batch4096.json")
+    with open(p) as f:
+        c = json.load(f)
+    G = c["graphs"]
+    assert len(c["K"]) == len(c["rounds"]) == len(c["edges_out"]) == G
+    assert c["support_sum_total"] == 3 * c["triangles_out_total"]
+    assert sum(c["edges_out"]) == c["edges_out_total"]
+    assert all(r >= 1 for r in c["rounds"])
+    specs = gg.batch_specs(G, c["seed"], c["m_lo"], c["m_hi"], c["k_lo"], c["k_hi"])
+    assert [K for _, K in specs] == c["K"]
+    hexes = []
+    edges = 0
+    for g, _ in gg.batch_config(G, seed=c["seed"], m_lo=c["m_lo"], m_hi=c["m_hi"],
+                                k_lo=c["k_lo"], k_hi=c["k_hi"]):
+        edges += g.m
+        assert c["edges_out"][len(hexes)] <= g.m
+        hexes.append(hashlib.sha256(np.ascontiguousarray(g.row_ptr, dtype="<i4").tobytes()
+                                    + np.ascontiguousarray(g.col, dtype="<i4").tobytes())
+                     .hexdigest())
+    assert edges == c["edges"]
+    assert hashlib.sha256("".join(hexes).encode("ascii")).hexdigest() == c["graphs_sha256"]
