@@ -182,6 +182,27 @@ def traffic_record(workload, K):
     return rec
 
 
+def host_cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the record
+    beside the oracle's timing."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=5).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name:"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith("model name"):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine() or "unknown"
+
+
 def cpu_baseline(seconds_cap=30.0, scale=CPU_SAMPLE_SCALE):
     import graphgen as gg
     import oracle
@@ -194,6 +215,7 @@ def cpu_baseline(seconds_cap=30.0, scale=CPU_SAMPLE_SCALE):
         if el > seconds_cap / 3 or runs >= 3:
             break
     return {"value": round(g.m * runs / el / 1e6, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_model": host_cpu_model(), "host_cores": os.cpu_count(),
             "sample": f"full K=3 run of the single-thread C oracle on R-MAT scale {scale}, "
                       f"edge factor 16 (same recipe, {g.m} edges), {runs} run(s), "
                       f"{el:.1f} s on {os.cpu_count()} host cores (1 used)"}
@@ -341,6 +363,7 @@ def run_reference(args, world, rank):
         "config": {"workload": WORKLOAD_DESC[args.workload] + f", K={args.K}",
                    "reference_sample": f"rmat{args.ref_scale}", "K": args.K},
         "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "cpu_model": host_cpu_model(), "host_cores": os.cpu_count(),
                          "sample": sample},
         "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
