@@ -317,6 +317,13 @@ def serve_config(count: int, seed: int = 0, m_lo: float = 1e4, m_hi: float = 5e7
     graph with probability 1/2, target size log-uniform in [m_lo, m_hi] edges
     (same recipes as batch_config), K uniform in [k_lo, k_hi].  Returns a list
     of (CSR, K)."""
+    return _generate(serve_specs(count, seed, m_lo, m_hi, k_lo, k_hi))
+
+
+def serve_specs(count: int, seed: int = 0, m_lo: float = 1e4, m_hi: float = 5e7,
+                k_lo: int = 3, k_hi: int = 16):
+    """The (spec, K) pairs of serve_config without building the graphs;
+    request r is from_spec(spec) of pair r."""
     import math
     key = stream_key(6, seed, count)
     specs = []
@@ -332,4 +339,4 @@ def serve_config(count: int, seed: int = 0, m_lo: float = 1e4, m_hi: float = 5e7
         else:
             scale = min(30, max(10, int(math.ceil(math.log2(max(mt, 1) / 16.0)))))
             specs.append((("rmat", scale, 16, sub_seed), K))
-    return _generate(specs)
+    return specs

@@ -10,12 +10,18 @@ large to rerun the oracle on in a test.
     python tests/golden/make_golden.py rmat20 rmat20r      # config 2
     python tests/golden/make_golden.py rmat23c --K 3       # config 3, K=3
     python tests/golden/make_golden.py batch --jobs 8      # config 4, 4096 graphs
+    python tests/golden/make_golden.py serve --jobs 8      # config 5, 64 requests
 
 The batching workload (graphgen.batch_config: 4096 graphs, 1e3..2e6 edges,
 K per graph in 3..12, seed 0) is stored per graph (K, rounds, kept edges) and
 as digests of digests: the SHA-256 of the concatenated hex SHA-256 digests of
 every graph's mask (resp. little-endian int32 supports, resp. CSR), in batch
 order.
+
+The serving workload (graphgen.serve_config: 64 requests, 1e4..5e7 edges, K in
+3..16, seed 0) is stored per request for every request the oracle can finish
+in minutes: all G(n, m) requests and the R-MAT requests up to scale 20 (the
+scale-21 and -22 ones would take hours at K up to 16).
 """
 from __future__ import annotations
 
@@ -128,6 +134,37 @@ def make_batch(jobs: int):
     print(f"wrote {path} ({len(res)} graphs, {out['wall_seconds']} s)")
 
 
+SERVE = {"requests": 64, "seed": 0, "m_lo": 1e4, "m_hi": 5e7, "k_lo": 3, "k_hi": 16,
+         "rmat_max_scale": 20}
+
+
+def make_serve(jobs: int):
+    import graphgen as gg
+    specs = gg.serve_specs(SERVE["requests"], SERVE["seed"], SERVE["m_lo"], SERVE["m_hi"],
+                           SERVE["k_lo"], SERVE["k_hi"])
+    tasks = [(k, sp, K) for k, (sp, K) in enumerate(specs)
+             if sp[0] == "er" or sp[1] <= SERVE["rmat_max_scale"]]
+    # R-MAT first (they take longest), larger first
+    tasks.sort(key=lambda t: (t[1][0] == "er", -(t[1][2] if t[1][0] == "er" else 16 << t[1][1])))
+    t0 = time.time()
+    with mp.get_context("spawn").Pool(jobs) as pool:
+        res = pool.map(one_batch_graph, tasks, chunksize=1)
+    res.sort(key=lambda r: r["index"])
+    for r in res:
+        r["seconds"] = round(r["seconds"], 2)
+    out = dict(SERVE)
+    out.update({
+        "source": "oracle.ktruss (CPU) on the requests of graphgen.serve_config listed here, "
+                  "tests/golden/make_golden.py",
+        "wall_seconds": round(time.time() - t0, 1),
+        "cases": res,
+    })
+    path = os.path.join(HERE, "serve64.json")
+    with open(path, "w") as f:
+        json.dump(out, f, indent=1)
+    print(f"wrote {path} ({len(res)} requests, {out['wall_seconds']} s)")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("workloads", nargs="+")
@@ -142,6 +179,9 @@ def main():
     for name in a.workloads:
         if name == "batch":
             make_batch(a.jobs)
+            continue
+        if name == "serve":
+            make_serve(a.jobs)
             continue
         seeds = a.seeds if a.seeds else DEFAULT_SEEDS[name]
         for s in seeds:

@@ -161,7 +161,26 @@ def test_full_serving_workload_served_equals_solo(kt):
     The oracle ties the results to the definition at this size: kept edges
     have support >= K - 2, removed edges report 0, and the supports of 256
     sampled kept edges per request are their triangle counts inside the kept
-    subgraph (oracle.edge_support, one edge at a time)."""
+    subgraph (oracle.edge_support, one edge at a time).  Every request the
+    oracle finishes in minutes (all G(n,m) requests, R-MAT up to scale 20) is
+    also compared whole with the oracle's stored results
+    (tests/golden/serve64.json, written by tests/golden/make_golden.py)."""
+    import hashlib
+    import json
+    import os
+    p = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "serve64.json")
+    golden = {}
+    if os.path.exists(p):
+        with open(p) as f:
+            golden = {c["index"]: c for c in json.load(f)["cases"]}
+
+    def sha(a) -> str:
+        return hashlib.sha256(a.tobytes()).hexdigest()
+
+    def graph_sha(g) -> str:
+        return hashlib.sha256(np.ascontiguousarray(g.row_ptr, dtype="<i4").tobytes()
+                              + np.ascontiguousarray(g.col, dtype="<i4").tobytes()).hexdigest()
+
     reqs = gg.serve_config(64, seed=0, m_lo=1e4, m_hi=5e7)
     edges = sum(g.m for g, _ in reqs)
     srv = kt.Server(max_vertices=sum(g.n for g, _ in reqs) + 1,
@@ -180,3 +199,12 @@ def test_full_serving_workload_served_equals_solo(kt):
             q = rng.choice(kept, size=min(256, kept.size), replace=False)
             want = oracle.edge_support(g.row_ptr, g.col, q, keep=mask)
             assert np.array_equal(sup[q].astype(np.int64), want), k
+        c = golden.get(k)
+        if c is not None:
+            assert c["K"] == K and c["m"] == g.m, k
+            assert graph_sha(g) == c["graph_sha256"], f"generator output changed ({k})"
+            assert r == c["rounds"] and int(mask.sum(dtype=np.int64)) == c["edges_out"], k
+            assert int(sup.sum(dtype=np.int64)) == c["support_sum"], k
+            assert sha(np.ascontiguousarray(mask, dtype=np.uint8)) == c["mask_sha256"], k
+            assert sha(np.ascontiguousarray(sup, dtype="<i4")) == c["support_sha256"], k
+    assert len(golden) == 0 or len(golden) >= 59

@@ -116,3 +116,31 @@ def test_batch_workload_reproduces_the_stored_oracle_record():
                      .hexdigest())
     assert edges == c["edges"]
     assert hashlib.sha256("".join(hexes).encode("ascii")).hexdigest() == c["graphs_sha256"]
+
+
+def test_serve_workload_reproduces_the_stored_oracle_record():
+    """The requests of the serving workload that tests/golden/serve64.json
+    holds oracle results for must still be generated as they were (K, edge
+    count, graph digest); each record is consistent in itself (support sum =
+    3 x triangles) and covers every G(n,m) request and every R-MAT request up
+    to the recorded scale."""
+    import hashlib
+    import json
+    import os
+    p = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "serve64.json")
+    with open(p) as f:
+        c = json.load(f)
+    specs = gg.serve_specs(c["requests"], c["seed"], c["m_lo"], c["m_hi"], c["k_lo"], c["k_hi"])
+    covered = [k for k, (sp, _) in enumerate(specs)
+               if sp[0] == "er" or sp[1] <= c["rmat_max_scale"]]
+    assert [x["index"] for x in c["cases"]] == covered
+    for x in c["cases"]:
+        assert x["support_sum"] == 3 * x["triangles_out"]
+        assert 0 <= x["edges_out"] <= x["m"] and x["rounds"] >= 1
+        sp, K = specs[x["index"]]
+        assert K == x["K"]
+        g = gg.from_spec(sp)
+        assert g.m == x["m"]
+        assert hashlib.sha256(np.ascontiguousarray(g.row_ptr, dtype="<i4").tobytes()
+                              + np.ascontiguousarray(g.col, dtype="<i4").tobytes()
+                              ).hexdigest() == x["graph_sha256"]
