@@ -46,7 +46,9 @@ def noalloc_supports(kt, torch, g):
 def test_noalloc_matches_regular_entry_point_twice():
     import torch
     import paper_2009_07929_gb300 as kt
-    graphs = [gg.rmat(14, 16, seed=21), gg.er(2000, 16000, seed=4)]
+    # the last graph sits at both size limits (n = m = 524288)
+    graphs = [gg.rmat(14, 16, seed=21), gg.er(2000, 16000, seed=4),
+              gg.er(kt.NOALLOC_MAX_VERTICES, kt.NOALLOC_MAX_EDGES, seed=6)]
     # two calls in a row on the same device; the second sees the first's leftovers
     for g in graphs + graphs[::-1]:
         want, want_tri = regular_supports(kt, torch, g)
