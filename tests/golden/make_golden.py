@@ -11,6 +11,12 @@ large to rerun the oracle on in a test.
     python tests/golden/make_golden.py rmat23c --K 3       # config 3, K=3
     python tests/golden/make_golden.py batch --jobs 8      # config 4, 4096 graphs
     python tests/golden/make_golden.py serve --jobs 8      # config 5, 64 requests
+    python tests/golden/make_golden.py decompose rmat20 rmat20r   # K = 3 .. K_max
+
+decompose stores, per graph, the oracle's truss decomposition (per-edge
+trussness by the second, independent algorithm, oracle.truss_decomposition):
+its digest (little-endian int32 in input edge order), K_max and the number of
+edges at each trussness.
 
 The batching workload (graphgen.batch_config: 4096 graphs, 1e3..2e6 edges,
 K per graph in 3..12, seed 0) is stored per graph (K, rounds, kept edges) and
@@ -165,6 +171,37 @@ def make_serve(jobs: int):
     print(f"wrote {path} ({len(res)} requests, {out['wall_seconds']} s)")
 
 
+def one_decomposition(args):
+    name, seed = args
+    import numpy as np
+    import graphgen as gg
+    import oracle
+    g = gg.cached_workload(name, seed)
+    t0 = time.time()
+    tr = oracle.truss_decomposition(g.row_ptr, g.col)
+    dt = time.time() - t0
+    hist = np.bincount(tr, minlength=int(tr.max()) + 1 if g.m else 1)
+    return {"workload": name, "seed": seed, "n": g.n, "m": g.m, "graph_sha256": graph_digest(g),
+            "kmax": int(tr.max()) if g.m else 0,
+            "trussness_sha256": sha(np.ascontiguousarray(tr, dtype="<i4")),
+            "edges_per_trussness": {str(k): int(c) for k, c in enumerate(hist) if c},
+            "oracle_seconds": round(dt, 1)}
+
+
+def make_decompositions(names, jobs: int):
+    import graphgen as gg
+    for name in names:
+        gg.cached_workload(name, 0)  # generate once, before the pool
+    with mp.get_context("spawn").Pool(min(jobs, len(names))) as pool:
+        res = pool.map(one_decomposition, [(name, 0) for name in names], chunksize=1)
+    for r in res:
+        path = os.path.join(HERE, f"{r['workload']}_trussness.json")
+        with open(path, "w") as f:
+            json.dump(dict(r, source="oracle.truss_decomposition (CPU), "
+                                     "tests/golden/make_golden.py"), f, indent=1)
+        print(f"wrote {path} ({r['oracle_seconds']} s)")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("workloads", nargs="+")
@@ -176,6 +213,9 @@ def main():
     import oracle
     gg.build()
     oracle.build()
+    if a.workloads[0] == "decompose":
+        make_decompositions(a.workloads[1:], a.jobs)
+        return
     for name in a.workloads:
         if name == "batch":
             make_batch(a.jobs)

@@ -491,6 +491,32 @@ def test_full_size_against_oracle_digests(kt, name):
         h.close()
 
 
+@pytest.mark.parametrize("name", ["rmat20", "rmat20r"])
+def test_full_size_decomposition_against_oracle(kt, name):
+    """ktruss_decompose (K = 3, 4, ... up to K_max, each K from the previous
+    truss) of the full R-MAT-20 graph, original ids and degree-relabelled,
+    against the oracle's truss decomposition by its second, independent
+    algorithm (sequential peeling; stored by tests/golden/make_golden.py):
+    every edge's trussness, hence the K-truss for every K at once."""
+    p = os.path.join(GOLDEN, f"{name}_trussness.json")
+    if not os.path.exists(p):
+        pytest.skip(f"no stored oracle decomposition for {name}")
+    with open(p) as f:
+        c = json.load(f)
+    import torch
+    g = gg.workload(name, c["seed"])
+    assert graph_digest(g) == c["graph_sha256"], "generator output changed"
+    h = kt.load(torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col).cuda())
+    tr_t, kmax = h.decompose()
+    torch.cuda.synchronize()
+    tr = np.ascontiguousarray(tr_t.cpu().numpy(), dtype="<i4")
+    h.close()
+    assert kmax == c["kmax"]
+    hist = np.bincount(tr)
+    assert {str(k): int(v) for k, v in enumerate(hist) if v} == c["edges_per_trussness"]
+    assert sha(tr) == c["trussness_sha256"]
+
+
 def test_rmat23_cliques_k3_sampled_and_kmax_sweep(kt):
     """Config 3 at full size: K=3 checked on sampled edges against per-edge
     oracle supports (for K=3 the kept edges are exactly those in a triangle and

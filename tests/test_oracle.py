@@ -370,3 +370,26 @@ def test_tail_start_reading():
                 a, b = run(g, K), _mutant_run(lib, g, K)
                 assert np.array_equal(a.mask, b.mask) and np.array_equal(a.support, b.support)
                 assert a.rounds == b.rounds
+
+
+@pytest.mark.parametrize("name", ["rmat20", "rmat20r"])
+def test_decomposition_agrees_with_peeling_on_rmat20(name):
+    """At full R-MAT-20 size the oracle's two algorithms agree: the stored
+    Alg. 1 results (K = 3, 4, 8, 16) keep exactly the edges whose trussness,
+    from the stored sequential-peeling decomposition, is at least K; both
+    were taken on the same graph."""
+    import json
+    import os
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    p = os.path.join(here, f"{name}_trussness.json")
+    if not os.path.exists(p):
+        pytest.skip(f"no stored oracle decomposition for {name}")
+    with open(p) as f:
+        dec = json.load(f)
+    with open(os.path.join(here, f"{name}.json")) as f:
+        cases = [c for c in json.load(f)["cases"] if c["seed"] == dec["seed"]]
+    assert cases and all(c["graph_sha256"] == dec["graph_sha256"] for c in cases)
+    hist = {int(k): v for k, v in dec["edges_per_trussness"].items()}
+    assert sum(hist.values()) == dec["m"] and max(hist) == dec["kmax"]
+    for c in cases:
+        assert c["edges_out"] == sum(v for t, v in hist.items() if t >= c["K"]), c["K"]
