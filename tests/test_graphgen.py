@@ -144,3 +144,24 @@ def test_serve_workload_reproduces_the_stored_oracle_record():
         assert hashlib.sha256(np.ascontiguousarray(g.row_ptr, dtype="<i4").tobytes()
                               + np.ascontiguousarray(g.col, dtype="<i4").tobytes()
                               ).hexdigest() == x["graph_sha256"]
+
+
+@pytest.mark.parametrize("name", ["rmat20", "rmat20r"])
+def test_rmat20_workloads_reproduce_the_stored_oracle_records(name):
+    """The R-MAT scale-20 graphs (original ids and degree-relabelled, seed 0)
+    must still be the ones the stored oracle digests and truss decompositions
+    were taken on."""
+    import hashlib
+    import json
+    import os
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    with open(os.path.join(here, f"{name}.json")) as f:
+        want = {c["graph_sha256"] for c in json.load(f)["cases"] if c["seed"] == 0}
+    with open(os.path.join(here, f"{name}_trussness.json")) as f:
+        want.add(json.load(f)["graph_sha256"])
+    assert len(want) == 1
+    g = gg.workload(name, 0)
+    h = hashlib.sha256()
+    h.update(np.ascontiguousarray(g.row_ptr, dtype="<i4").tobytes())
+    h.update(np.ascontiguousarray(g.col, dtype="<i4").tobytes())
+    assert h.hexdigest() in want
