@@ -269,34 +269,6 @@ int oracle_triangles(int32_t n, int64_t m, const int32_t *row_ptr, const int32_t
 /* ------------------------------------------------------------------------ */
 /* Truss decomposition: a second, independent K-truss algorithm.             */
 
-typedef struct { int64_t key; int64_t e; } heap_item;
-
-static void heap_push(heap_item *h, int64_t *len, heap_item it) {
-    int64_t i = (*len)++;
-    h[i] = it;
-    while (i > 0) {
-        int64_t p = (i - 1) / 2;
-        if (h[p].key < h[i].key || (h[p].key == h[i].key && h[p].e <= h[i].e)) break;
-        heap_item t = h[p]; h[p] = h[i]; h[i] = t;
-        i = p;
-    }
-}
-
-static heap_item heap_pop(heap_item *h, int64_t *len) {
-    heap_item top = h[0];
-    h[0] = h[--(*len)];
-    int64_t i = 0;
-    for (;;) {
-        int64_t l = 2 * i + 1, r = l + 1, s = i;
-        if (l < *len && (h[l].key < h[s].key || (h[l].key == h[s].key && h[l].e < h[s].e))) s = l;
-        if (r < *len && (h[r].key < h[s].key || (h[r].key == h[s].key && h[r].e < h[s].e))) s = r;
-        if (s == i) break;
-        heap_item t = h[s]; h[s] = h[i]; h[i] = t;
-        i = s;
-    }
-    return top;
-}
-
 /* position of w in the sorted list nbr[lo, hi), or -1 */
 static int64_t find_sorted(const int32_t *nbr, int64_t lo, int64_t hi, int32_t w) {
     int64_t end = hi;
@@ -309,11 +281,20 @@ static int64_t find_sorted(const int32_t *nbr, int64_t lo, int64_t hi, int32_t w
 
 /*
  * trussness[e] = the largest K such that edge e belongs to the K-truss (2 for
- * an edge in no triangle).  Classic sequential peeling: every edge starts with
- * its triangle count; repeatedly take a remaining edge of least current
- * support s, set k = max(k, s + 2), give it trussness k, delete it and lower by
- * one the support of the two other edges of every remaining triangle on it.
- * The K-truss is then {e : trussness[e] >= K}.
+ * an edge in no triangle).  Sequential peeling in increasing support order,
+ * with the edges kept sorted by current support in bins (the bin-sort edge
+ * peeling of Wang and Cheng, "Truss decomposition in massive networks",
+ * PVLDB 2012):
+ *   every edge starts with its triangle count;
+ *   take the remaining edge e of least current support s, set k = max(k, s+2),
+ *   give e trussness k and delete it;
+ *   for every remaining triangle (e, e1, e2) on e, lower the support of e1 and
+ *   of e2 by one, except that a support already at or below s stays (such an
+ *   edge gets trussness k anyway, as k never decreases);
+ * until no edge remains.  The K-truss is then {e : trussness[e] >= K}.
+ * The triangles on e = (u, v) are the common neighbours of u and v: the
+ * neighbour list of the endpoint with fewer neighbours is walked and each
+ * neighbour is looked up in the other list by binary search.
  */
 int oracle_truss_decomposition(int32_t n, int64_t m, const int32_t *row_ptr, const int32_t *col,
                                int32_t *trussness) {
@@ -321,55 +302,70 @@ int oracle_truss_decomposition(int32_t n, int64_t m, const int32_t *row_ptr, con
     if (rc != OR_OK) return rc;
     sym_adj a;
     if (sym_build(&a, n, m, row_ptr, col) != OR_OK) return OR_ENOMEM;
-    int64_t *sup = (int64_t *)calloc((size_t)(m > 0 ? m : 1), sizeof(int64_t));
-    uint8_t *gone = (uint8_t *)calloc((size_t)(m > 0 ? m : 1), 1);
-    int32_t *eu = (int32_t *)malloc((size_t)(m > 0 ? m : 1) * sizeof(int32_t));
-    int64_t heap_cap = 4 * m + 16;
-    heap_item *h = (heap_item *)malloc((size_t)heap_cap * sizeof(heap_item));
-    if (!sup || !gone || !eu || !h) {
-        free(sup); free(gone); free(eu); free(h); sym_free(&a);
-        return OR_ENOMEM;
-    }
+    size_t mm = (size_t)(m > 0 ? m : 1);
+    int64_t *sup = (int64_t *)calloc(mm, sizeof(int64_t));
+    uint8_t *gone = (uint8_t *)calloc(mm, 1);
+    int32_t *eu = (int32_t *)malloc(mm * sizeof(int32_t));
+    int64_t *order = (int64_t *)malloc(mm * sizeof(int64_t)); /* edges by support */
+    int64_t *pos = (int64_t *)malloc(mm * sizeof(int64_t));   /* order[pos[e]] == e */
+    int64_t *bin = NULL;
+    if (!sup || !gone || !eu || !order || !pos) goto nomem;
     for (int32_t i = 0; i < n; ++i)
         for (int64_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p) eu[p] = i;
     /* initial supports: common neighbours by binary search in the longer list */
+    int64_t smax = 0;
     for (int64_t e = 0; e < m; ++e) {
         int32_t u = eu[e], v = col[e];
         int32_t s = (a.off[u + 1] - a.off[u] <= a.off[v + 1] - a.off[v]) ? u : v;
         int32_t l = (s == u) ? v : u;
         for (int64_t x = a.off[s]; x < a.off[s + 1]; ++x)
             if (find_sorted(a.nbr, a.off[l], a.off[l + 1], a.nbr[x]) >= 0) sup[e]++;
+        if (sup[e] > smax) smax = sup[e];
     }
-    int64_t hl = 0;
-    for (int64_t e = 0; e < m; ++e) heap_push(h, &hl, (heap_item){sup[e], e});
+    /* counting sort of the edges by support; bin[d] = first position of
+     * support d among the edges not yet taken */
+    bin = (int64_t *)calloc((size_t)smax + 2, sizeof(int64_t));
+    if (!bin) goto nomem;
+    for (int64_t e = 0; e < m; ++e) bin[sup[e] + 1]++;
+    for (int64_t d = 0; d <= smax; ++d) bin[d + 1] += bin[d];
+    for (int64_t e = 0; e < m; ++e) {
+        pos[e] = bin[sup[e]]++;
+        order[pos[e]] = e;
+    }
+    for (int64_t d = smax; d > 0; --d) bin[d] = bin[d - 1];
+    bin[0] = 0;
     int64_t k = 2;
-    while (hl > 0) {
-        heap_item it = heap_pop(h, &hl);
-        int64_t e = it.e;
-        if (gone[e] || it.key != sup[e]) continue; /* stale entry */
-        if (sup[e] + 2 > k) k = sup[e] + 2;
+    for (int64_t i = 0; i < m; ++i) {
+        int64_t e = order[i];
+        int64_t s = sup[e];
+        if (s + 2 > k) k = s + 2;
         trussness[e] = (int32_t)k;
         gone[e] = 1;
         int32_t u = eu[e], v = col[e];
-        for (int64_t x = a.off[u]; x < a.off[u + 1]; ++x) {
+        int32_t w0 = (a.off[u + 1] - a.off[u] <= a.off[v + 1] - a.off[v]) ? u : v;
+        int32_t w1 = (w0 == u) ? v : u;
+        for (int64_t x = a.off[w0]; x < a.off[w0 + 1]; ++x) {
             if (gone[a.eid[x]]) continue;
-            int32_t w = a.nbr[x];
-            int64_t y = find_sorted(a.nbr, a.off[v], a.off[v + 1], w);
+            int64_t y = find_sorted(a.nbr, a.off[w1], a.off[w1 + 1], a.nbr[x]);
             if (y < 0 || gone[a.eid[y]]) continue;
-            int64_t e1 = a.eid[x], e2 = a.eid[y];
-            sup[e1]--;
-            sup[e2]--;
-            if (hl + 2 > heap_cap) {
-                heap_cap *= 2;
-                heap_item *nh = (heap_item *)realloc(h, (size_t)heap_cap * sizeof(heap_item));
-                if (!nh) { free(sup); free(gone); free(eu); free(h); sym_free(&a); return OR_ENOMEM; }
-                h = nh;
+            int64_t f2[2] = {a.eid[x], a.eid[y]};
+            for (int t = 0; t < 2; ++t) {
+                int64_t f = f2[t], d = sup[f];
+                if (d <= s) continue;
+                /* move f to the front of bin d, then shrink bin d past it */
+                int64_t pf = pos[f], pg = bin[d], g = order[pg];
+                order[pf] = g; pos[g] = pf;
+                order[pg] = f; pos[f] = pg;
+                bin[d]++;
+                sup[f] = d - 1;
             }
-            heap_push(h, &hl, (heap_item){sup[e1], e1});
-            heap_push(h, &hl, (heap_item){sup[e2], e2});
         }
     }
-    free(sup); free(gone); free(eu); free(h);
+    free(sup); free(gone); free(eu); free(order); free(pos); free(bin);
     sym_free(&a);
     return OR_OK;
+nomem:
+    free(sup); free(gone); free(eu); free(order); free(pos); free(bin);
+    sym_free(&a);
+    return OR_ENOMEM;
 }
