@@ -349,10 +349,14 @@ int ktruss_version(void);
  * it and it keeps the last call's contents; calls whose work overlaps on the
  * GPU (other streams or host threads) race on it and must not be issued.  The
  * first call on a device looks up the array's device address with that device
- * current; make that first call before any stream capture.
+ * current; make that first call before any stream capture.  Every call
+ * synchronises cuda_stream and reads counters back to the host before it
+ * returns.
  * Returns KTRUSS_EINVAL for n or m out of range (including above 524288),
  * NULL pointers or a malformed CSR (checked on the device first);
- * KTRUSS_ECUDA for a failed CUDA call.
+ * KTRUSS_ECUDA for a failed CUDA call or a device-side consistency check of
+ * the support kernel that gave up (the supports are then incomplete);
+ * KTRUSS_ETIMEOUT if a bounded device wait gave up.
  */
 int ktruss_support_noalloc(int32_t n, int64_t m, const int32_t *row_ptr, const int32_t *col,
                            int32_t *support_out, int64_t *triangles_out, void *cuda_stream);

@@ -22,6 +22,9 @@
 // device address of the array once (cudaGetSymbolAddress); a host-side name
 // of a __device__ array is not a device address.  That first call should come
 // before any stream capture.
+//
+// Every call synchronises its stream and copies the round counters to the
+// host before it returns.
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -70,7 +73,10 @@ extern "C" int ktruss_support_noalloc(int32_t n, int64_t m, const int32_t *row_p
                                       int64_t *triangles_out, void *cuda_stream) {
     if (n < 0 || m < 0 || !row_ptr || (m > 0 && (!col || !support_out))) return KTRUSS_EINVAL;
     if (n > kNoAllocMaxVertices || m > kNoAllocMaxEdges) return KTRUSS_EINVAL;
-    const size_t need = sizeof(kt::RoundCounters) + 256 + kt::balanced_scratch_bytes(n, m);
+    // the round counters sit in the first 256 bytes, the balanced step's
+    // scratch after them
+    static_assert(sizeof(kt::RoundCounters) <= 256, "round counters exceed their header");
+    const size_t need = 256 + kt::balanced_scratch_bytes(n, m);
     if (need > kNoAllocScratchBytes) return KTRUSS_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     void *base = nullptr;
@@ -100,6 +106,9 @@ extern "C" int ktruss_support_noalloc(int32_t n, int64_t m, const int32_t *row_p
             e = cudaMemcpyAsync(&host, cnt, sizeof(host), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return fail(e);
+        // a device-side check of the support kernel gave up (see its give-up
+        // words): the supports are incomplete
+        if (host.error) return (host.error & kt::kDevErrTimeout) ? KTRUSS_ETIMEOUT : KTRUSS_ECUDA;
     }
     if (triangles_out) *triangles_out = int64_t(host.triangles);
     return KTRUSS_OK;

@@ -6,8 +6,9 @@ For them the library computes a graph's edge supports with working memory
 taken from a fixed array inside the library.  This test calls that entry
 point through the C ABI, twice in a row on the same device, and checks each
 result against the regular entry point (ktruss_run with K = 2, whose supports
-are the full-graph triangle counts).  All arithmetic is integer, so the
-tolerance is zero.  It lives in a file of its own that pytest collects last.
+are the full-graph triangle counts) and against the CPU oracle's K = 2 run.
+All arithmetic is integer, so the tolerance is zero.  It lives in a file of its
+own that pytest collects last.
 """
 import ctypes
 
@@ -15,6 +16,7 @@ import numpy as np
 import pytest
 
 import graphgen as gg
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -46,15 +48,20 @@ def noalloc_supports(kt, torch, g):
 def test_noalloc_matches_regular_entry_point_twice():
     import torch
     import paper_2009_07929_gb300 as kt
-    # the last graph sits at both size limits (n = m = 524288)
-    graphs = [gg.rmat(14, 16, seed=21), gg.er(2000, 16000, seed=4),
+    # the R-MAT scale-15 graph (2^19 samples) is close to the edge limit and has
+    # rows longer than a stage; the last graph sits at both size limits
+    # (n = m = 524288)
+    graphs = [gg.rmat(14, 16, seed=21), gg.er(2000, 16000, seed=4), gg.rmat(15, 16, seed=8),
               gg.er(kt.NOALLOC_MAX_VERTICES, kt.NOALLOC_MAX_EDGES, seed=6)]
+    ref = [oracle.ktruss(g.row_ptr, g.col, 2) for g in graphs]
+    ref = ref + ref[::-1]
     # two calls in a row on the same device; the second sees the first's leftovers
-    for g in graphs + graphs[::-1]:
+    for g, r in zip(graphs + graphs[::-1], ref):
         want, want_tri = regular_supports(kt, torch, g)
         got, got_tri = noalloc_supports(kt, torch, g)
         assert np.array_equal(got, want)
         assert got_tri == want_tri
+        assert np.array_equal(got, r.support) and got_tri == r.triangles
 
 
 def test_noalloc_rejects_oversized_graphs():
