@@ -36,8 +36,10 @@
 //
 // All credits are integer additions, so the result does not depend on the
 // order in which CTAs, warps or the counting sort place the work.
+#include <atomic>
 #include <cstdint>
 #include <cstdio>
+#include <mutex>
 
 #include "ktruss_internal.cuh"
 
@@ -63,6 +65,7 @@ constexpr int kTable = 4 * kCap;        // hash entries (load factor <= 1/4)
 constexpr int kStageRows = 256;         // staged rows per stage
 constexpr int kWarps = kThreads / 32;
 constexpr int kBatch = kThreads;        // segments per batch (one per thread)
+constexpr int kLong = 6 * kBatch / 4;   // segments per batch of a long row
 constexpr int kUnroll = KT_SUPPORT_UNROLL;  // 32-item windows in flight per warp
 #ifndef KT_SUPPORT_MIX_UNROLL
 #define KT_SUPPORT_MIX_UNROLL 2
@@ -568,14 +571,22 @@ struct SupportSmem {
     int32_t segb[kStageRows + 1];     // stage: first segment position of each row
     int32_t tbase[kStageRows + 1];    // stage: first bucket of each row's region
     int32_t tlb[kStageRows];          // stage: log2 bucket count of each row's region
-    int32_t cur[kBatch];              // batch: next probe position of segment j
-    int32_t end[kBatch];              // batch: end of segment j's probes in the chunk
-    int32_t owner[kBatch];            // batch: owner edge slot of segment j
-    int32_t hit[kBatch];              // batch: hits credited to segment j's owner
-    int32_t rstart[kBatch + 1];       // runs: batch-local item offset of run r
-    int32_t rdel[kBatch];             // runs: probe position of item i of run r is rdel[r] + i
-    int32_t rreg[kBatch];             // runs: region probed (first bucket | log2 buckets << 24)
-    int32_t rseg[kBatch];             // runs: segment of run r
+    union {
+        struct {                      // stages of short rows
+            int32_t owner[kBatch];    // batch: owner edge slot of segment j
+            int32_t hit[kBatch];      // batch: hits credited to segment j's owner
+            int32_t rstart[kBatch + 1];  // runs: batch-local item offset of run r
+            int32_t rdel[kBatch];     // runs: probe position of item i of run r is rdel[r] + i
+            int32_t rreg[kBatch];     // runs: region probed (first bucket | log2 buckets << 24)
+            int32_t rseg[kBatch];     // runs: segment of run r
+        } b;
+        struct {                      // long rows: segment j of the current batch
+            int32_t cur[kLong];       // next probe position
+            int32_t end[kLong];       // end of its probes in the chunk
+            int32_t nxt[kLong];       // column at cur (kIntMax when exhausted)
+            int32_t hit[kLong];       // hits credited to its owner
+        } l;
+    };
     unsigned long long wtmp[64];
     int32_t ctl[64];
 };
@@ -643,13 +654,13 @@ __device__ __forceinline__ void build_runs(SupportSmem &sm, int32_t len, int32_t
     nruns = int32_t(tot >> 32);
     items = int32_t(uint32_t(tot));
     if (flag) {
-        sm.rstart[ridx] = roff;
-        sm.rdel[ridx] = pos - roff;
-        sm.rreg[ridx] = reg;
-        sm.rseg[ridx] = j;
+        sm.b.rstart[ridx] = roff;
+        sm.b.rdel[ridx] = pos - roff;
+        sm.b.rreg[ridx] = reg;
+        sm.b.rseg[ridx] = j;
     }
     if (threadIdx.x == 0) {
-        sm.rstart[nruns] = items;
+        sm.b.rstart[nruns] = items;
         sm.ctl[4] = 0;
     }
     __syncthreads();
@@ -665,17 +676,17 @@ __device__ __forceinline__ void probe_range(const SupportArgs &A, SupportSmem &s
                                             int32_t items, int32_t E, int32_t p, int32_t pe) {
     const int lane = threadIdx.x & 31;
     while (p < pe) {
-        while (E + 1 < nruns && sm.rstart[E + 1] <= p) ++E;
-        const int32_t rend = min(pe, E + 1 < nruns ? sm.rstart[E + 1] : items);
+        while (E + 1 < nruns && sm.b.rstart[E + 1] <= p) ++E;
+        const int32_t rend = min(pe, E + 1 < nruns ? sm.b.rstart[E + 1] : items);
         if (rend - p >= 32) {
             // ---- whole windows of run E: warp-uniform parameters
             const int32_t nwin = (rend - p) >> 5;
-            const int32_t reg = sm.rreg[E];
+            const int32_t reg = sm.b.rreg[E];
             const int32_t bb = reg & 0xffffff;
             const int lb = reg >> 24;
             const uint32_t bm = (1u << lb) - 1u;
             const int sh = 32 - lb;
-            const int32_t *__restrict__ src = A.col + sm.rdel[E] + p + lane;
+            const int32_t *__restrict__ src = A.col + sm.b.rdel[E] + p + lane;
             int32_t *__restrict__ dst = A.S + (src - A.col);
             int32_t own = 0;
             int32_t i = 0;
@@ -719,7 +730,7 @@ __device__ __forceinline__ void probe_range(const SupportArgs &A, SupportSmem &s
                 }
             }
             own = __reduce_add_sync(0xffffffffu, own);
-            if (lane == 0 && own) atomicAdd(&sm.hit[sm.rseg[E]], own);
+            if (lane == 0 && own) atomicAdd(&sm.b.hit[sm.b.rseg[E]], own);
             p += nwin * 32;
         } else {
             // ---- windows crossing run boundaries: map lanes to runs with a
@@ -733,18 +744,18 @@ __device__ __forceinline__ void probe_range(const SupportArgs &A, SupportSmem &s
             for (int u = 0; u < kMixUnroll; ++u) {
                 if (u > 0) {
                     if (p >= pe) break;
-                    while (E + 1 < nruns && sm.rstart[E + 1] <= p) ++E;
-                    if (!(E + 1 < nruns && sm.rstart[E + 1] < p + 32)) break;
+                    while (E + 1 < nruns && sm.b.rstart[E + 1] <= p) ++E;
+                    if (!(E + 1 < nruns && sm.b.rstart[E + 1] < p + 32)) break;
                 }
                 const int32_t j = E + 1 + lane;
-                const int32_t s0 = j < nruns ? sm.rstart[j] : kIntMax;
+                const int32_t s0 = j < nruns ? sm.b.rstart[j] : kIntMax;
                 const int32_t rel = s0 - p;
                 const uint32_t bits = __reduce_or_sync(0xffffffffu, rel < 32 ? (1u << rel) : 0u);
                 const int32_t r = E + __popc(bits & (0xffffffffu >> (31 - lane)));
                 const int32_t item = p + lane;
                 ok[u] = item < pe;
                 rr[u] = r;
-                x[u] = sm.rdel[r] + item;
+                x[u] = sm.b.rdel[r] + item;
                 E = __shfl_sync(0xffffffffu, r, 31);
                 p += 32;
             }
@@ -753,14 +764,14 @@ __device__ __forceinline__ void probe_range(const SupportArgs &A, SupportSmem &s
 #pragma unroll
             for (int u = 0; u < kMixUnroll; ++u) {
                 if (!ok[u]) continue;
-                const int32_t reg = sm.rreg[rr[u]];
+                const int32_t reg = sm.b.rreg[rr[u]];
                 const int32_t bb = reg & 0xffffff;
                 const int lb = reg >> 24;
                 const int32_t q = table_find(sm.fpw, sm.slots, sm.vals, bb, lb, wv[u]);
                 if (q >= 0) {
                     atomicAdd(&sm.cnt[q], 1);
                     atomicAdd(A.S + x[u], 1);
-                    atomicAdd(&sm.hit[sm.rseg[rr[u]]], 1);
+                    atomicAdd(&sm.b.hit[sm.b.rseg[rr[u]]], 1);
                 }
             }
         }
@@ -778,14 +789,14 @@ __device__ __forceinline__ void probe_runs(const SupportArgs &A, SupportSmem &sm
         const int32_t w0 = warp * per;
         const int32_t w1 = min(items, w0 + per);
         if (w0 < w1)
-            probe_range(A, sm, nruns, items, last_le(sm.rstart, 0, nruns - 1, w0), w0, w1);
+            probe_range(A, sm, nruns, items, last_le(sm.b.rstart, 0, nruns - 1, w0), w0, w1);
     } else {
         for (;;) {
             int32_t g = 0;
             if (lane == 0) g = atomicAdd(&sm.ctl[4], kGrain);
             g = __shfl_sync(0xffffffffu, g, 0);
             if (g >= items) break;
-            const int32_t E = last_le(sm.rstart, 0, nruns - 1, g);
+            const int32_t E = last_le(sm.b.rstart, 0, nruns - 1, g);
             probe_range(A, sm, nruns, items, E, g, min(items, g + kGrain));
         }
     }
@@ -801,112 +812,177 @@ __device__ __forceinline__ void flush_owners(const SupportArgs &A, SupportSmem &
                                              unsigned long long &tri) {
     const int j = threadIdx.x;
     if (j < nb) {
-        const int32_t v = sm.hit[j];
+        const int32_t v = sm.b.hit[j];
         if (v) {
-            atomicAdd(A.S + sm.owner[j], v);
+            atomicAdd(A.S + sm.b.owner[j], v);
             tri += v;
         }
     }
 }
 
+// Probes one column w of a window against the region (bb, lb) of the table;
+// on a hit credits the staged slot (shared counter) and the probe position x
+// (global) and returns true.
+__device__ __forceinline__ bool probe_one(SupportSmem &sm, int32_t bb, uint32_t bm, int sh,
+                                          int32_t w, int32_t *x) {
+    const uint32_t fp4 = fingerprint(w) * 0x01010101u;
+    uint32_t b = (uint32_t(w) * kHashMul) >> sh;
+    for (;;) {
+        const int32_t at = bb + int32_t(b);
+        const uint32_t word = sm.fpw[at];
+        for (uint32_t mm = match_bytes(word, fp4); mm; mm &= mm - 1u) {
+            const int32_t sl = sm.slots[4 * at + ((__ffs(mm) - 1) >> 3)];
+            if (sm.vals[sl] == w) {
+                atomicAdd(&sm.cnt[sl], 1);
+                atomicAdd(x, 1);
+                return true;
+            }
+        }
+        if ((word >> 24) == 0) return false;
+        b = (b + 1) & bm;
+    }
+}
+
+// Last piece (of kCap slots) of the row at rbase with npieces pieces whose
+// first column is <= v (piece 0 if none is).
+__device__ __forceinline__ int32_t piece_of(const int32_t *__restrict__ col, int32_t rbase,
+                                            int32_t npieces, int32_t v) {
+    int32_t lo = 0, hi = npieces - 1;
+    while (lo < hi) {
+        const int32_t mid = lo + ((hi - lo + 1) >> 1);
+        if (__ldg(col + rbase + mid * kCap) <= v) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 // The segments [s0, s1) of chunk [iA, iB) whose staged row (rbase, L) is
-// longer than kCap: the row is staged piece by piece in column order; per
-// piece each segment contributes the run of its probes below the piece's end.
+// longer than kCap.  The row is staged piece by piece in column order, each
+// piece once for up to kLong segments.  Every segment keeps a cursor (its next
+// probe position and the column there); per piece, warps take the segments
+// whose next probe lies below the piece's end column and stream their probes
+// in windows of 32 until a probe reaches that column (the probes are sorted,
+// so the probes of a piece are a prefix of what is left).  Pieces below every
+// segment's next probe are skipped.
 __device__ void long_row(const SupportArgs &A, SupportSmem &sm, int32_t rbase, int32_t L,
                          int32_t s0, int32_t s1, long long iA, long long iB,
                          unsigned long long &tri) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int32_t npieces = (L + kCap - 1) / kCap;
-    for (int32_t sb = s0; sb < s1; sb += kBatch) {
-        const int32_t nb = min(kBatch, s1 - sb);
-        int32_t minv = kIntMax;
-        if (tid < nb) {
-            const int32_t pos = sb + tid;
+    for (int32_t sb = s0; sb < s1; sb += kLong) {
+        const int32_t nb = min(kLong, s1 - sb);
+        int32_t mv = kIntMax;
+        for (int32_t j = tid; j < nb; j += kThreads) {
+            const int32_t pos = sb + j;
             const long long base = __ldg(A.wp + pos);
             const int32_t ka = int32_t(max(iA, base) - base);
             const int32_t kb = int32_t(min(iB, __ldg(A.wp + pos + 1)) - base);
             const int32_t p0 = __ldg(A.pst + pos);
-            sm.cur[tid] = p0 + ka;
-            sm.end[tid] = p0 + max(ka, kb);
-            sm.owner[tid] = __ldg(A.seg + pos);
-            sm.hit[tid] = 0;
-            if (kb > ka) minv = __ldg(A.col + p0 + ka);
+            sm.l.cur[j] = p0 + ka;
+            sm.l.end[j] = p0 + max(ka, kb);
+            sm.l.hit[j] = 0;
+            const int32_t v = kb > ka ? __ldg(A.col + p0 + ka) : kIntMax;
+            sm.l.nxt[j] = v;
+            mv = min(mv, v);
         }
-        minv = __reduce_min_sync(0xffffffffu, minv);
-        if (lane == 0) sm.ctl[16 + warp] = minv;
+        mv = __reduce_min_sync(0xffffffffu, mv);
+        if (lane == 0) sm.ctl[16 + warp] = mv;
         __syncthreads();
         if (tid == 0) {
-            int32_t mv = kIntMax;
-            for (int k = 0; k < kWarps; ++k) mv = min(mv, sm.ctl[16 + k]);
-            int32_t lo = 0, hi = npieces - 1;  // last piece starting at a column <= mv
-            while (lo < hi) {
-                const int32_t mid = lo + ((hi - lo + 1) >> 1);
-                if (__ldg(A.col + rbase + mid * kCap) <= mv) lo = mid; else hi = mid - 1;
-            }
-            sm.ctl[2] = mv == kIntMax ? npieces : lo;
+            int32_t v = kIntMax;
+            for (int k = 0; k < kWarps; ++k) v = min(v, sm.ctl[16 + k]);
+            sm.ctl[2] = v;
         }
         __syncthreads();
-        const int32_t pfirst = sm.ctl[2];
-        for (int32_t p = pfirst; p < npieces; ++p) {
+        mv = sm.ctl[2];
+        int32_t p = mv == kIntMax ? npieces : piece_of(A.col, rbase, npieces, mv);
+        while (p < npieces) {
             const int32_t ps = rbase + p * kCap;
             const int32_t plen = min(kCap, L - p * kCap);
             const int32_t vhi = (p + 1 < npieces) ? __ldg(A.col + ps + plen) : kIntMax;
-            // run of segment tid: its probes below vhi (binary search)
-            int32_t k = 0, cnt_in = 0, left = 0;
-            if (tid < nb) {
-                // galloping search for the first probe >= vhi in [cur, end)
-                k = sm.cur[tid];
-                const int32_t ke = sm.end[tid];
-                int32_t lo = k, hi = ke;
-                if (k < ke && __ldg(A.col + k) < vhi) {
-                    lo = k + 1;
-                    // positions stay below 2^31 (int32 slots); the step and
-                    // the probe position are kept in 64 bits so neither wraps
-                    for (int64_t step = 1;; step <<= 1) {
-                        const int64_t t = int64_t(k) + step;
-                        if (t >= ke) break;
-                        if (__ldg(A.col + t) >= vhi) {
-                            hi = int32_t(t);
-                            break;
-                        }
-                        lo = int32_t(t) + 1;
-                    }
-                    while (lo < hi) {
-                        const int32_t mid = lo + ((hi - lo) >> 1);
-                        if (__ldg(A.col + mid) < vhi) lo = mid + 1; else hi = mid;
-                    }
-                } else {
-                    hi = k;
-                    lo = k;
-                }
-                cnt_in = lo - k;
-                left = ke - lo;
-            }
-            int32_t nruns, items;
             const int lb = region_lb(plen);
-            build_runs(sm, cnt_in, k, region_word(0, lb), tid, nruns, items);
-            if (items > 0) {
-                clear_table(sm, 1 << lb, plen, tid);
-                __syncthreads();
-                for (int q = tid; q < plen; q += kThreads) {
-                    const int32_t w = __ldg(A.col + ps + q);
-                    sm.vals[q] = w;
-                    if (!table_insert(sm.fpw, sm.slots, 0, lb, w, q))
-                        give_up(A.sched, A.err, kGiveUpInsert, plen, lb);
-                }
-                __syncthreads();
-                probe_runs(A, sm, nruns, items);
-                __syncthreads();
-                for (int q = tid; q < plen; q += kThreads) {
-                    const int32_t v = sm.cnt[q];
-                    if (v) atomicAdd(A.S + ps + q, v);
-                }
-                if (tid < nb) sm.cur[tid] = k + cnt_in;
+            clear_table(sm, 1 << lb, plen, tid);
+            if (tid == 0) {
+                sm.ctl[5] = 0;        // next group of segments to take
+                sm.ctl[6] = kIntMax;  // smallest next probe after this piece
             }
-            if (!__syncthreads_or(left > 0)) break;  // every segment exhausted
+            __syncthreads();
+            for (int q = tid; q < plen; q += kThreads) {
+                const int32_t w = __ldg(A.col + ps + q);
+                sm.vals[q] = w;
+                if (!table_insert(sm.fpw, sm.slots, 0, lb, w, q))
+                    give_up(A.sched, A.err, kGiveUpInsert, plen, lb);
+            }
+            __syncthreads();
+            const uint32_t bm = (1u << lb) - 1u;
+            const int sh = 32 - lb;
+            // warps take one segment at a time, so that long runs spread
+            int32_t low = kIntMax;  // smallest next probe this warp saw
+            for (;;) {
+                int32_t j = 0;
+                if (lane == 0) j = atomicAdd(&sm.ctl[5], 1);
+                j = __shfl_sync(0xffffffffu, j, 0);
+                if (j >= nb) break;
+                const int32_t nx = sm.l.nxt[j];
+                if (nx >= vhi) {
+                    low = min(low, nx);
+                    continue;
+                }
+                int32_t x = sm.l.cur[j];
+                const int32_t xe = sm.l.end[j];
+                int32_t own = 0, nextv = kIntMax;
+                for (;;) {
+                    int32_t wv[kUnroll];
+#pragma unroll
+                    for (int u = 0; u < kUnroll; ++u) {
+                        const int32_t i = x + 32 * u + lane;
+                        wv[u] = i < xe ? __ldg(A.col + i) : kIntMax;
+                    }
+                    int32_t tot = 0;
+                    bool done = false;
+#pragma unroll
+                    for (int u = 0; u < kUnroll; ++u) {
+                        const bool valid = wv[u] < vhi;
+                        if (valid && probe_one(sm, 0, bm, sh, wv[u], A.S + x + 32 * u + lane))
+                            ++own;
+                        const int nv = __popc(__ballot_sync(0xffffffffu, valid));
+                        if (!done) {
+                            tot += nv;
+                            if (nv < 32) {
+                                nextv = __shfl_sync(0xffffffffu, wv[u], nv & 31);
+                                done = true;
+                            }
+                        }
+                    }
+                    x += tot;
+                    if (done) break;
+                }
+                own = __reduce_add_sync(0xffffffffu, own);
+                if (lane == 0) {
+                    sm.l.cur[j] = x;
+                    sm.l.nxt[j] = nextv;
+                    sm.l.hit[j] += own;
+                }
+                low = min(low, nextv);
+            }
+            if (lane == 0 && low < kIntMax) atomicMin(&sm.ctl[6], low);
+            __syncthreads();
+            for (int q = tid; q < plen; q += kThreads) {
+                const int32_t v = sm.cnt[q];
+                if (v) atomicAdd(A.S + ps + q, v);
+            }
+            mv = sm.ctl[6];
+            __syncthreads();  // the next piece clears the table and resets ctl[6]
+            p = mv == kIntMax ? npieces : piece_of(A.col, rbase, npieces, mv);
         }
-        // the next batch writes only this thread's owner/hit entries
-        flush_owners(A, sm, nb, tri);
+        // owner credits of the batch
+        for (int32_t j = tid; j < nb; j += kThreads) {
+            const int32_t v = sm.l.hit[j];
+            if (v) {
+                atomicAdd(A.S + __ldg(A.seg + sb + j), v);
+                tri += v;
+            }
+        }
+        __syncthreads();  // the next batch rewrites the segment arrays
     }
 }
 
@@ -1026,8 +1102,8 @@ support_kernel(SupportArgs A) {
                     len = kb - ka;
                     pos0 = __ldg(A.pst + pos) + ka;
                     key = __ldg(A.sact + pos) - a;
-                    sm.owner[tid] = __ldg(A.seg + pos);
-                    sm.hit[tid] = 0;
+                    sm.b.owner[tid] = __ldg(A.seg + pos);
+                    sm.b.hit[tid] = 0;
                 }
                 int32_t nruns, items;
                 build_runs(sm, len, pos0, tid < nb ? region_word(sm.tbase[key], sm.tlb[key]) : 0,
@@ -1056,21 +1132,40 @@ support_kernel(SupportArgs A) {
     if (lane == 0 && tri) atomicAdd(A.tri, tri);
 }
 
-int g_support_blocks = 0;
+// Resident support CTAs per device (SM count x CTAs per SM), set up once per
+// device together with the kernel's shared-memory attribute, which is a
+// per-device setting.  The first caller on a device does the set-up under a
+// lock; later callers read the table without it.
+constexpr int kMaxDevices = 64;
+std::atomic<int> g_support_blocks[kMaxDevices];
+std::mutex g_configure_mu;
 
-cudaError_t configure_once() {
-    if (g_support_blocks > 0) return cudaSuccess;
-    int dev = 0, sms = 0, occ = 0;
+cudaError_t configure_support(int *blocks) {
+    int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(support_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 int(sizeof(SupportSmem)));
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, support_kernel, kThreads,
-                                                          sizeof(SupportSmem));
     if (e != cudaSuccess) return e;
-    g_support_blocks = sms * (occ > 0 ? occ : 1);
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    int b = g_support_blocks[dev].load(std::memory_order_acquire);
+    if (b > 0) {
+        *blocks = b;
+        return cudaSuccess;
+    }
+    std::lock_guard<std::mutex> lock(g_configure_mu);
+    b = g_support_blocks[dev].load(std::memory_order_acquire);
+    if (b == 0) {
+        int sms = 0, occ = 0;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(support_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     int(sizeof(SupportSmem)));
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, support_kernel, kThreads,
+                                                              sizeof(SupportSmem));
+        if (e != cudaSuccess) return e;
+        b = sms * (occ > 0 ? occ : 1);
+        g_support_blocks[dev].store(b, std::memory_order_release);
+    }
+    *blocks = b;
     return cudaSuccess;
 }
 
@@ -1207,7 +1302,8 @@ cudaError_t launch_support_balanced(const Live &g, int32_t *S, RoundCounters *cn
         if (ev) return cudaEventRecord(ev[1], s);
         return cudaSuccess;
     }
-    cudaError_t e = configure_once();
+    int blocks = 0;
+    cudaError_t e = configure_support(&blocks);
     if (e != cudaSuccess) return e;
     Carve c;
     carve(bs->base, bs->cap_n, bs->cap_m, &c);
@@ -1255,7 +1351,7 @@ cudaError_t launch_support_balanced(const Live &g, int32_t *S, RoundCounters *cn
     active_rows_kernel<<<int((rows + 255) / 256), 256, 0, s>>>(c.rcount, c.rstart, c.arank,
                                                                c.rtot, n, c.arow, c.aseg);
     trace_phase(s, "row scan + active rows");
-    scatter_kernel<<<(m + 255) / 256, 256, 0, s>>>(c.ekey, c.epst, c.eitems, m, c.rstart,
+    scatter_kernel<<<int((int64_t(m) + 255) / 256), 256, 0, s>>>(c.ekey, c.epst, c.eitems, m, c.rstart,
                                                    c.arank, c.rcount, c.seg, c.pst, c.sitems,
                                                    c.sact);
     trace_phase(s, "scatter");
@@ -1268,7 +1364,7 @@ cudaError_t launch_support_balanced(const Live &g, int32_t *S, RoundCounters *cn
     scan_apply_kernel<long long, ItemLoad, ItemStore>
         <<<itiles, kScanThreads, 0, s>>>(il, is, m, c.itile_off);
     trace_phase(s, "item scan");
-    plan_kernel<<<1, 1, 0, s>>>(c.itot, c.rtot, c.wp, c.plan, c.sched, g_support_blocks);
+    plan_kernel<<<1, 1, 0, s>>>(c.itot, c.rtot, c.wp, c.plan, c.sched, blocks);
     partition_kernel<<<64, 256, 0, s>>>(c.wp, c.aseg, c.plan, c.sched, c.bound);
     trace_phase(s, "plan + partition");
     if (trace_phases()) {
@@ -1289,7 +1385,7 @@ cudaError_t launch_support_balanced(const Live &g, int32_t *S, RoundCounters *cn
     }
     SupportArgs A{g.rp, g.col, c.seg, c.pst, c.sact, c.wp, c.arow, c.aseg, c.plan, c.bound,
                   c.sched, S, &cnt->triangles, &cnt->error};
-    support_kernel<<<g_support_blocks, kThreads, sizeof(SupportSmem), s>>>(A);
+    support_kernel<<<blocks, kThreads, sizeof(SupportSmem), s>>>(A);
     if (side) {
         e = cudaStreamWaitEvent(s, bs->join, 0);
         if (e != cudaSuccess) return e;
