@@ -1,23 +1,29 @@
 """K-truss benchmark: Medges/s at fixed K on one GB300 (JSON line on stdout).
 
-Workload (default): R-MAT scale 20, edge factor 16, (a,b,c,d) = (.57,.19,.19,.05),
-symmetrised, de-duplicated, upper-triangular int32 CSR with original vertex ids,
-seed 0; K = 3.  A step is one whole K-truss computation (every peel round:
-support, prune, compaction, convergence test, final outputs) of that graph.
+Workload (default): R-MAT scale 23, edge factor 16, (a,b,c,d) = (.57,.19,.19,.05),
+symmetrised, de-duplicated, with 64 planted cliques of 20..200 vertices,
+upper-triangular int32 CSR with original vertex ids, seed 0; K = 3.  A step is
+one whole K-truss computation (every peel round: support, prune, compaction,
+convergence test, final outputs) of that graph.
 
   value     = edges / device time of ktruss_run, graph resident in HBM
   e2e       = the same metric through the public C ABI with host buffers:
               ktruss_load_csr from pinned host memory + ktruss_run with pinned
               host outputs + ktruss_free, all inside the timed region
-  roofline  = the support step (dominant) against measured HBM bandwidth, with
-              algorithmic bytes per round 4*W + 8*m + 16*T + 8*(n+1)
-              (W = sum over live edges of tail + row-kappa lengths)
+  roofline  = the support kernel (dominant) against measured HBM bandwidth.
+              achieved = the bytes the kernel's design moves per launch
+              (counted on the host from the CSR: probe reads, staged-row
+              reads, credits, segment records) / its CUDA-event time; the
+              merge accounting 4*W + 8*m + 16*T + 8*(n+1) (W = sum over live
+              edges of tail + row-kappa lengths) is reported beside it.
+              `bound` names what the committed ncu capture of the kernel says
+              limits it (DRAM, L2 or SM instruction issue)
   cpu_baseline = the CPU oracle, single thread, on a bounded sample
 
 Between timed steps L2 is flushed by writing a buffer larger than L2.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload rmat20|rmat20r|rmat23c|er2000] [--K 3]
+                  [--workload rmat23c|rmat20|rmat20r|er2000] [--K 3]
                   [--kernel auto|balanced|edge|coarse]
 """
 from __future__ import annotations
@@ -161,25 +167,72 @@ def max_over_ranks(x: float, device=None) -> float:
 
 
 def algorithmic_bytes(n, live, merge, tris):
+    """The merge accounting of a support step: both lists of every task read
+    once (4*W), S zeroed and the owner written (8 per live edge), two credit
+    RMWs per triangle, row_ptr."""
     return 4 * merge + 8 * live + 16 * tris + 8 * (n + 1)
 
 
+def support_work(row_ptr, col, light=64):
+    """Work of the first support step of a CSR, counted on the host.
+
+    For the task of edge e = (i, kappa) at slot e: t = tail length of row i
+    after e, d = length of row kappa.  W = sum of (t + d) over all edges (the
+    merge work the library reports as merge_work).  Tasks with t + d <= light
+    are merged by one thread; every other task with min(t, d) > 0 is a segment
+    that stages the longer list (row kappa if t < d, else row i) and probes it
+    with min(t, d) items.  Returns W, probes (items), staged (total length of
+    the distinct staged rows), segments and active_rows (distinct staged
+    rows)."""
+    import numpy as np
+    rp = np.asarray(row_ptr, dtype=np.int64)
+    c = np.asarray(col, dtype=np.int64)
+    n, m = rp.shape[0] - 1, c.shape[0]
+    deg = np.diff(rp)
+    row = np.repeat(np.arange(n, dtype=np.int64), deg)
+    t = rp[row + 1] - np.arange(m, dtype=np.int64) - 1
+    d = deg[c]
+    W = int(t.sum() + d.sum())
+    short = np.minimum(t, d)
+    heavy = (t + d > light) & (short > 0)
+    staged = np.zeros(max(n, 1), dtype=bool)
+    staged[np.where(t < d, c, row)[heavy]] = True
+    return {"W": W, "probes": int(short[heavy].sum()), "staged": int(deg[staged[:n]].sum()),
+            "segments": int(heavy.sum()), "active_rows": int(staged.sum())}
+
+
+def design_bytes(work, tris):
+    """Bytes the support kernel's design moves in one launch: 4 per probe
+    read, 12 per staged column (read once, plus the read-modify-write that
+    flushes its credits), 8 per triangle (the credit RMW at the probe
+    position), 28 per segment (its records: owner, probe start, active-row
+    rank, item prefix, and the owner's credit RMW), 16 per active staged row
+    (row pointers, active-row tables)."""
+    return (4 * work["probes"] + 12 * work["staged"] + 8 * tris + 28 * work["segments"]
+            + 16 * work["active_rows"])
+
+
 def traffic_record(workload, K):
-    """Per-launch DRAM traffic of the support step from the committed ncu
-    summary, if it was taken on the current kernel source and on this workload
-    and K (else None)."""
+    """The committed ncu record of the support kernel for this workload and K
+    (profiles/support_traffic.json: a list of captures).  Returns (record,
+    fresh): fresh is False when the kernel source changed since the capture,
+    in which case its counters no longer describe the kernel and are not
+    reported."""
     p = os.path.join(ROOT, "profiles", "support_traffic.json")
     try:
         with open(p) as f:
-            rec = json.load(f)
+            recs = json.load(f)
     except (OSError, ValueError):
-        return None
+        return None, False
+    if isinstance(recs, dict):
+        recs = [recs]
     src = os.path.join(ROOT, "paper_2009_07929_gb300", "csrc", "support_balanced.cu")
     with open(src, "rb") as f:
         h = hashlib.sha256(f.read()).hexdigest()
-    if rec.get("source_sha256") != h or rec.get("workload") != f"{workload} K={K} round 1":
-        return None
-    return rec
+    for rec in recs:
+        if rec.get("workload") == f"{workload} K={K} round 1":
+            return rec, rec.get("source_sha256") == h
+    return None, False
 
 
 def host_cpu_model() -> str:
@@ -219,6 +272,50 @@ def cpu_baseline(seconds_cap=30.0, scale=CPU_SAMPLE_SCALE):
             "sample": f"full K=3 run of the single-thread C oracle on R-MAT scale {scale}, "
                       f"edge factor 16 (same recipe, {g.m} edges), {runs} run(s), "
                       f"{el:.1f} s on {os.cpu_count()} host cores (1 used)"}
+
+
+def measure_workload(kt, gg, name, K, steps, flush):
+    """Medges/s of ktruss_run (K, graph resident in HBM, L2 flushed between
+    steps, CUDA events) and the time of its K_max sweep (ktruss_decompose) on
+    another workload, for comparison with the headline one."""
+    import torch
+    progress(f"extra workload {name}")
+    g = gg.cached_workload(name, 0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    h = kt.load(torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col).to(dev))
+    mask = torch.empty(g.m, dtype=torch.uint8, device=dev)
+    sup = torch.empty(g.m, dtype=torch.int32, device=dev)
+    for _ in range(3):
+        flush.fill_(1)
+        h.run(K, out=(mask, sup))
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    sup1 = 0.0
+    for i in range(steps):
+        flush.fill_(i)
+        ev[i][0].record(stream)
+        h.run(K, out=(mask, sup))
+        ev[i][1].record(stream)
+        sup1 += h.stats().ms_support_per_round[0]
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    h.decompose()
+    torch.cuda.synchronize()
+    d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush.fill_(7)
+    d0.record(stream)
+    _, kmax = h.decompose()
+    d1.record(stream)
+    torch.cuda.synchronize()
+    st = h.stats()
+    h.close()
+    return {"workload": WORKLOAD_DESC[name] + f", K={K}", "n": g.n, "m": g.m,
+            "value": round(g.m * steps / (ms / 1e3) / 1e6, 2), "unit": UNIT,
+            "ms_per_step": round(ms / steps, 4), "support_ms_round1": round(sup1 / steps, 4),
+            "kmax_sweep": {"kmax": kmax, "ms": round(d0.elapsed_time(d1), 3),
+                           "rounds": st.rounds, "support_steps": st.support_launches}}
 
 
 def measure_batched(kt, gg, count, m_hi, seed=0):
@@ -376,11 +473,13 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rmat20", choices=sorted(WORKLOAD_DESC))
+    ap.add_argument("--workload", default="rmat23c", choices=sorted(WORKLOAD_DESC))
     ap.add_argument("--K", type=int, default=3)
     ap.add_argument("--kernel", default="auto", choices=["auto", "balanced", "edge", "coarse"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-kmax", action="store_true", help="skip the K_max sweep timing")
+    ap.add_argument("--no-rmat20", action="store_true",
+                    help="skip the extra R-MAT-20 measurement (value and K_max sweep)")
     ap.add_argument("--batch-graphs", type=int, default=4096,
                     help="graphs of the batched-vs-plain measurement (0 = skip)")
     ap.add_argument("--update", choices=sorted(UPDATE_MODES), default="auto",
@@ -424,6 +523,8 @@ def main():
     dev = torch.device("cuda", local)
     rp_d = torch.from_numpy(g.row_ptr).to(dev)
     col_d = torch.from_numpy(g.col).to(dev)
+    progress("counting the support step's work on the host")
+    work = support_work(g.row_ptr, g.col)
     h = kt.load(rp_d, col_d)
     h.set_kernel({"balanced": kt.KERNEL_BALANCED, "edge": kt.KERNEL_EDGE,
                   "coarse": kt.KERNEL_COARSE, "auto": kt.KERNEL_AUTO}[args.kernel])
@@ -445,7 +546,7 @@ def main():
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
-    sup_ms, sup_launches, bytes_alg, launches, st = 0.0, 0, 0, 0, None
+    sup_ms, launches, st = 0.0, 0, None
     with ClockSampler(local) as clk:
         wall0 = time.perf_counter()
         for i in range(args.steps):
@@ -455,13 +556,8 @@ def main():
             ev[i][1].record(stream)
             st = h.stats()
             launches += st.kernel_launches
-            sup_ms += sum(st.ms_support_per_round)
-            sup_launches += st.support_launches
-            # rounds whose supports came from the decremental update ran no
-            # support kernel
-            bytes_alg += sum(algorithmic_bytes(n, lv, mw, tr) for lv, mw, tr, up in
-                             zip(st.live_per_round, st.merge_work_per_round,
-                                 st.triangles_per_round, st.updated_per_round) if not up)
+            # the round-1 support kernel (events around its launch only)
+            sup_ms += st.ms_support_per_round[0] if st.ms_support_per_round else 0.0
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
     step_ms = [a.elapsed_time(b) for a, b in ev]
@@ -539,34 +635,52 @@ def main():
         return
 
     peak, peak_kind = peaks()
-    sup_avg_ms = sup_ms / max(sup_launches, 1)
-    bytes_per_launch = bytes_alg / max(sup_launches, 1)
-    achieved = bytes_per_launch / (sup_avg_ms / 1000.0) / 1e9 if sup_avg_ms > 0 else None
-    tr = traffic_record(args.workload, args.K)
+    sup_avg_ms = sup_ms / args.steps
+    # merge accounting (W counted on the host) and the design's own bytes,
+    # both for the support step of round 1, the only one of a K = 3 run with
+    # the decremental update (later support steps run on smaller graphs)
+    tri1 = st.triangles_per_round[0] if st.triangles_per_round else 0
+    survey_b = algorithmic_bytes(n, m, work["W"], tri1)
+    design_b = design_bytes(work, tri1)
+    achieved = design_b / (sup_avg_ms / 1000.0) / 1e9 if sup_avg_ms > 0 else None
+    rec, fresh = traffic_record(args.workload, args.K)
     roofline = {
-        "bound": "hbm", "achieved": round(achieved, 1) if achieved else None, "peak": peak,
+        "bound": None, "roof": "hbm",
+        "achieved": round(achieved, 1) if achieved else None, "peak": peak,
         "unit": "GB/s", "frac": round(achieved / peak, 4) if achieved else None,
-        "traffic": (int(tr["dram_bytes_per_launch"]) if tr else None),
+        "traffic": None,
         "peak_kind": f"{peak_kind} (HBM copy)",
         "kernel": "support_kernel (support step, Alg. 3)",
         "support_ms_per_launch": round(sup_avg_ms, 4),
-        "alg_bytes_per_launch": int(bytes_per_launch),
-        "accounting": "4*W + 8*m + 16*T + 8*(n+1) per round, W = sum over live edges of "
-                      "tail + row-kappa lengths (merge reads); the kernel probes only the "
-                      "shorter list, so frac can exceed 1",
+        "design_bytes_per_launch": int(design_b),
+        "work": work,
+        "accounting": "design bytes: 4 per probe + 12 per staged column + 8 per triangle + 28 per "
+                      "segment + 16 per active staged row (counted on the host from the CSR; "
+                      "triangles from the run)",
+        "survey_bytes_per_launch": int(survey_b),
+        "frac_survey_accounting": round(survey_b / (sup_avg_ms / 1e3) / 1e9 / peak, 4)
+        if sup_avg_ms > 0 else None,
+        "survey_accounting": "4*W + 8*m + 16*T + 8*(n+1): a full merge of both lists of every "
+                             "task; the kernel probes only the shorter list, so this exceeds the "
+                             "bytes it moves",
     }
-    if tr:
-        roofline["dram_frac"] = round(tr["dram_bytes_per_launch"] / (sup_avg_ms / 1e3) / 1e9 / peak, 4)
-        roofline["traffic_workload"] = tr.get("workload")
-        if "sm_issue_active" in tr:
-            # what bounds the kernel: SM instruction issue (fraction of issue
-            # slots active, ncu), not HBM bandwidth (dram_frac)
-            roofline["sm_issue_active"] = tr["sm_issue_active"]
-        # L2 sector hit rate and warp execution efficiency (active threads per
-        # executed warp instruction / 32) of the same capture
-        for key in ("l2_hit_rate", "warp_exec_efficiency"):
-            if key in tr:
-                roofline[key] = tr[key]
+    if rec is not None and fresh:
+        dram = rec["dram_bytes_per_launch"]
+        roofline["traffic"] = int(dram)
+        roofline["dram_frac"] = round(dram / (sup_avg_ms / 1e3) / 1e9 / peak, 4)
+        roofline["l2_frac"] = rec.get("l2_throughput")
+        roofline["sm_issue_active"] = rec.get("sm_issue_active")
+        for key in ("l2_hit_rate", "warp_exec_efficiency", "warps_active", "traffic_note"):
+            if key in rec:
+                roofline[key] = rec[key]
+        # what limits the kernel: the busiest of DRAM, L2 and SM issue
+        cand = {"hbm": roofline["dram_frac"], "l2": roofline["l2_frac"] or 0.0,
+                "sm_issue": roofline["sm_issue_active"] or 0.0}
+        roofline["bound"] = max(cand, key=cand.get)
+        roofline["ncu_command"] = rec.get("command")
+    else:
+        roofline["traffic_record"] = ("stale: the kernel changed since the committed ncu capture"
+                                      if rec is not None else "none for this workload")
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tot_ms / args.steps, 4),
@@ -589,6 +703,8 @@ def main():
                              "rounds": dec_rounds,
                              "Medges_per_s": round(m / (dec_ms / 1e3) / 1e6, 2),
                              "what": "ktruss_decompose: K = 3 .. K_max, each K from the previous truss"}
+    if not args.no_rmat20 and args.workload != "rmat20":
+        out["rmat20"] = measure_workload(kt, gg, "rmat20", args.K, args.steps, flush)
     if args.batch_graphs > 0:
         out["batched"] = measure_batched(kt, gg, args.batch_graphs, args.batch_mmax)
     if args.serve_requests > 0:

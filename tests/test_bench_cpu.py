@@ -81,7 +81,8 @@ def test_algorithmic_bytes_formula():
 
 def test_traffic_record_is_bound_to_the_profiled_source_and_workload(tmp_path, monkeypatch):
     """An ncu traffic record is used only for the kernel source it was captured
-    on (its sha256) and for its own workload and K."""
+    on (its sha256) and for its own workload and K; a record of a changed
+    source is returned as stale."""
     import hashlib
     sys.path.insert(0, ROOT)
     import bench
@@ -92,13 +93,52 @@ def test_traffic_record_is_bound_to_the_profiled_source_and_workload(tmp_path, m
     rec = {"kernel": "support_kernel", "workload": "rmat20 K=3 round 1",
            "source_sha256": hashlib.sha256(src.read_bytes()).hexdigest(),
            "dram_bytes_per_launch": 123456}
-    (tmp_path / "profiles" / "support_traffic.json").write_text(json.dumps(rec))
+    (tmp_path / "profiles" / "support_traffic.json").write_text(json.dumps([rec]))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench.traffic_record("rmat20", 3)["dram_bytes_per_launch"] == 123456
-    assert bench.traffic_record("rmat20", 4) is None
-    assert bench.traffic_record("rmat23c", 3) is None
+    r, fresh = bench.traffic_record("rmat20", 3)
+    assert fresh and r["dram_bytes_per_launch"] == 123456
+    assert bench.traffic_record("rmat20", 4) == (None, False)
+    assert bench.traffic_record("rmat23c", 3) == (None, False)
     src.write_bytes(b"// kernel source changed after the capture\n")
-    assert bench.traffic_record("rmat20", 3) is None
+    r, fresh = bench.traffic_record("rmat20", 3)
+    assert r is not None and not fresh
+
+
+def _work_by_loops(rp, col, light):
+    """support_work's quantities by plain loops over the edges."""
+    n = len(rp) - 1
+    W = probes = segs = 0
+    staged = set()
+    for i in range(n):
+        for e in range(rp[i], rp[i + 1]):
+            k = col[e]
+            t = rp[i + 1] - e - 1
+            d = rp[k + 1] - rp[k]
+            W += t + d
+            if t + d > light and min(t, d) > 0:
+                probes += min(t, d)
+                segs += 1
+                staged.add(k if t < d else i)
+    return {"W": W, "probes": probes, "segments": segs, "active_rows": len(staged),
+            "staged": sum(rp[r + 1] - rp[r] for r in staged)}
+
+
+@pytest.mark.parametrize("light", [0, 4, 64])
+def test_support_work_counts_match_loops(light):
+    sys.path.insert(0, ROOT)
+    import bench
+    import graphgen as gg
+    for g in (gg.rmat(9, 16, seed=3), gg.er(300, 3000, seed=1), gg.complete(40), gg.star(30),
+              gg.empty(5)):
+        want = _work_by_loops(g.row_ptr.tolist(), g.col.tolist(), light)
+        assert bench.support_work(g.row_ptr, g.col, light) == want
+
+
+def test_design_bytes_formula():
+    sys.path.insert(0, ROOT)
+    import bench
+    w = {"probes": 10, "staged": 5, "segments": 2, "active_rows": 1, "W": 99}
+    assert bench.design_bytes(w, 3) == 40 + 60 + 24 + 56 + 16
 
 
 def test_clock_summary_uses_samples_inside_the_timed_region():

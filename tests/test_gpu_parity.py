@@ -567,3 +567,16 @@ def test_rmat23_cliques_k3_sampled_and_kmax_sweep(kt):
             assert np.array_equal(sup[qs], oracle.edge_support(g.row_ptr, g.col, qs, keep=mask))
         prev = mask
     h.close()
+
+
+def test_host_work_count_equals_library_merge_work(kt):
+    """The benchmark's host count of the merge work W (sum over edges of the
+    tail length plus the row-kappa length, from the CSR alone) equals the merge
+    work the library reports for the first support step."""
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    for g in (gg.rmat(14, 16, seed=0), gg.rmat(12, 16, seed=1, relabel=True),
+              gg.workload("er2000", 0)):
+        _, _, st = gpu_run(kt, g, 3, kernel=0)
+        assert st.merge_work_per_round[0] == bench.support_work(g.row_ptr, g.col)["W"]
