@@ -274,6 +274,29 @@ def cpu_baseline(seconds_cap=30.0, scale=CPU_SAMPLE_SCALE):
                       f"{el:.1f} s on {os.cpu_count()} host cores (1 used)"}
 
 
+def cpu_f_baseline(K=3, name="rmat20"):
+    """The paper's fine-grained CPU design (oracle/cpu_f.c: per-edge tasks,
+    atomic supports, zero-terminated rows; OpenMP) timed once on all host
+    cores on the R-MAT-20 workload, next to the GPU's number for the same
+    graph."""
+    import graphgen as gg
+    import oracle
+    try:
+        oracle.build_cpu_f()
+    except Exception as e:  # no OpenMP compiler on this host
+        return {"unavailable": f"cpu_f.c did not build: {str(e)[:160]}"}
+    g = gg.cached_workload(name, 0)
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    r = oracle.cpu_f_ktruss(g.row_ptr, g.col, K, cores)
+    el = time.perf_counter() - t0
+    return {"value": round(g.m / el / 1e6, 4), "unit": UNIT, "cores": cores,
+            "kind": "cpu_f (the paper's fine-grained CPU design, OpenMP)",
+            "cpu_model": host_cpu_model(),
+            "sample": f"one full K={K} run ({r.rounds} rounds) on {WORKLOAD_DESC[name]} "
+                      f"({g.m} edges), {el:.1f} s on {cores} threads"}
+
+
 def measure_workload(kt, gg, name, K, steps, flush):
     """Medges/s of ktruss_run (K, graph resident in HBM, L2 flushed between
     steps, CUDA events) and the time of its K_max sweep (ktruss_decompose) on
@@ -712,6 +735,8 @@ def main():
     if not args.no_cpu_baseline:
         progress("cpu baseline (oracle)")
         out["cpu_baseline"] = cpu_baseline()
+        progress("cpu baseline (paper's fine-grained CPU design, all cores)")
+        out["cpu_f"] = cpu_f_baseline(args.K)
     print(json.dumps(out), flush=True)
     if pg:
         pg.destroy_process_group()

@@ -18,6 +18,10 @@ package; the product path never does.  It shares no code with the CUDA library.
                              (plain C).
 * ``brute.ktruss_dense``     Alg. 1 written literally with dense 0/1 matrices in
                              numpy, for tiny graphs (``oracle/brute.py``).
+* ``cpu_f_ktruss``           the paper's fine-grained CPU design (per-edge tasks,
+                             atomic supports, zero-terminated rows) with OpenMP
+                             (``cpu_f.c``): the multi-core CPU baseline that the
+                             benchmark times; checked against ``ktruss``.
 
 Parity pins (what ties the oracle to something other than itself) live in
 ``tests/test_oracle.py``.
@@ -35,6 +39,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lib = None
+_CPUF_SRC = os.path.join(_HERE, "cpu_f.c")
+_CPUF_LIB = os.path.join(_HERE, "liboracle_cpuf.so")
+_cpuf = None
 
 ERR_INVALID = -1
 ERR_NOMEM = -2
@@ -47,6 +54,16 @@ def build(force: bool = False) -> str:
         subprocess.check_call(["gcc", "-O2", "-shared", "-fPIC", "-o", tmp, _SRC])
         os.replace(tmp, _LIB)
     return _LIB
+
+
+def build_cpu_f(force: bool = False) -> str:
+    """Compiles cpu_f.c with OpenMP into liboracle_cpuf.so if it is stale."""
+    if force or not os.path.exists(_CPUF_LIB) or \
+            os.path.getmtime(_CPUF_LIB) < os.path.getmtime(_CPUF_SRC):
+        tmp = _CPUF_LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-o", tmp, _CPUF_SRC])
+        os.replace(tmp, _CPUF_LIB)
+    return _CPUF_LIB
 
 
 def _load():
@@ -148,3 +165,25 @@ def triangles(row_ptr, col, keep=None) -> int:
     if rc != 0:
         raise OracleError(rc)
     return t.value
+
+
+def cpu_f_ktruss(row_ptr, col, K: int, threads: int = 0) -> KtrussResult:
+    """The paper's fine-grained CPU K-truss (cpu_f.c) on `threads` OpenMP
+    threads (0 = the runtime's default, all cores).  Returns mask, support and
+    rounds (per-round lists are not recorded)."""
+    global _cpuf
+    if _cpuf is None:
+        lib = ctypes.CDLL(build_cpu_f())
+        vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        lib.cpuf_ktruss.argtypes = [i32, i64, vp, vp, i32, i32, vp, vp, vp]
+        lib.cpuf_ktruss.restype = ctypes.c_int
+        _cpuf = lib
+    rp, c, n, m = _csr(row_ptr, col)
+    mask = np.zeros(max(m, 1), dtype=np.uint8)
+    sup = np.zeros(max(m, 1), dtype=np.int32)
+    rounds = ctypes.c_int32(0)
+    rc = _cpuf.cpuf_ktruss(n, m, rp.ctypes.data, _ptr(c), K, threads, mask.ctypes.data,
+                           sup.ctypes.data, ctypes.addressof(rounds))
+    if rc != 0:
+        raise OracleError(rc)
+    return KtrussResult(mask[:m], sup[:m], rounds.value)

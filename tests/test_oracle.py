@@ -393,3 +393,21 @@ def test_decomposition_agrees_with_peeling_on_rmat20(name):
     assert sum(hist.values()) == dec["m"] and max(hist) == dec["kmax"]
     for c in cases:
         assert c["edges_out"] == sum(v for t, v in hist.items() if t >= c["K"]), c["K"]
+
+
+# ---------------------------------------------- multi-core CPU baseline (CPU-F)
+
+def test_cpu_f_matches_oracle():
+    """The paper's fine-grained CPU design (per-edge tasks with atomic
+    supports on several threads, zero-terminated rows) gives the oracle's
+    masks, supports and round counts."""
+    graphs = er_seeds()[:3] + [gg.rmat(12, 16, seed=s) for s in range(2)] + \
+        [gg.rmat(12, 16, seed=0, relabel=True), gg.complete(12), gg.book(30), gg.star(9),
+         gg.triangle_strip(40), gg.empty(4)]
+    for g in graphs:
+        for K in (2, 3, 4, 6):
+            a = run(g, K)
+            for threads in (1, 4):
+                b = oracle.cpu_f_ktruss(g.row_ptr, g.col, K, threads)
+                assert np.array_equal(a.mask, b.mask) and np.array_equal(a.support, b.support)
+                assert a.rounds == b.rounds
