@@ -83,6 +83,11 @@ extern "C" {
 #define KTRUSS_OPT_SMALL_EDGES 5    /* KTRUSS_KERNEL_AUTO: live graphs with fewer edges use
                                        the one-thread-per-edge kernel; >= 0, default
                                        131072 */
+#define KTRUSS_OPT_DEVICE_LOOP 6    /* 1 (default): rounds whose supports come from the
+                                       decremental update run in a device-driven loop (one
+                                       CUDA graph launch, conditional nodes, no host
+                                       synchronisation per round; results identical);
+                                       0: every round is driven from the host */
 
 typedef struct ktruss_graph ktruss_graph; /* opaque, library-owned */
 
@@ -113,6 +118,10 @@ typedef struct {
                                          decremental update of the previous round's (no
                                          support step ran: its time and merge work are 0) */
     float ms_update;           /* sum of decremental updates (timing on) */
+    float ms_device_loop;      /* rounds run by the device-driven round loop (CUDA graph
+                                  launches and the final scatter after one; timing on) */
+    int32_t device_loop_launches; /* launches of the device-driven round loop */
+    int32_t device_loop_rounds;   /* rounds it ran (included in rounds above) */
 } ktruss_stats_t;
 
 /*

@@ -30,6 +30,7 @@ HOST, DEVICE = 0, 1
 KERNEL_BALANCED, KERNEL_EDGE, KERNEL_COARSE, KERNEL_AUTO = 0, 1, 2, 3
 UPDATE_NEVER, UPDATE_ALWAYS, UPDATE_AUTO = 0, 1, 2
 OPT_SUPPORT_KERNEL, OPT_TIMING, OPT_UPDATE, OPT_LIGHT_MERGE, OPT_SMALL_EDGES = 1, 2, 3, 4, 5
+OPT_DEVICE_LOOP = 6
 
 _lib = None
 
@@ -64,6 +65,9 @@ class _Stats(ctypes.Structure):
         ("kernel_launches", ctypes.c_int32),
         ("updated_per_round", ctypes.POINTER(ctypes.c_int32)),
         ("ms_update", ctypes.c_float),
+        ("ms_device_loop", ctypes.c_float),
+        ("device_loop_launches", ctypes.c_int32),
+        ("device_loop_rounds", ctypes.c_int32),
     ]
 
 
@@ -188,6 +192,9 @@ class Stats:
     kernel_launches: int
     updated_per_round: list
     ms_update: float
+    ms_device_loop: float
+    device_loop_launches: int
+    device_loop_rounds: int
 
     def __getitem__(self, k):
         return getattr(self, k)
@@ -233,6 +240,11 @@ class Graph:
         """UPDATE_NEVER (recompute S every round, Alg. 1 as written),
         UPDATE_ALWAYS or UPDATE_AUTO (default): see KTRUSS_OPT_UPDATE."""
         self.set_option(OPT_UPDATE, mode)
+
+    def set_device_loop(self, on: bool):
+        """KTRUSS_OPT_DEVICE_LOOP: rounds whose supports come from the update
+        run in the device-driven loop (True, default) or from the host."""
+        self.set_option(OPT_DEVICE_LOOP, 1 if on else 0)
 
     def run(self, K: int, support: bool = True, out=None, stream=None):
         """K-truss on the device (ktruss_run, device outputs on the current
@@ -318,7 +330,8 @@ class Graph:
                      arr(st.merge_work_per_round),
                      st.ms_total, st.ms_support, st.ms_balance, st.ms_prune_compact,
                      st.ms_finalize, st.support_launches, st.kernel_launches,
-                     arr(st.updated_per_round), st.ms_update)
+                     arr(st.updated_per_round), st.ms_update, st.ms_device_loop,
+                     st.device_loop_launches, st.device_loop_rounds)
 
 
 def load(row_ptr, col, stream=None) -> Graph:

@@ -151,6 +151,11 @@ struct ktruss_graph {
     uint8_t *keep = nullptr, *done = nullptr, *upd_g = nullptr;
     int32_t *listed_g = nullptr;
     kt::UpdateState ust;  // lower degrees and vertex flags of the support update
+    // device-driven round loop: control block, round records, graph
+    kt::LoopCtl *lc = nullptr;
+    kt::LoopRecord *rec = nullptr;
+    kt::LoopGraph lg;
+    int device_loop = 1;
     std::vector<Owned> owned;
     std::atomic<int> busy{0};
     // options
@@ -190,6 +195,7 @@ void release(ktruss_graph *g) {
     // device blocks (the balanced scratch is part of one) go back to the cache
     for (const Owned &o : g->owned) kt::cache_put(o.p, o.bytes);
     kt::balanced_side_destroy(&g->bs);
+    kt::loop_graph_destroy(&g->lg);
     if (g->cnt_host) pinned_slots().put(g->cnt_host);
     for (cudaEvent_t e : g->events) cudaEventDestroy(e);
     delete g;
@@ -209,6 +215,11 @@ cudaError_t ensure_events(ktruss_graph *g, size_t count) {
 // done, [3] prune + counter read done, [4] update done, [5] compaction or
 // finalize done.
 constexpr size_t kEventsPerRound = 6;
+
+// Round records and iterations one launch of the device loop may run before
+// it returns to the host (which then launches it again).
+constexpr int32_t kLoopRecords = 1024;
+constexpr int32_t kLoopIters = 4096;
 
 // After a round that removed edges: take the next round's supports from the
 // decremental update (true) or recompute them (false).  Under AUTO the update
@@ -364,6 +375,77 @@ float elapsed(cudaEvent_t a, cudaEvent_t b) {
     return ms;
 }
 
+// Launches the handle's device loop (built on first use) from control block
+// c0 on stream s, waits for it, and returns the final control block in *c1
+// and the round records it wrote in *recs.  seed, when given, is copied to
+// record 0 first (the K sweep entering the loop on a graph it already
+// recorded).
+cudaError_t run_device_loop(ktruss_graph *g, cudaStream_t s, const kt::LoopCtl &c0,
+                            const kt::LoopRecord *seed, kt::LoopCtl *c1,
+                            std::vector<kt::LoopRecord> *recs) {
+    if (!g->lg.exec) {
+        kt::LoopBuffers b;
+        b.n = g->n;
+        b.cap_m = int32_t(g->m);
+        for (int p = 0; p < 2; ++p) {
+            b.rp[p] = g->rp[p];
+            b.col[p] = g->col[p];
+            b.eid[p] = g->eid[p];
+        }
+        b.S[0] = g->S;
+        b.S[1] = g->S2;
+        b.pos = g->pos;
+        b.tile_count = g->tile_count;
+        b.tile_off = g->tile_off;
+        b.keep = g->keep;
+        b.cnt = g->cnt;
+        b.us = kt::update_scratch(&g->bs);
+        b.ust = &g->ust;
+        b.lc = g->lc;
+        b.rec = g->rec;
+        cudaError_t e = kt::loop_graph_build(&g->lg, b);
+        if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = cudaMemcpyAsync(g->lc, &c0, sizeof(c0), cudaMemcpyHostToDevice, s);
+    // the loop's prune appends to the list from a zero count (its end kernel
+    // resets it for the next round)
+    if (e == cudaSuccess) e = cudaMemsetAsync(&g->cnt[0].removed_tri, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess && seed)
+        e = cudaMemcpyAsync(g->rec, seed, sizeof(*seed), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaGraphLaunch(g->lg.exec, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c1, g->lc, sizeof(*c1), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    // every iteration either records a round, raises K or stops the loop; a
+    // launch that did none of these would be relaunched forever
+    if (c1->iters < 1 || c1->rec < c0.rec ||
+        (c1->status == kt::kLoopCap && c1->rec == c0.rec && c1->thr == c0.thr && c1->m == c0.m))
+        return cudaErrorLaunchFailure;
+    recs->resize(size_t(c1->rec));
+    if (c1->rec > 0) {
+        e = cudaMemcpyAsync(recs->data(), g->rec, size_t(c1->rec) * sizeof(kt::LoopRecord),
+                            cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    return e;
+}
+
+// Control block of a device loop entered on the current graph of a run.
+kt::LoopCtl loop_start(ktruss_graph *g, int32_t m, int32_t thr, int32_t cur_buf, long long tri) {
+    kt::LoopCtl c{};
+    c.m = m;
+    c.thr = thr;
+    c.ldeg_valid = 1;
+    c.update_mode = g->update_mode;
+    c.buf = cur_buf;
+    c.fresh = 1;
+    c.updated = 1;
+    c.tri = tri;
+    c.rec_cap = kLoopRecords;
+    c.iter_cap = kLoopIters;
+    return c;
+}
+
 }  // namespace
 
 extern "C" {
@@ -419,7 +501,9 @@ static int load_impl(ktruss_graph **out, int32_t n, int64_t m, const int32_t *ro
               A((void **)&g->keep, size_t(m) + 1) &&
               A((void **)&g->ust.ldeg, rpb) && A((void **)&g->ust.flag, rpb) &&
               A((void **)&g->ust.nz, 16) &&
-              A((void **)&g->cnt, 2 * sizeof(kt::RoundCounters));
+              A((void **)&g->cnt, 2 * sizeof(kt::RoundCounters)) &&
+              A((void **)&g->lc, sizeof(kt::LoopCtl)) &&
+              A((void **)&g->rec, kLoopRecords * sizeof(kt::LoopRecord));
     if (ok && G > 0) {
         const size_t gb = (size_t(G) + 1) * 4;
         ok = A((void **)&g->vo, gb) && A((void **)&g->gid, (size_t(n) + 1) * 4) &&
@@ -666,6 +750,10 @@ int ktruss_set_option(ktruss_graph *g, int32_t key, int64_t value) {
             if (value < 0) return KTRUSS_EINVAL;
             g->small_edges = value;
             return KTRUSS_OK;
+        case KTRUSS_OPT_DEVICE_LOOP:
+            if (value != 0 && value != 1) return KTRUSS_EINVAL;
+            g->device_loop = int(value);
+            return KTRUSS_OK;
         default:
             return KTRUSS_EINVAL;
     }
@@ -697,23 +785,73 @@ int ktruss_run(ktruss_graph *g, int32_t K, uint8_t *mask_out, int32_t *support_o
     const kt::UpdateScratch us = kt::update_scratch(&g->bs);
     const Trace trace("run");
     kt::Live cur{g->rp0, g->col0, nullptr, n, m};
+    // The next compaction writes buffer buf; the current graph's supports
+    // are in Sb[buf ^ 1] (the loaded graph counts as buffer 1), so that a
+    // graph in buffer p always has its supports in Sb[p].
     int buf = 0;
+    bool compacted = false;  // cur lives in buffer buf ^ 1 (not the loaded graph)
     int32_t rounds = 0;
-    int32_t *S = g->S, *S_next = g->S2;
-    bool have_s = false;  // S holds the supports of cur (from the update)
+    int32_t *Sb[2] = {g->S, g->S2};
+    bool have_s = false;  // Sb[buf ^ 1] holds the supports of cur (from the update)
     int64_t tri_cur = 0, tri_final = 0;
-    std::vector<size_t> ev_base;
+    std::vector<size_t> ev_base;     // events of each host-driven round
+    std::vector<int32_t> ev_round;   // ... and its round index
+    std::vector<size_t> loop_ev;     // event pairs around device-loop launches
+    std::vector<kt::LoopRecord> recs;
+    int loop_launches = 0, loop_rounds = 0;
+    bool finished = false;
+    size_t next_ev = 2;  // events [0], [1] bracket the run
     cudaEvent_t *ev = nullptr;
     auto mark = [&](size_t k) -> cudaError_t {
         return timing ? cudaEventRecord(ev[k], s) : cudaSuccess;
     };
-    while (cur.m > 0) {
+    while (cur.m > 0 && !finished) {
+        int32_t *S = Sb[buf ^ 1], *S_next = Sb[buf];
+        if (have_s && compacted && g->device_loop) {
+            // rounds whose supports come from the update, on the device
+            if (timing) {
+                KT_CK(ensure_events(g, next_ev + 2));
+                loop_ev.push_back(next_ev);
+                KT_CK(cudaEventRecord(g->events[next_ev], s));
+                next_ev += 2;
+            }
+            kt::LoopCtl c0 = loop_start(g, cur.m, thr, buf ^ 1, tri_cur);
+            c0.mask_out = mask_d;
+            c0.sup_out = sup_d;
+            kt::LoopCtl c1{};
+            KT_CK(run_device_loop(g, s, c0, nullptr, &c1, &recs));
+            ++loop_launches;
+            for (const kt::LoopRecord &r : recs) {
+                ++rounds;
+                ++loop_rounds;
+                g->removed.push_back(r.removed);
+                g->live.push_back(r.live);
+                g->tris.push_back(r.tri);
+                g->merge.push_back(0);
+                g->upd.push_back(r.upd);
+                trace.round(rounds, r.live, r.removed, 0, r.upd != 0);
+            }
+            tri_cur = c1.tri;
+            cur = kt::Live{g->rp[c1.buf], g->col[c1.buf], g->eid[c1.buf], n, c1.m};
+            buf = c1.buf ^ 1;
+            if (c1.status == kt::kLoopConverged) {
+                KT_CK(kt::launch_finalize(cur, Sb[c1.buf], mask_d, sup_d, s, &launches));
+                tri_final = tri_cur;
+                finished = true;
+            } else if (c1.status == kt::kLoopEmpty) {
+                tri_final = 0;
+            }
+            if (timing) KT_CK(cudaEventRecord(g->events[loop_ev.back() + 1], s));
+            have_s = c1.status == kt::kLoopCap;
+            continue;
+        }
         ++rounds;
         if (timing) {
-            const size_t base = 2 + size_t(rounds - 1) * kEventsPerRound;
-            KT_CK(ensure_events(g, base + kEventsPerRound));
-            ev_base.push_back(base);
-            ev = g->events.data() + base;
+            KT_CK(ensure_events(g, next_ev + kEventsPerRound));
+            ev_base.push_back(next_ev);
+            ev_round.push_back(rounds - 1);
+            ev = g->events.data() + next_ev;
+            next_ev += kEventsPerRound;
         }
         const bool updated = have_s;
         if (!have_s) {
@@ -767,7 +905,7 @@ int ktruss_run(ktruss_graph *g, int32_t K, uint8_t *mask_out, int32_t *support_o
         KT_CK(mark(5));
         cur = kt::Live{g->rp[nb], g->col[nb], g->eid[nb], n, kept};
         buf ^= 1;
-        if (upd) std::swap(S, S_next);
+        compacted = true;
         have_s = upd;
         tri_final = 0;
     }
@@ -780,7 +918,8 @@ int ktruss_run(ktruss_graph *g, int32_t K, uint8_t *mask_out, int32_t *support_o
     KT_CK(cudaStreamSynchronize(s));
 
     float ms_total = 0.f, ms_balance = 0.f, ms_support = 0.f, ms_prune = 0.f, ms_final = 0.f,
-          ms_upd = 0.f;
+          ms_upd = 0.f, ms_loop = 0.f;
+    g->ms_sup.assign(size_t(rounds), 0.f);
     if (timing) {
         ms_total = elapsed(g->events[0], g->events[1]);
         for (size_t r = 0; r < ev_base.size(); ++r) {
@@ -793,21 +932,23 @@ int ktruss_run(ktruss_graph *g, int32_t K, uint8_t *mask_out, int32_t *support_o
             ms_balance += bal;
             ms_support += sup;
             ms_upd += up;
-            g->ms_sup.push_back(sup);
-            if (r + 1 == ev_base.size() && g->removed.back() == 0) {
+            g->ms_sup[size_t(ev_round[r])] = sup;
+            if (g->removed[size_t(ev_round[r])] == 0) {
                 ms_prune += pr;
                 ms_final += tail;
             } else {
                 ms_prune += pr + tail;
             }
         }
-    } else {
-        g->ms_sup.assign(size_t(rounds), 0.f);
+        for (size_t k : loop_ev) ms_loop += elapsed(g->events[k], g->events[k + 1]);
     }
     int64_t edges_out = 0;
     if (rounds > 0 && g->removed.back() == 0) edges_out = g->live.back();
     fill_stats(g, rounds, edges_out, tri_final, ms_total, ms_support, ms_balance, ms_prune,
                ms_final, ms_upd, support_launches, launches);
+    g->st.ms_device_loop = ms_loop;
+    g->st.device_loop_launches = loop_launches;
+    g->st.device_loop_rounds = loop_rounds;
     return KTRUSS_OK;
 }
 
@@ -837,14 +978,68 @@ int ktruss_decompose(ktruss_graph *g, int32_t *trussness_out, int32_t *kmax_out,
     const Trace trace("decompose");
     int launches = 0, support_launches = 0, rounds = 0;
     kt::Live cur{g->rp0, g->col0, nullptr, n, m};
+    // buffers and supports as in ktruss_run: the graph in buffer p has its
+    // supports in Sb[p]; the next compaction writes buffer buf
     int buf = 0;
-    int32_t *S = g->S, *S_next = g->S2;
+    bool compacted = false;
+    int32_t *Sb[2] = {g->S, g->S2};
     int32_t K = 3;          // the whole graph is the 2-truss
     bool have_s = false;    // S holds the supports of the current live graph
     bool fresh = true;      // the current live graph has not been pruned yet
     bool updated = false;   // ... and its supports came from the update
     int64_t tri_cur = 0;
+    std::vector<kt::LoopRecord> recs;
+    int loop_launches = 0, loop_rounds = 0;
     while (cur.m > 0) {
+        int32_t *S = Sb[buf ^ 1], *S_next = Sb[buf];
+        if (have_s && compacted && g->device_loop) {
+            // rounds whose supports are current (from the update, or the same
+            // graph at the next K), on the device
+            if (!g->ust.ldeg_valid) KT_CK(kt::launch_lower_degree(cur, &g->ust, s, &launches));
+            kt::LoopCtl c0 = loop_start(g, cur.m, K - 2, buf ^ 1, tri_cur);
+            c0.level_out = tr_d;
+            c0.decompose = 1;
+            c0.fresh = fresh ? 1 : 0;
+            c0.updated = updated ? 1 : 0;
+            kt::LoopRecord seed{};
+            if (!fresh) {
+                // the current graph's round is already recorded: the loop
+                // adds its removals at the next K to that record
+                seed.live = int32_t(g->live.back());
+                seed.removed = int32_t(g->removed.back());
+                seed.upd = g->upd.back();
+                seed.tri = g->tris.back();
+                c0.rec = 1;
+            }
+            kt::LoopCtl c1{};
+            KT_CK(run_device_loop(g, s, c0, fresh ? nullptr : &seed, &c1, &recs));
+            ++loop_launches;
+            size_t first = 0;
+            if (!fresh) {
+                g->removed.back() = recs[0].removed;
+                first = 1;
+            }
+            for (size_t k = first; k < recs.size(); ++k) {
+                const kt::LoopRecord &r = recs[k];
+                ++rounds;
+                ++loop_rounds;
+                g->removed.push_back(r.removed);
+                g->live.push_back(r.live);
+                g->tris.push_back(r.tri);
+                g->merge.push_back(0);
+                g->ms_sup.push_back(0.f);
+                g->upd.push_back(r.upd);
+                trace.round(rounds, r.live, r.removed, 0, r.upd != 0);
+            }
+            K = c1.thr + 2;
+            fresh = c1.fresh != 0;
+            updated = c1.updated != 0;
+            tri_cur = c1.tri;
+            cur = kt::Live{g->rp[c1.buf], g->col[c1.buf], g->eid[c1.buf], n, c1.m};
+            buf = c1.buf ^ 1;
+            have_s = c1.status == kt::kLoopCap;
+            continue;
+        }
         if (fresh) {
             ++rounds;
             if (!have_s) {
@@ -896,7 +1091,7 @@ int ktruss_decompose(ktruss_graph *g, int32_t *trussness_out, int32_t *kmax_out,
                                  K - 1, upd ? g->keep : nullptr, upd ? S_next : nullptr));
         cur = kt::Live{g->rp[nb], g->col[nb], g->eid[nb], n, kept};
         buf ^= 1;
-        if (upd) std::swap(S, S_next);
+        compacted = true;
         have_s = upd;
         updated = upd;
         fresh = true;
@@ -908,6 +1103,8 @@ int ktruss_decompose(ktruss_graph *g, int32_t *trussness_out, int32_t *kmax_out,
     if (kmax_out) *kmax_out = m == 0 ? 0 : K - 1;
     fill_stats(g, rounds, 0, 0, timing ? elapsed(g->events[0], g->events[1]) : 0.f, 0.f, 0.f,
                0.f, 0.f, 0.f, support_launches, launches);
+    g->st.device_loop_launches = loop_launches;
+    g->st.device_loop_rounds = loop_rounds;
     return KTRUSS_OK;
 }
 

@@ -66,6 +66,56 @@ bool trace_on();      // KTRUSS_TRACE >= 1
 bool trace_phases();
 void trace_phase(cudaStream_t s, const char *name);
 
+// ---- device-driven round loop (loop.cu) ------------------------------------
+// Control block of the device-driven round loop, in device memory.  The round
+// kernels launched with a LoopCtl take the live edge count, the threshold and
+// the round's decision from it instead of from their arguments (so their
+// grids are fixed and they loop over the work), and skip their work when the
+// decision does not call for it; the loop's decide and end kernels advance it.
+constexpr int32_t kActUpdate = 1;   // the round updates S (decremental update)
+constexpr int32_t kActCompact = 2;  // the round compacts the live graph into the other buffer
+constexpr int32_t kActCarry = 4;    // the compaction carries S into the other buffer
+
+// Why a device loop stopped (LoopCtl::status).
+constexpr int32_t kLoopRunning = 0;
+constexpr int32_t kLoopConverged = 1;    // a round removed nothing (fixed K): finalize
+constexpr int32_t kLoopEmpty = 2;        // no edge is left
+constexpr int32_t kLoopNeedSupport = 3;  // the next supports need a support step
+constexpr int32_t kLoopCap = 4;          // record or iteration capacity reached
+
+struct LoopCtl {
+    // read by the round kernels
+    int32_t m;           // live edges of the current graph
+    int32_t thr;         // K - 2
+    int32_t action;      // kAct* bits of the current round (decide kernel)
+    int32_t nlist;       // listed edges of the round: removed with S > 0
+    int32_t level;       // trussness written for edges removed now (K - 1)
+    int32_t ldeg_valid;  // the update state's lower degrees are current
+    uint8_t *mask_out;   // outputs of removed edges (may be null)
+    int32_t *sup_out;
+    int32_t *level_out;
+    // loop state
+    int32_t decompose;    // 1: K grows when a round removes nothing; 0: fixed K
+    int32_t update_mode;  // KTRUSS_UPDATE_* value
+    int32_t buf;          // CSR and S buffer holding the current graph (0 or 1)
+    int32_t fresh;        // decompose: the current graph has not been pruned yet
+    int32_t updated;      // the current graph's supports came from the update
+    int32_t status;       // kLoop* value when the loop stopped
+    int32_t rec, rec_cap; // round records written / capacity
+    int32_t iters, iter_cap;  // loop iterations done / capacity
+    long long tri;        // triangles of the current graph
+};
+
+// One round as the host records it (ktruss_stats): live edges, edges removed,
+// whether the supports came from the update, triangles of the live graph.
+struct LoopRecord {
+    int32_t live;
+    int32_t removed;
+    int32_t upd;
+    int32_t pad;
+    long long tri;
+};
+
 // ---- device memory cache (memory.cu) ---------------------------------------
 // cache_get: a block of at least `bytes` on the current device, reused from
 // the cache (blocks of half to all of its size) or newly allocated; give it
@@ -140,8 +190,11 @@ struct UpdateState {
 };
 UpdateScratch update_scratch(const BalancedScratch *bs);
 // out[i] = in[0] + ... + in[i-1] for i in [0, count) (int32, count <= cap_m + 1).
+// With lc (device loop): count is the capacity, the scanned count is
+// lc->nlist + 1 and nothing runs in rounds without update.
 cudaError_t launch_scan_i32(const int32_t *in, int32_t *out, int64_t count,
-                            const UpdateScratch &u, cudaStream_t s, int *launches);
+                            const UpdateScratch &u, cudaStream_t s, int *launches,
+                            const LoopCtl *lc = nullptr);
 
 // Balanced support step: work estimate + int64 scan + partition + staged
 // warp-cooperative intersection.  Adds supports into S (zero on entry).
@@ -167,7 +220,8 @@ cudaError_t launch_support_update(const Live &g, const uint8_t *keep, const int3
                                   int32_t nlist, int32_t *S, unsigned long long *destroyed,
                                   const UpdateScratch &u, UpdateState *st, cudaStream_t s,
                                   int *launches, const int32_t *pos = nullptr,
-                                  int32_t *S_out = nullptr, const uint8_t *upd_g = nullptr);
+                                  int32_t *S_out = nullptr, const uint8_t *upd_g = nullptr,
+                                  const LoopCtl *lc = nullptr);
 
 // ---- prune + compaction + finalize (compact.cu) ---------------------------
 // Tile geometry of the compaction kernels.
@@ -175,9 +229,13 @@ constexpr int kCompactThreads = 256;
 constexpr int kCompactItemsPerThread = 16;
 constexpr int kCompactTile = kCompactThreads * kCompactItemsPerThread;
 
-inline int32_t compact_tiles(int32_t m) {
+inline __host__ __device__ int32_t compact_tiles(int32_t m) {
     return int32_t((int64_t(m) + kCompactTile - 1) / kCompactTile);
 }
+
+// Grid of the round kernels inside the device loop: enough blocks to fill the
+// GPU, each looping over its share of the tiles, slots or list entries.
+constexpr int kLoopBlocks = 152 * 8;
 
 // Counts edges with S >= thr per tile into tile_count[tiles], then scans the
 // tile counts into tile_off[tiles] and writes the total into cnt->kept.  When
@@ -187,7 +245,8 @@ inline int32_t compact_tiles(int32_t m) {
 cudaError_t launch_prune_count(const int32_t *S, int32_t m, int32_t thr, int32_t *tile_count,
                                int32_t *tile_off, RoundCounters *cnt, cudaStream_t s,
                                int *launches, uint8_t *keep = nullptr, int32_t *list = nullptr,
-                               const int32_t *col = nullptr, int32_t *ldeg = nullptr);
+                               const int32_t *col = nullptr, int32_t *ldeg = nullptr,
+                               const LoopCtl *lc = nullptr);
 
 // Scatters kept edges (S >= thr) of `in` into (col_out, eid_out) in order,
 // writes the exclusive kept-prefix of every slot into pos[m_in] (pos[m] =
@@ -202,7 +261,8 @@ cudaError_t launch_compact(const Live &in, const int32_t *S, int32_t thr, const 
                            int32_t *col_out, int32_t *eid_out, uint8_t *mask_out,
                            int32_t *support_out, cudaStream_t s, int *launches,
                            int32_t *level_out = nullptr, int32_t level = 0,
-                           const uint8_t *keep = nullptr, int32_t *S_out = nullptr);
+                           const uint8_t *keep = nullptr, int32_t *S_out = nullptr,
+                           const LoopCtl *lc = nullptr);
 
 // Exclusive scan of tile counts by one block (total -> cnt->kept).
 cudaError_t launch_scan_tiles(const int32_t *tile_count, int32_t tiles, int32_t *tile_off,
@@ -211,6 +271,35 @@ cudaError_t launch_scan_tiles(const int32_t *tile_count, int32_t tiles, int32_t 
 // rp_out[i] = pos[rp_in[i]] (cnt->kept where rp_in[i] == m).
 cudaError_t launch_rowptr(const Live &in, const int32_t *pos, const RoundCounters *cnt,
                           int32_t *rp_out, cudaStream_t s, int *launches);
+
+// ---- device-driven round loop (loop.cu) ------------------------------------
+// The buffers of a handle that the loop's kernels are captured with: the two
+// live CSR buffers and the two support buffers (buffer p holds a graph whose
+// supports are S[p]; a round reads p and writes p ^ 1), the compaction and
+// prune arrays, the round counters ([2]: the round's, the update's), the
+// update's scratch and state, the control block and the round records.
+struct LoopBuffers {
+    int32_t n = 0, cap_m = 0;
+    int32_t *rp[2] = {nullptr, nullptr}, *col[2] = {nullptr, nullptr},
+            *eid[2] = {nullptr, nullptr}, *S[2] = {nullptr, nullptr};
+    int32_t *pos = nullptr, *tile_count = nullptr, *tile_off = nullptr;
+    uint8_t *keep = nullptr;
+    RoundCounters *cnt = nullptr;
+    UpdateScratch us{};
+    const UpdateState *ust = nullptr;
+    LoopCtl *lc = nullptr;
+    LoopRecord *rec = nullptr;
+};
+// The instantiated loop graph of a handle (built on first use, on the device
+// the handle lives on; launched with cudaGraphLaunch on the caller's stream).
+struct LoopGraph {
+    cudaGraphExec_t exec = nullptr;
+};
+cudaError_t loop_graph_build(LoopGraph *lg, const LoopBuffers &b);
+void loop_graph_destroy(LoopGraph *lg);
+
+// st->ldeg = lower degree of every vertex in the live graph g (all its edges).
+cudaError_t launch_lower_degree(const Live &g, UpdateState *st, cudaStream_t s, int *launches);
 
 // ---- batches (batch.cu) -----------------------------------------------------
 // gid[v] = graph of vertex v for vertex offsets vo[G+1].

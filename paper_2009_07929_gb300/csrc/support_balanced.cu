@@ -256,37 +256,56 @@ __device__ __forceinline__ int32_t table_find(const uint32_t *fpw, const uint16_
 
 // ------------------------------------------------------- generic tile scan
 // Exclusive scan in three kernels: per-tile totals, a one-block scan of the
-// totals, and the per-tile rescan that stores the prefixes.
+// totals, and the per-tile rescan that stores the prefixes.  Blocks loop over
+// tiles.  With a LoopCtl (the device loop's int32 scan of the update) the
+// count is lc->nlist + 1 and nothing runs in rounds without update.
+__device__ __forceinline__ bool scan_loop_count(const LoopCtl *lc, int64_t &count) {
+    if (!lc) return true;
+    if (!(lc->action & kActUpdate)) return false;
+    count = int64_t(lc->nlist) + 1;
+    return true;
+}
+
 template <typename V, typename Load>
 __global__ void __launch_bounds__(kScanThreads)
-scan_reduce_kernel(Load ld, int64_t count, V *__restrict__ tile_sum) {
+scan_reduce_kernel(Load ld, int64_t count, V *__restrict__ tile_sum, const LoopCtl *lc) {
     __shared__ V part[kScanThreads / 32];
-    const int64_t i0 = int64_t(blockIdx.x) * kScanTile + threadIdx.x;
-    V s{};
+    if (!scan_loop_count(lc, count)) return;
+    const int64_t tiles = (count + kScanTile - 1) / kScanTile;
+    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int64_t i0 = tile * kScanTile + threadIdx.x;
+        V s{};
 #pragma unroll
-    for (int j = 0; j < kScanPer; ++j) {
-        const int64_t i = i0 + int64_t(j) * kScanThreads;
-        if (i < count) s = s + ld(i);
-    }
+        for (int j = 0; j < kScanPer; ++j) {
+            const int64_t i = i0 + int64_t(j) * kScanThreads;
+            if (i < count) s = s + ld(i);
+        }
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const V u = shfl_up(s, d);
-        if ((threadIdx.x & 31) >= d) s = s + u;
-    }
-    if ((threadIdx.x & 31) == 31) part[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        V t{};
-        for (int k = 0; k < kScanThreads / 32; ++k) t = t + part[k];
-        tile_sum[blockIdx.x] = t;
+        for (int d = 1; d < 32; d <<= 1) {
+            const V u = shfl_up(s, d);
+            if ((threadIdx.x & 31) >= d) s = s + u;
+        }
+        if ((threadIdx.x & 31) == 31) part[threadIdx.x >> 5] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            V t{};
+            for (int k = 0; k < kScanThreads / 32; ++k) t = t + part[k];
+            tile_sum[tile] = t;
+        }
+        __syncthreads();
     }
 }
 
 template <typename V>
 __global__ void __launch_bounds__(1024)
 scan_totals_kernel(const V *__restrict__ tile_sum, int32_t tiles, V *__restrict__ tile_off,
-                   V *__restrict__ total) {
+                   V *__restrict__ total, const LoopCtl *lc) {
     __shared__ V wsum[32];
+    if (lc) {
+        int64_t count = 0;
+        if (!scan_loop_count(lc, count)) return;
+        tiles = int32_t((count + kScanTile - 1) / kScanTile);
+    }
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int32_t per = (tiles + 1023) / 1024;
     const int32_t b = tid * per, e = min(tiles, b + per);
@@ -322,36 +341,42 @@ scan_totals_kernel(const V *__restrict__ tile_sum, int32_t tiles, V *__restrict_
 
 template <typename V, typename Load, typename Store>
 __global__ void __launch_bounds__(kScanThreads)
-scan_apply_kernel(Load ld, Store st, int64_t count, const V *__restrict__ tile_off) {
+scan_apply_kernel(Load ld, Store st, int64_t count, const V *__restrict__ tile_off,
+                  const LoopCtl *lc) {
     __shared__ V part[kScanThreads / 32];
+    if (!scan_loop_count(lc, count)) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    // blocked arrangement: a thread owns kScanPer consecutive items
-    const int64_t i0 = int64_t(blockIdx.x) * kScanTile + int64_t(threadIdx.x) * kScanPer;
-    V v[kScanPer];
-    V s{};
+    const int64_t tiles = (count + kScanTile - 1) / kScanTile;
+    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        // blocked arrangement: a thread owns kScanPer consecutive items
+        const int64_t i0 = tile * kScanTile + int64_t(threadIdx.x) * kScanPer;
+        V v[kScanPer];
+        V s{};
 #pragma unroll
-    for (int j = 0; j < kScanPer; ++j) {
-        const int64_t i = i0 + j;
-        v[j] = i < count ? ld(i) : V{};
-        s = s + v[j];
-    }
-    V incl = s;
+        for (int j = 0; j < kScanPer; ++j) {
+            const int64_t i = i0 + j;
+            v[j] = i < count ? ld(i) : V{};
+            s = s + v[j];
+        }
+        V incl = s;
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const V u = shfl_up(incl, d);
-        if (lane >= d) incl = incl + u;
-    }
-    if (lane == 31) part[w] = incl;
-    __syncthreads();
-    V run = tile_off[blockIdx.x];
-    for (int k = 0; k < w; ++k) run = run + part[k];
-    const V prev = shfl_up(incl, 1);
-    if (lane > 0) run = run + prev;
+        for (int d = 1; d < 32; d <<= 1) {
+            const V u = shfl_up(incl, d);
+            if (lane >= d) incl = incl + u;
+        }
+        if (lane == 31) part[w] = incl;
+        __syncthreads();
+        V run = tile_off[tile];
+        for (int k = 0; k < w; ++k) run = run + part[k];
+        const V prev = shfl_up(incl, 1);
+        if (lane > 0) run = run + prev;
 #pragma unroll
-    for (int j = 0; j < kScanPer; ++j) {
-        const int64_t i = i0 + j;
-        if (i < count) st(i, run);
-        run = run + v[j];
+        for (int j = 0; j < kScanPer; ++j) {
+            const int64_t i = i0 + j;
+            if (i < count) st(i, run);
+            run = run + v[j];
+        }
+        __syncthreads();  // part is rewritten by the next tile
     }
 }
 
@@ -1246,15 +1271,17 @@ UpdateScratch update_scratch(const BalancedScratch *bs) {
 }
 
 cudaError_t launch_scan_i32(const int32_t *in, int32_t *out, int64_t count,
-                            const UpdateScratch &u, cudaStream_t s, int *launches) {
+                            const UpdateScratch &u, cudaStream_t s, int *launches,
+                            const LoopCtl *lc) {
     if (count <= 0) return cudaSuccess;
-    const int32_t tiles = int32_t((count + kScanTile - 1) / kScanTile);
+    int32_t tiles = int32_t((count + kScanTile - 1) / kScanTile);
+    const int32_t grid = lc && tiles > kLoopBlocks ? kLoopBlocks : tiles;
     I32Load ld{in};
     I32Store st{out};
-    scan_reduce_kernel<int32_t, I32Load><<<tiles, kScanThreads, 0, s>>>(ld, count, u.scan_sum);
-    scan_totals_kernel<int32_t><<<1, 1024, 0, s>>>(u.scan_sum, tiles, u.scan_off, u.scan_tot);
+    scan_reduce_kernel<int32_t, I32Load><<<grid, kScanThreads, 0, s>>>(ld, count, u.scan_sum, lc);
+    scan_totals_kernel<int32_t><<<1, 1024, 0, s>>>(u.scan_sum, tiles, u.scan_off, u.scan_tot, lc);
     scan_apply_kernel<int32_t, I32Load, I32Store>
-        <<<tiles, kScanThreads, 0, s>>>(ld, st, count, u.scan_off);
+        <<<grid, kScanThreads, 0, s>>>(ld, st, count, u.scan_off, lc);
     *launches += 3;
     return cudaGetLastError();
 }
@@ -1344,10 +1371,11 @@ cudaError_t launch_support_balanced(const Live &g, int32_t *S, RoundCounters *cn
     const int32_t rtiles = int32_t((rows + kScanTile - 1) / kScanTile);
     RowCountLoad rl{c.rcount};
     RowCountStore rs{c.rstart, c.arank};
-    scan_reduce_kernel<Pair, RowCountLoad><<<rtiles, kScanThreads, 0, s>>>(rl, rows, c.rtile_sum);
-    scan_totals_kernel<Pair><<<1, 1024, 0, s>>>(c.rtile_sum, rtiles, c.rtile_off, c.rtot);
+    scan_reduce_kernel<Pair, RowCountLoad><<<rtiles, kScanThreads, 0, s>>>(rl, rows, c.rtile_sum,
+                                                                       nullptr);
+    scan_totals_kernel<Pair><<<1, 1024, 0, s>>>(c.rtile_sum, rtiles, c.rtile_off, c.rtot, nullptr);
     scan_apply_kernel<Pair, RowCountLoad, RowCountStore>
-        <<<rtiles, kScanThreads, 0, s>>>(rl, rs, rows, c.rtile_off);
+        <<<rtiles, kScanThreads, 0, s>>>(rl, rs, rows, c.rtile_off, nullptr);
     active_rows_kernel<<<int((rows + 255) / 256), 256, 0, s>>>(c.rcount, c.rstart, c.arank,
                                                                c.rtot, n, c.arow, c.aseg);
     trace_phase(s, "row scan + active rows");
@@ -1359,10 +1387,12 @@ cudaError_t launch_support_balanced(const Live &g, int32_t *S, RoundCounters *cn
     const int32_t itiles = int32_t((int64_t(m) + kScanTile - 1) / kScanTile);
     ItemLoad il{c.sitems, c.rtot};
     ItemStore is{c.wp};
-    scan_reduce_kernel<long long, ItemLoad><<<itiles, kScanThreads, 0, s>>>(il, m, c.itile_sum);
-    scan_totals_kernel<long long><<<1, 1024, 0, s>>>(c.itile_sum, itiles, c.itile_off, c.itot);
+    scan_reduce_kernel<long long, ItemLoad><<<itiles, kScanThreads, 0, s>>>(il, m, c.itile_sum,
+                                                                          nullptr);
+    scan_totals_kernel<long long><<<1, 1024, 0, s>>>(c.itile_sum, itiles, c.itile_off, c.itot,
+                                                     nullptr);
     scan_apply_kernel<long long, ItemLoad, ItemStore>
-        <<<itiles, kScanThreads, 0, s>>>(il, is, m, c.itile_off);
+        <<<itiles, kScanThreads, 0, s>>>(il, is, m, c.itile_off, nullptr);
     trace_phase(s, "item scan");
     plan_kernel<<<1, 1, 0, s>>>(c.itot, c.rtot, c.wp, c.plan, c.sched, blocks);
     partition_kernel<<<64, 256, 0, s>>>(c.wp, c.aseg, c.plan, c.sched, c.bound);

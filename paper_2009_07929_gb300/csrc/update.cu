@@ -56,13 +56,38 @@ __device__ __forceinline__ int32_t lower_bound(const int32_t *__restrict__ col, 
 }
 
 // ldeg[v] = number of kept edges (u, v), u < v, of the live graph (its lower
-// degree once the removed edges are gone).
+// degree once the removed edges are gone; keep == nullptr keeps every edge).
 __global__ void __launch_bounds__(kThreads)
 lower_degree_kernel(const int32_t *__restrict__ col, const uint8_t *__restrict__ keep, int32_t m,
                     int32_t *__restrict__ ldeg) {
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < m; e += stride)
-        if (keep[e]) atomicAdd(ldeg + __ldg(col + e), 1);
+        if (!keep || keep[e]) atomicAdd(ldeg + __ldg(col + e), 1);
+}
+
+// Device loop: true when this round runs no update; otherwise the list length
+// and the live edge count come from the loop's control block.
+__device__ __forceinline__ bool loop_skip(const LoopCtl *lc, int32_t &nlist, int32_t &m) {
+    if (!lc) return false;
+    if (!(lc->action & kActUpdate)) return true;
+    nlist = lc->nlist;
+    m = lc->m;
+    return false;
+}
+
+// Device loop: zeroes the per-list counters [0, nlist + 1) and the claimed
+// vertex count before an update.
+__global__ void __launch_bounds__(kThreads)
+update_zero_kernel(const LoopCtl *lc, int32_t *__restrict__ lcnt, int32_t *__restrict__ lfill,
+                   int32_t *__restrict__ nz) {
+    int32_t nlist = 0, m = 0;
+    if (loop_skip(lc, nlist, m)) return;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k <= nlist; k += stride) {
+        lcnt[k] = 0;
+        lfill[k] = 0;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *nz = 0;
 }
 
 // Per listed edge p = (x, y): its row x and the endpoint z of smaller degree
@@ -73,7 +98,9 @@ __global__ void __launch_bounds__(kThreads)
 pick_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, int32_t n,
             const int32_t *__restrict__ ldeg, const int32_t *__restrict__ list, int32_t nlist,
             int32_t *__restrict__ flag, int32_t *__restrict__ lx, const int32_t *__restrict__ gid,
-            const uint8_t *__restrict__ upd_g) {
+            const uint8_t *__restrict__ upd_g, const LoopCtl *lc) {
+    int32_t m_ = 0;
+    if (loop_skip(lc, nlist, m_)) return;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < nlist; k += stride) {
         const int32_t p = __ldg(list + k);
@@ -97,7 +124,9 @@ pick_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, int
 __global__ void __launch_bounds__(kThreads)
 claim_kernel(const int32_t *__restrict__ col, const int32_t *__restrict__ list,
              const int32_t *__restrict__ lx, int32_t nlist, int32_t *__restrict__ flag,
-             int32_t *__restrict__ zlist, int32_t *__restrict__ nz) {
+             int32_t *__restrict__ zlist, int32_t *__restrict__ nz, const LoopCtl *lc) {
+    int32_t m_ = 0;
+    if (loop_skip(lc, nlist, m_)) return;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < nlist; k += stride) {
         const int32_t xw = __ldg(lx + k);
@@ -114,7 +143,9 @@ claim_kernel(const int32_t *__restrict__ col, const int32_t *__restrict__ list,
 // flag[zlist[c]] = 0 for every claimed vertex (c < *nz).
 __global__ void __launch_bounds__(kThreads)
 unflag_kernel(const int32_t *__restrict__ zlist, const int32_t *__restrict__ nz, int32_t cap,
-              int32_t *__restrict__ flag) {
+              int32_t *__restrict__ flag, const LoopCtl *lc) {
+    int32_t m_ = 0;
+    if (loop_skip(lc, cap, m_)) return;
     const int32_t count = *nz;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; c < count && c < cap;
@@ -125,7 +156,9 @@ unflag_kernel(const int32_t *__restrict__ zlist, const int32_t *__restrict__ nz,
 // lcnt[c] += number of edges (u, v) of the live graph, for v with compact index c.
 __global__ void __launch_bounds__(kThreads)
 lower_count_kernel(const int32_t *__restrict__ col, int32_t m, const int32_t *__restrict__ flag,
-                   int32_t *__restrict__ lcnt) {
+                   int32_t *__restrict__ lcnt, const LoopCtl *lc) {
+    int32_t nl_ = 0;
+    if (loop_skip(lc, nl_, m)) return;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < m; e += stride) {
         const int32_t f = flag[__ldg(col + e)];
@@ -140,21 +173,25 @@ __global__ void __launch_bounds__(kThreads)
 lower_fill_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, int32_t n,
                   int32_t m, const int32_t *__restrict__ flag, const int32_t *__restrict__ lrp,
                   int32_t *__restrict__ lfill, int32_t *__restrict__ lsrc,
-                  int32_t *__restrict__ lslot) {
-    const int64_t e0 = (int64_t(blockIdx.x) * kThreads + threadIdx.x) * kSlotsPerThread;
-    if (e0 >= m) return;
-    const int64_t e1 = e0 + kSlotsPerThread < m ? e0 + kSlotsPerThread : m;
-    int32_t u = -1, uend = 0;
-    for (int64_t e = e0; e < e1; ++e) {
-        const int32_t f = flag[__ldg(col + e)];
-        if (f < 2) continue;
-        if (u < 0 || e >= uend) {
-            u = row_of(rp, n, int32_t(e));
-            uend = __ldg(rp + u + 1);
+                  int32_t *__restrict__ lslot, const LoopCtl *lc) {
+    int32_t nl_ = 0;
+    if (loop_skip(lc, nl_, m)) return;
+    const int64_t span = int64_t(gridDim.x) * kThreads * kSlotsPerThread;
+    for (int64_t e0 = (int64_t(blockIdx.x) * kThreads + threadIdx.x) * kSlotsPerThread; e0 < m;
+         e0 += span) {
+        const int64_t e1 = e0 + kSlotsPerThread < m ? e0 + kSlotsPerThread : m;
+        int32_t u = -1, uend = 0;
+        for (int64_t e = e0; e < e1; ++e) {
+            const int32_t f = flag[__ldg(col + e)];
+            if (f < 2) continue;
+            if (u < 0 || e >= uend) {
+                u = row_of(rp, n, int32_t(e));
+                uend = __ldg(rp + u + 1);
+            }
+            const int32_t at = __ldg(lrp + (f - 2)) + atomicAdd(lfill + (f - 2), 1);
+            lsrc[at] = u;
+            lslot[at] = int32_t(e);
         }
-        const int32_t at = __ldg(lrp + (f - 2)) + atomicAdd(lfill + (f - 2), 1);
-        lsrc[at] = u;
-        lslot[at] = int32_t(e);
     }
 }
 
@@ -165,7 +202,10 @@ update_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
               const int32_t *__restrict__ lslot, const uint8_t *__restrict__ keep,
               const int32_t *__restrict__ list, const int32_t *__restrict__ lx, int32_t nlist,
               const int32_t *__restrict__ S, int32_t *__restrict__ S_dec,
-              const int32_t *__restrict__ pos, unsigned long long *__restrict__ destroyed) {
+              const int32_t *__restrict__ pos, unsigned long long *__restrict__ destroyed,
+              const LoopCtl *lc) {
+    int32_t m_ = 0;
+    if (loop_skip(lc, nlist, m_)) return;
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t(gridDim.x) * blockDim.x) >> 5;
     unsigned long long mine = 0;
@@ -222,18 +262,35 @@ update_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
 
 }  // namespace
 
+cudaError_t launch_lower_degree(const Live &g, UpdateState *st, cudaStream_t s, int *launches) {
+    cudaError_t e = cudaMemsetAsync(st->ldeg, 0, (size_t(g.n) + 1) * 4, s);
+    if (e != cudaSuccess) return e;
+    if (g.m > 0) {
+        const int64_t blocks = (int64_t(g.m) + kThreads - 1) / kThreads;
+        lower_degree_kernel<<<int(blocks < 152 * 16 ? blocks : 152 * 16), kThreads, 0, s>>>(
+            g.col, nullptr, g.m, st->ldeg);
+        ++*launches;
+    }
+    st->ldeg_valid = true;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_support_update(const Live &g, const uint8_t *keep, const int32_t *list,
                                   int32_t nlist, int32_t *S, unsigned long long *destroyed,
                                   const UpdateScratch &u, UpdateState *st, cudaStream_t s,
                                   int *launches, const int32_t *pos, int32_t *S_out,
-                                  const uint8_t *upd_g) {
+                                  const uint8_t *upd_g, const LoopCtl *lc) {
+    // in the device loop nlist and g.m are capacities (fixed grids): the
+    // kernels read the round's values from lc and skip rounds without update
     if (nlist <= 0 || g.m == 0) return cudaSuccess;
     const int64_t rows = int64_t(g.n) + 1;
-    auto grid = [](int64_t work, int64_t cap) { return int((work + kThreads - 1) / kThreads < cap
-                                                               ? (work + kThreads - 1) / kThreads
-                                                               : cap); };
+    auto grid = [lc](int64_t work, int64_t cap) {
+        if (lc && cap > kLoopBlocks) cap = kLoopBlocks;
+        return int((work + kThreads - 1) / kThreads < cap ? (work + kThreads - 1) / kThreads : cap);
+    };
     cudaError_t e = cudaSuccess;
     if (!st->ldeg_valid) {
+        if (lc) return cudaErrorInvalidValue;  // the loop starts with valid lower degrees
         // lower degrees after this round's removals; prune keeps them current
         // from here on by subtracting the edges it removes
         e = cudaMemsetAsync(st->ldeg, 0, size_t(rows) * 4, s);
@@ -245,26 +302,32 @@ cudaError_t launch_support_update(const Live &g, const uint8_t *keep, const int3
     // per-list arrays: at most nlist flagged vertices (st->flag is all zero
     // between calls; the claimed entries are reset at the end)
     const int64_t zcap = int64_t(nlist) + 1;
-    e = cudaMemsetAsync(st->nz, 0, 4, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(u.lcnt, 0, size_t(zcap) * 4, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(u.lfill, 0, size_t(zcap) * 4, s);
-    if (e != cudaSuccess) return e;
+    if (lc) {
+        update_zero_kernel<<<grid(zcap, 152 * 16), kThreads, 0, s>>>(lc, u.lcnt, u.lfill, st->nz);
+        ++*launches;
+    } else {
+        e = cudaMemsetAsync(st->nz, 0, 4, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(u.lcnt, 0, size_t(zcap) * 4, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(u.lfill, 0, size_t(zcap) * 4, s);
+        if (e != cudaSuccess) return e;
+    }
     pick_kernel<<<grid(nlist, 152 * 16), kThreads, 0, s>>>(g.rp, g.col, g.n, st->ldeg, list, nlist,
-                                                            st->flag, u.lx, g.gid, upd_g);
+                                                            st->flag, u.lx, g.gid, upd_g, lc);
     claim_kernel<<<grid(nlist, 152 * 16), kThreads, 0, s>>>(g.col, list, u.lx, nlist, st->flag,
-                                                             u.zlist, st->nz);
-    lower_count_kernel<<<grid(g.m, 152 * 16), kThreads, 0, s>>>(g.col, g.m, st->flag, u.lcnt);
+                                                             u.zlist, st->nz, lc);
+    lower_count_kernel<<<grid(g.m, 152 * 16), kThreads, 0, s>>>(g.col, g.m, st->flag, u.lcnt, lc);
     *launches += 3;
-    e = launch_scan_i32(u.lcnt, u.lrp, zcap, u, s, launches);
+    e = launch_scan_i32(u.lcnt, u.lrp, zcap, u, s, launches, lc);
     if (e != cudaSuccess) return e;
-    const int64_t fblocks =
+    int64_t fblocks =
         (int64_t(g.m) + int64_t(kThreads) * kSlotsPerThread - 1) / (int64_t(kThreads) * kSlotsPerThread);
+    if (lc && fblocks > kLoopBlocks) fblocks = kLoopBlocks;
     lower_fill_kernel<<<int(fblocks), kThreads, 0, s>>>(g.rp, g.col, g.n, g.m, st->flag, u.lrp,
-                                                        u.lfill, u.lsrc, u.lslot);
+                                                        u.lfill, u.lsrc, u.lslot, lc);
     update_kernel<<<grid(int64_t(nlist) * 32, 152 * 32), kThreads, 0, s>>>(
         g.rp, g.col, st->flag, u.lrp, u.lsrc, u.lslot, keep, list, u.lx, nlist, S,
-        pos ? S_out : S, pos, destroyed);
-    unflag_kernel<<<grid(nlist, 152 * 16), kThreads, 0, s>>>(u.zlist, st->nz, nlist, st->flag);
+        pos ? S_out : S, pos, destroyed, lc);
+    unflag_kernel<<<grid(nlist, 152 * 16), kThreads, 0, s>>>(u.zlist, st->nz, nlist, st->flag, lc);
     *launches += 3;
     return cudaGetLastError();
 }

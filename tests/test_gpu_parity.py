@@ -580,3 +580,79 @@ def test_host_work_count_equals_library_merge_work(kt):
               gg.workload("er2000", 0)):
         _, _, st = gpu_run(kt, g, 3, kernel=0)
         assert st.merge_work_per_round[0] == bench.support_work(g.row_ptr, g.col)["W"]
+
+
+# ------------------------------------------------ device-driven round loop
+
+def _run_loop(kt, g, K, loop, update):
+    import torch
+    h = kt.load(torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col).cuda())
+    h.set_device_loop(loop)
+    h.set_update(update)
+    m_t, s_t = h.run(K)
+    torch.cuda.synchronize()
+    st = h.stats()
+    out = (m_t.cpu().numpy(), s_t.cpu().numpy(), st)
+    h.close()
+    return out
+
+
+@pytest.mark.parametrize("update", [1, 2])
+def test_device_loop_rounds_match_oracle(kt, update):
+    """Rounds whose supports come from the decremental update run in the
+    device-driven loop (one CUDA graph launch with conditional nodes, no host
+    synchronisation per round).  Masks, supports and every per-round statistic
+    equal the oracle's, with the loop on and off."""
+    cases = [(g, K) for g, K, _ in deep_cascade_graphs()]
+    cases += [(gg.triangle_strip(101), 4), (gg.rmat(14, 16, 1), 4), (gg.rmat(14, 16, 1), 8),
+              (gg.rmat(12, 8, seed=4, n_cliques=6, clique_lo=10, clique_hi=30), 12),
+              (gg.workload("er2000", 3), 4)]
+    for g, K in cases:
+        r = oracle.ktruss(g.row_ptr, g.col, K)
+        for loop in (True, False):
+            mask, sup, st = _run_loop(kt, g, K, loop, update)
+            where = f"(K={K}, loop={loop}, update={update})"
+            assert np.array_equal(mask, r.mask), where
+            assert np.array_equal(sup, r.support), where
+            assert st.rounds == r.rounds, where
+            assert st.removed_per_round == r.removed_per_round, where
+            assert st.triangles_per_round == r.triangles_per_round, where
+            assert st.triangles_out == r.triangles and st.edges_out == int(r.mask.sum())
+            if not loop:
+                assert st.device_loop_rounds == 0 and st.device_loop_launches == 0
+            elif update == 1 and r.rounds >= 2:
+                # round 1 runs the support step on the host; every later
+                # round takes its supports from the update, on the device
+                assert st.device_loop_rounds == r.rounds - 1, where
+                assert st.device_loop_launches >= 1
+
+
+@pytest.mark.parametrize("update", [1, 2])
+def test_device_loop_decomposition(kt, update):
+    """The K sweep in the device-driven loop (a round that removes nothing
+    raises K on the same graph) gives the oracle's trussness and the host
+    loop's per-round statistics."""
+    import torch
+    graphs = [gg.rmat(14, 8, seed=3, n_cliques=8, clique_lo=20, clique_hi=60),
+              gg.triangle_strip(60), gg.er(2000, 16000, 1), gg.book(20), gg.complete(12),
+              gg.rmat(13, 16, seed=5)]
+    for g in graphs:
+        want = oracle.truss_decomposition(g.row_ptr, g.col)
+        stats = []
+        for loop in (True, False):
+            h = kt.load(torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col).cuda())
+            h.set_device_loop(loop)
+            h.set_update(update)
+            tr, kmax = h.decompose()
+            torch.cuda.synchronize()
+            assert np.array_equal(tr.cpu().numpy(), want)
+            assert kmax == (int(want.max()) if g.m else 0)
+            stats.append(h.stats())
+            h.close()
+        a, b = stats
+        assert a.rounds == b.rounds
+        assert a.removed_per_round == b.removed_per_round
+        assert a.live_per_round == b.live_per_round
+        assert a.triangles_per_round == b.triangles_per_round
+        assert a.updated_per_round == b.updated_per_round
+        assert b.device_loop_rounds == 0
