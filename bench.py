@@ -212,6 +212,19 @@ def design_bytes(work, tris):
             + 16 * work["active_rows"])
 
 
+KERNEL_SOURCES = ("support_balanced.cu", "support_shape.cuh")
+
+
+def kernel_source_sha256(root=None) -> str:
+    """SHA-256 over the support kernel's source files (in a fixed order)."""
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        p = os.path.join(root or ROOT, "paper_2009_07929_gb300", "csrc", name)
+        with open(p, "rb") as f:
+            h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()
+
+
 def traffic_record(workload, K):
     """The committed ncu record of the support kernel for this workload and K
     (profiles/support_traffic.json: a list of captures).  Returns (record,
@@ -226,9 +239,7 @@ def traffic_record(workload, K):
         return None, False
     if isinstance(recs, dict):
         recs = [recs]
-    src = os.path.join(ROOT, "paper_2009_07929_gb300", "csrc", "support_balanced.cu")
-    with open(src, "rb") as f:
-        h = hashlib.sha256(f.read()).hexdigest()
+    h = kernel_source_sha256()
     for rec in recs:
         if rec.get("workload") == f"{workload} K={K} round 1":
             return rec, rec.get("source_sha256") == h
@@ -430,7 +441,8 @@ def measure_serving(kt, gg, count, m_hi, seed=0):
     warm.close()
     srv = server()
     progress("serving: saturated")
-    _, sat_s, _ = kt.serve_poisson(srv, reqs, rate=None, outputs=outs)
+    steps = []
+    _, sat_s, _ = kt.serve_poisson(srv, reqs, rate=None, outputs=outs, step_times=steps)
     srv.close()
     sat = count / sat_s
     progress(f"serving: saturated {sat:.2f} graphs/s; Poisson arrivals")
@@ -450,7 +462,16 @@ def measure_serving(kt, gg, count, m_hi, seed=0):
             "arrival_rate": round(0.7 * sat, 2),
             "graphs_per_s": round(count / mk, 2),
             "p50_latency_ms": round(float(np.percentile(lat, 50)) * 1e3, 3),
-            "p99_latency_ms": round(float(np.percentile(lat, 99)) * 1e3, 3)}
+            "p99_latency_ms": round(float(np.percentile(lat, 99)) * 1e3, 3),
+            "saturated_steps": len(steps),
+            "step_host_ms": {"mean": round(1e3 * float(np.mean(steps)), 3),
+                             "p50": round(1e3 * float(np.percentile(steps, 50)), 3),
+                             "p99": round(1e3 * float(np.percentile(steps, 99)), 3),
+                             "sum": round(1e3 * float(np.sum(steps)), 1)},
+            "what": "latency from arrival to results in host memory; step_host_ms = wall time "
+                    "of each Server.step of the saturated run (admission, one batched peel "
+                    "round of every active request on the device, output copies of finished "
+                    "requests)"}
 
 
 def run_reference(args, world, rank):
@@ -508,7 +529,7 @@ def main():
     ap.add_argument("--update", choices=sorted(UPDATE_MODES), default="auto",
                     help="supports after the first round: decremental update (auto/always) or "
                          "recomputed every round (never, Alg. 1 as written)")
-    ap.add_argument("--serve-requests", type=int, default=64,
+    ap.add_argument("--serve-requests", type=int, default=256,
                     help="requests of the serving measurement (0 = skip)")
     ap.add_argument("--serve-mmax", type=float, default=5e7,
                     help="largest request size (edges) of the serving measurement (the "

@@ -83,6 +83,11 @@ extern "C" {
 #define KTRUSS_OPT_SMALL_EDGES 5    /* KTRUSS_KERNEL_AUTO: live graphs with fewer edges use
                                        the one-thread-per-edge kernel; >= 0, default
                                        131072 */
+#define KTRUSS_OPT_SUPPORT_SHAPE 7  /* CTA shape of the balanced support kernel: 0 = 1024
+                                       threads per CTA, one CTA per SM, stages of 8192 staged
+                                       slots (32 warps resident); 1 (default) = 512 threads,
+                                       three CTAs per SM, stages of 2048 slots (48 warps);
+                                       results identical */
 #define KTRUSS_OPT_DEVICE_LOOP 6    /* 1 (default): rounds whose supports come from the
                                        decremental update run in a device-driven loop (one
                                        CUDA graph launch, conditional nodes, no host
@@ -297,12 +302,15 @@ typedef struct {
     int32_t update_mode;  /* KTRUSS_OPT_UPDATE */
     float ms;             /* device time of the best run (ms) */
     int32_t trials;       /* runs timed */
+    int32_t support_shape; /* KTRUSS_OPT_SUPPORT_SHAPE */
 } ktruss_tune_t;
 
 /*
- * Autotuner: picks KTRUSS_OPT_LIGHT_MERGE (merge or stage-and-probe, by list
- * length), KTRUSS_OPT_SMALL_EDGES (per-edge or balanced kernel, by live size)
- * and KTRUSS_OPT_UPDATE for this handle's graph by timing whole runs on it:
+ * Autotuner: picks KTRUSS_OPT_SUPPORT_SHAPE (threads per CTA and staging
+ * tile of the support kernel), KTRUSS_OPT_LIGHT_MERGE (merge or stage-and-
+ * probe, by list length), KTRUSS_OPT_SMALL_EDGES (per-edge or balanced kernel,
+ * by live size) and KTRUSS_OPT_UPDATE for this handle's graph by timing whole
+ * runs on it:
  * ktruss_run with K[0] when num_K == 1, or ktruss_run_batch with K[0..G) when
  * the handle is a batch of G graphs and num_K == G.  Candidates are tried one
  * option at a time (coordinate descent from the current settings), each run

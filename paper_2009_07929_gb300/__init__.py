@@ -30,7 +30,7 @@ HOST, DEVICE = 0, 1
 KERNEL_BALANCED, KERNEL_EDGE, KERNEL_COARSE, KERNEL_AUTO = 0, 1, 2, 3
 UPDATE_NEVER, UPDATE_ALWAYS, UPDATE_AUTO = 0, 1, 2
 OPT_SUPPORT_KERNEL, OPT_TIMING, OPT_UPDATE, OPT_LIGHT_MERGE, OPT_SMALL_EDGES = 1, 2, 3, 4, 5
-OPT_DEVICE_LOOP = 6
+OPT_DEVICE_LOOP, OPT_SUPPORT_SHAPE = 6, 7
 
 _lib = None
 
@@ -78,6 +78,7 @@ class _Tune(ctypes.Structure):
         ("update_mode", ctypes.c_int32),
         ("ms", ctypes.c_float),
         ("trials", ctypes.c_int32),
+        ("support_shape", ctypes.c_int32),
     ]
 
 
@@ -226,20 +227,27 @@ class Graph:
 
     def autotune(self, K, reps: int = 2, stream=None) -> dict:
         """ktruss_autotune: times whole runs of this graph (K an int) or batch
-        (K one value per graph) with candidate light-merge thresholds, AUTO
-        kernel thresholds and update modes, leaves the fastest set on the
-        handle and returns them."""
+        (K one value per graph) with candidate support-kernel CTA shapes,
+        light-merge thresholds, AUTO kernel thresholds and update modes,
+        leaves the fastest set on the handle and returns them."""
         Ks = np.ascontiguousarray(np.atleast_1d(np.asarray(K, dtype=np.int32)))
         t = _Tune()
         _check(lib().ktruss_autotune(self._h, Ks.ctypes.data, Ks.shape[0], reps, ctypes.byref(t),
                                      _stream_ptr(stream)), "ktruss_autotune")
         return {"light_merge": t.light_merge, "small_edges": t.small_edges,
-                "update_mode": t.update_mode, "ms": t.ms, "trials": t.trials}
+                "update_mode": t.update_mode, "support_shape": t.support_shape, "ms": t.ms,
+                "trials": t.trials}
 
     def set_update(self, mode: int):
         """UPDATE_NEVER (recompute S every round, Alg. 1 as written),
         UPDATE_ALWAYS or UPDATE_AUTO (default): see KTRUSS_OPT_UPDATE."""
         self.set_option(OPT_UPDATE, mode)
+
+    def set_support_shape(self, shape: int):
+        """KTRUSS_OPT_SUPPORT_SHAPE: 0 = 1024-thread CTAs with 8192-slot
+        stages, 1 (default) = 512-thread CTAs, three per SM, 2048-slot
+        stages."""
+        self.set_option(OPT_SUPPORT_SHAPE, shape)
 
     def set_device_loop(self, on: bool):
         """KTRUSS_OPT_DEVICE_LOOP: rounds whose supports come from the update
@@ -472,13 +480,14 @@ class Server:
         return q.value, a.value, e.value
 
 
-def serve_poisson(server, requests, rate, seed=0, clock=None, outputs=None):
+def serve_poisson(server, requests, rate, seed=0, clock=None, outputs=None, step_times=None):
     """Feeds (csr, K) requests to a Server with Poisson arrivals of the given
     rate (requests/s; None = all at time 0) in real time and steps it until
     every request is done.  outputs: optional (mask, support) host arrays per
-    request (Server.submit's mask_out / support_out).  Returns per-request
-    latencies (s, arrival to completion), the makespan and the results by
-    request index."""
+    request (Server.submit's mask_out / support_out).  step_times: optional
+    list that receives the host time (s) of every Server.step call.  Returns
+    per-request latencies (s, arrival to completion), the makespan and the
+    results by request index."""
     import time
     clock = clock or time.perf_counter
     rng = np.random.default_rng(seed)
@@ -503,7 +512,11 @@ def serve_poisson(server, requests, rate, seed=0, clock=None, outputs=None):
             if i < N:
                 time.sleep(max(0.0, min(0.001, arrivals[i] - (clock() - t0))))
             continue
-        for t, r, mask, sup in server.step():
+        ts = clock()
+        finished = server.step()
+        if step_times is not None:
+            step_times.append(clock() - ts)
+        for t, r, mask, sup in finished:
             k = ticket_of.pop(t)
             latency[k] = (clock() - t0) - arrivals[k]
             results[k] = (r, mask, sup)

@@ -750,6 +750,10 @@ int ktruss_set_option(ktruss_graph *g, int32_t key, int64_t value) {
             if (value < 0) return KTRUSS_EINVAL;
             g->small_edges = value;
             return KTRUSS_OK;
+        case KTRUSS_OPT_SUPPORT_SHAPE:
+            if (value != 0 && value != 1) return KTRUSS_EINVAL;
+            g->bs.shape = int32_t(value);
+            return KTRUSS_OK;
         case KTRUSS_OPT_DEVICE_LOOP:
             if (value != 0 && value != 1) return KTRUSS_EINVAL;
             g->device_loop = int(value);
@@ -1157,12 +1161,14 @@ int ktruss_autotune(ktruss_graph *g, const int32_t *K, int32_t num_K, int32_t re
     const int64_t smalls[] = {int64_t(1) << 15, int64_t(1) << 17, int64_t(1) << 19,
                               int64_t(1) << 21};
     const int64_t updates[] = {KTRUSS_UPDATE_AUTO, KTRUSS_UPDATE_NEVER, KTRUSS_UPDATE_ALWAYS};
+    const int64_t shapes[] = {0, 1};
     struct Axis {
         int32_t key;
         const int64_t *vals;
         int count;
         int64_t cur;
-    } axes[] = {{KTRUSS_OPT_LIGHT_MERGE, lights, 5, g->bs.light},
+    } axes[] = {{KTRUSS_OPT_SUPPORT_SHAPE, shapes, 2, g->bs.shape},
+                {KTRUSS_OPT_LIGHT_MERGE, lights, 5, g->bs.light},
                 {KTRUSS_OPT_SMALL_EDGES, smalls, 4, g->small_edges},
                 {KTRUSS_OPT_UPDATE, updates, 3, g->update_mode}};
     for (Axis &ax : axes) {
@@ -1187,6 +1193,7 @@ int ktruss_autotune(ktruss_graph *g, const int32_t *K, int32_t num_K, int32_t re
         out->light_merge = g->bs.light;
         out->small_edges = g->small_edges;
         out->update_mode = g->update_mode;
+        out->support_shape = g->bs.shape;
         out->ms = best;
         out->trials = trials;
     }

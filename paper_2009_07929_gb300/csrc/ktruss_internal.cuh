@@ -50,6 +50,9 @@ constexpr int kWarp = 32;
 // BalancedScratch::light); chosen by a sweep on R-MAT and G(n,m) graphs.
 constexpr int32_t kDefaultLight = 64;
 constexpr int32_t kMaxLight = 1024;
+// Default CTA shape of the support kernel (BalancedScratch::shape): the faster
+// of the two on R-MAT-20 and on R-MAT-23 with planted cliques.
+constexpr int32_t kDefaultShape = 1;
 // Per-graph update rule of batches and the server: a graph's next supports
 // come from the decremental update while its listed edges (removed, in some
 // triangle) are at most a quarter of its surviving edges.  A graph above that
@@ -151,6 +154,9 @@ struct BalancedScratch {
     // tasks whose two lists hold at most `light` columns together are merged
     // by one thread instead of being staged and probed (0 = none)
     int32_t light = kDefaultLight;
+    // CTA shape of the support kernel: 0 = 1024 threads, one CTA per SM,
+    // 8192-slot stages; 1 = 512 threads, three CTAs per SM, 2048-slot stages
+    int32_t shape = kDefaultShape;
     // optional: a second stream and two events on which the light merge runs
     // alongside the balancing kernels (joined before the step returns)
     cudaStream_t side = nullptr;

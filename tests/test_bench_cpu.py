@@ -89,9 +89,11 @@ def test_traffic_record_is_bound_to_the_profiled_source_and_workload(tmp_path, m
     src = tmp_path / "paper_2009_07929_gb300" / "csrc" / "support_balanced.cu"
     src.parent.mkdir(parents=True)
     src.write_bytes(b"// kernel source as captured\n")
+    shape = src.parent / "support_shape.cuh"
+    shape.write_bytes(b"// per-shape part\n")
     (tmp_path / "profiles").mkdir()
     rec = {"kernel": "support_kernel", "workload": "rmat20 K=3 round 1",
-           "source_sha256": hashlib.sha256(src.read_bytes()).hexdigest(),
+           "source_sha256": bench.kernel_source_sha256(str(tmp_path)),
            "dram_bytes_per_launch": 123456}
     (tmp_path / "profiles" / "support_traffic.json").write_text(json.dumps([rec]))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
@@ -99,7 +101,7 @@ def test_traffic_record_is_bound_to_the_profiled_source_and_workload(tmp_path, m
     assert fresh and r["dram_bytes_per_launch"] == 123456
     assert bench.traffic_record("rmat20", 4) == (None, False)
     assert bench.traffic_record("rmat23c", 3) == (None, False)
-    src.write_bytes(b"// kernel source changed after the capture\n")
+    shape.write_bytes(b"// per-shape part changed after the capture\n")
     r, fresh = bench.traffic_record("rmat20", 3)
     assert r is not None and not fresh
 

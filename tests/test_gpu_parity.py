@@ -350,12 +350,42 @@ def test_autotune_picks_candidates_and_keeps_results(kt):
         assert t["light_merge"] in (0, 32, 64, 128, 256)
         assert t["small_edges"] in (1 << 15, 1 << 17, 1 << 19, 1 << 21)
         assert t["update_mode"] in (0, 1, 2) and t["trials"] >= 10 and t["ms"] > 0
+        assert t["support_shape"] in (0, 1)
         r = oracle.ktruss(g.row_ptr, g.col, K)
         m_t, s_t = h.run(K)
         torch.cuda.synchronize()
         assert np.array_equal(m_t.cpu().numpy(), r.mask)
         assert np.array_equal(s_t.cpu().numpy(), r.support)
         assert h.stats().rounds == r.rounds
+        h.close()
+
+
+@pytest.mark.parametrize("shape", [0, 1])
+def test_support_shapes(kt, shape):
+    """Both CTA shapes of the balanced support kernel (1024 threads with
+    8192-slot stages; 512 threads, three per SM, with 2048-slot stages) give
+    the oracle's results, on graphs whose staged rows are shorter than a
+    stage, longer than a 2048-slot stage, and longer than an 8192-slot one."""
+    import torch
+    L = 20000
+    edges = [(0, j) for j in range(1, L + 1)]
+    edges += [(j, j + 1) for j in range(1, L)] + [(j, j + 7) for j in range(1, L - 7, 3)]
+    cases = [(gg.rmat(12, 16, 0), (3, 4)), (gg.rmat(16, 16, 2), (3, 5)),
+             (gg.rmat(14, 16, 1, relabel=True), (3, 4)), (gg.from_edges(L + 1, edges), (3, 4)),
+             (gg.book(70000), (3,)), (gg.workload("er2000", 1), (3, 4)),
+             (gg.rmat(14, 8, seed=3, n_cliques=8, clique_lo=20, clique_hi=60), (3, 20))]
+    for g, Ks in cases:
+        h = kt.load(torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col).cuda())
+        h.set_kernel(0)
+        h.set_support_shape(shape)
+        for K in Ks:
+            r = oracle.ktruss(g.row_ptr, g.col, K)
+            m_t, s_t = h.run(K)
+            torch.cuda.synchronize()
+            st = h.stats()
+            assert np.array_equal(m_t.cpu().numpy(), r.mask), (shape, K)
+            assert np.array_equal(s_t.cpu().numpy(), r.support), (shape, K)
+            assert st.rounds == r.rounds and st.triangles_per_round == r.triangles_per_round
         h.close()
 
 
@@ -477,7 +507,11 @@ def test_full_size_against_oracle_digests(kt, name):
         g = gg.workload(name, seed)
         assert graph_digest(g) == cs[0]["graph_sha256"], "generator output changed"
         h = kt.load(torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col).cuda())
-        for c in cs:
+        # the default CTA shape of the support kernel for every case, and the
+        # other shape for the first case of each graph
+        for shape, c in [(None, c) for c in cs] + [(0, cs[0])]:
+            if shape is not None:
+                h.set_support_shape(shape)
             m_t, s_t = h.run(c["K"])
             torch.cuda.synchronize()
             st = h.stats()
