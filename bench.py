@@ -352,13 +352,15 @@ def measure_workload(kt, gg, name, K, steps, flush):
                            "rounds": st.rounds, "support_steps": st.support_launches}}
 
 
-def measure_batched(kt, gg, count, m_hi, seed=0):
+def measure_batched(kt, gg, count, m_hi, seed=0, autotune=True):
     """Batched graphs/s against the plain path on the batching workload
     (graphgen.batch_config: sizes log-uniform in [1e3, m_hi] edges, half G(n,m)
     with degree 8..64, half R-MAT scale 10..17, K uniform in 3..12).  Plain:
     every graph preloaded into its own handle, then one ktruss_run per graph.
     Batched: the block-diagonal batch preloaded into one handle, then one
-    ktruss_run_batch.  Both timed with CUDA events, graphs resident in HBM."""
+    ktruss_run_batch.  Both timed with CUDA events, graphs resident in HBM.
+    With autotune, ktruss_autotune picks the settings on the batch first and
+    both arms run with them."""
     import torch
     progress(f"batched: generating {count} graphs, m up to {m_hi:g}")
     batch = gg.batch_config(count, seed=seed, m_lo=1e3, m_hi=m_hi)
@@ -367,9 +369,29 @@ def measure_batched(kt, gg, count, m_hi, seed=0):
     edges = sum(g.m for g in graphs)
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
+    vo, rp, col, eo = kt.concat_graphs(graphs)
+    tune = None
+    if autotune:
+        # the library's autotuner picks the support kernel's CTA shape, the
+        # merge/probe threshold, the per-edge/balanced threshold and the
+        # update rule on the batch; both arms then run with those settings
+        progress("batched: autotuning on the batch")
+        hb = kt.load_batch(vertex_offsets=vo, row_ptr=torch.from_numpy(rp).to(dev),
+                           col=torch.from_numpy(col).to(dev))
+        tune = hb.autotune(Ks, reps=1)
+        hb.close()
+
+    def apply(h):
+        if tune is not None:
+            h.set_support_shape(tune["support_shape"])
+            h.set_option(kt.OPT_LIGHT_MERGE, tune["light_merge"])
+            h.set_option(kt.OPT_SMALL_EDGES, tune["small_edges"])
+            h.set_update(tune["update_mode"])
+        return h
+
     progress(f"batched: {edges} edges generated; loading plain handles")
     # plain
-    handles = [kt.load(torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col).to(dev))
+    handles = [apply(kt.load(torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col).to(dev)))
                for g in graphs]
     outs = [(torch.empty(max(g.m, 1), dtype=torch.uint8, device=dev)[:g.m],
              torch.empty(max(g.m, 1), dtype=torch.int32, device=dev)[:g.m]) for g in graphs]
@@ -389,9 +411,8 @@ def measure_batched(kt, gg, count, m_hi, seed=0):
         h.close()
     progress(f"batched: plain {plain_ms:.1f} ms; loading the batch")
     # batched
-    vo, rp, col, eo = kt.concat_graphs(graphs)
-    hb = kt.load_batch(vertex_offsets=vo, row_ptr=torch.from_numpy(rp).to(dev),
-                       col=torch.from_numpy(col).to(dev))
+    hb = apply(kt.load_batch(vertex_offsets=vo, row_ptr=torch.from_numpy(rp).to(dev),
+                             col=torch.from_numpy(col).to(dev)))
     mb = torch.empty(max(int(eo[-1]), 1), dtype=torch.uint8, device=dev)[:int(eo[-1])]
     sb = torch.empty(max(int(eo[-1]), 1), dtype=torch.int32, device=dev)[:int(eo[-1])]
     hb.run_batch(Ks, out=(mb, sb))
@@ -409,7 +430,10 @@ def measure_batched(kt, gg, count, m_hi, seed=0):
             "plain_graphs_per_s": round(count / (plain_ms / 1e3), 1),
             "speedup": round(plain_ms / batch_ms, 2), "batch_ms": round(batch_ms, 3),
             "plain_ms": round(plain_ms, 3), "batch_rounds": int(brounds),
-            "max_graph_rounds": int(max(rounds)) if len(rounds) else 0}
+            "max_graph_rounds": int(max(rounds)) if len(rounds) else 0,
+            "autotuned": ({k: tune[k] for k in ("support_shape", "light_merge", "small_edges",
+                                                  "update_mode", "trials")}
+                          if tune is not None else None)}
 
 
 def measure_serving(kt, gg, count, m_hi, seed=0):
@@ -717,10 +741,15 @@ def main():
         for key in ("l2_hit_rate", "warp_exec_efficiency", "warps_active", "traffic_note"):
             if key in rec:
                 roofline[key] = rec[key]
-        # what limits the kernel: the busiest of DRAM, L2 and SM issue
-        cand = {"hbm": roofline["dram_frac"], "l2": roofline["l2_frac"] or 0.0,
-                "sm_issue": roofline["sm_issue_active"] or 0.0}
+        # what limits the kernel: the busiest of DRAM, L2 and SM issue among
+        # the counters the record holds
+        cand = {"hbm": roofline["dram_frac"], "l2": roofline["l2_frac"],
+                "sm_issue": roofline["sm_issue_active"]}
+        cand = {k: v for k, v in cand.items() if v is not None}
         roofline["bound"] = max(cand, key=cand.get)
+        missing = [k for k in ("l2_frac", "sm_issue_active") if roofline.get(k) is None]
+        if missing:
+            roofline["bound_note"] = "not in the ncu record of this workload: " + ", ".join(missing)
         roofline["ncu_command"] = rec.get("command")
     else:
         roofline["traffic_record"] = ("stale: the kernel changed since the committed ncu capture"
