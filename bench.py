@@ -546,6 +546,9 @@ def main():
     ap.add_argument("--kernel", default="auto", choices=["auto", "balanced", "edge", "coarse"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-kmax", action="store_true", help="skip the K_max sweep timing")
+    ap.add_argument("--no-reorder", action="store_true",
+                    help="run from the loaded vertex numbering instead of the degree-ordered "
+                         "relabel the library makes at load (KTRUSS_OPT_REORDER)")
     ap.add_argument("--no-rmat20", action="store_true",
                     help="skip the extra R-MAT-20 measurement (value and K_max sweep)")
     ap.add_argument("--batch-graphs", type=int, default=4096,
@@ -591,12 +594,22 @@ def main():
     dev = torch.device("cuda", local)
     rp_d = torch.from_numpy(g.row_ptr).to(dev)
     col_d = torch.from_numpy(g.col).to(dev)
-    progress("counting the support step's work on the host")
-    work = support_work(g.row_ptr, g.col)
+    # the library runs from the degree-ordered relabel it makes at load
+    # (KTRUSS_OPT_REORDER, default on): count the support step's work on the
+    # same CSR, which the generators' relabel of the same edges reproduces
+    if args.no_reorder:
+        progress("counting the support step's work on the host")
+        work = support_work(g.row_ptr, g.col)
+    else:
+        progress("relabelling by degree on the host and counting the support step's work")
+        gr = gg.from_edges(g.n, g.edges(), relabel=True)
+        work = support_work(gr.row_ptr, gr.col)
+        del gr
     h = kt.load(rp_d, col_d)
     h.set_kernel({"balanced": kt.KERNEL_BALANCED, "edge": kt.KERNEL_EDGE,
                   "coarse": kt.KERNEL_COARSE, "auto": kt.KERNEL_AUTO}[args.kernel])
     h.set_update(UPDATE_MODES[args.update])
+    h.set_reorder(not args.no_reorder)
     mask = torch.empty(m, dtype=torch.uint8, device=dev)
     sup = torch.empty(m, dtype=torch.int32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
@@ -711,7 +724,7 @@ def main():
     survey_b = algorithmic_bytes(n, m, work["W"], tri1)
     design_b = design_bytes(work, tri1)
     achieved = design_b / (sup_avg_ms / 1000.0) / 1e9 if sup_avg_ms > 0 else None
-    rec, fresh = traffic_record(args.workload, args.K)
+    rec, fresh = traffic_record(args.workload + ("" if args.no_reorder else " reordered"), args.K)
     roofline = {
         "bound": None, "roof": "hbm",
         "achieved": round(achieved, 1) if achieved else None, "peak": peak,
@@ -760,6 +773,7 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC[args.workload] + f", K={args.K}", "K": args.K,
+                   "reorder": not args.no_reorder,
                    "n": n, "m": m, "rounds": st.rounds, "kernel": args.kernel,
                    "update": args.update, "support_steps": st.support_launches,
                    "parallelism": f"replicas{world}", "l2": "flushed between steps (512 MiB write)"},

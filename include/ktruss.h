@@ -88,6 +88,12 @@ extern "C" {
                                        slots (32 warps resident); 1 (default) = 512 threads,
                                        three CTAs per SM, stages of 2048 slots (48 warps);
                                        results identical */
+#define KTRUSS_OPT_REORDER 8        /* 1 (default): runs of a single-graph handle start from
+                                       its vertices renumbered by ascending degree (ties by
+                                       old id), made once at load on the device (graph
+                                       rebalancing by sorting, the paper's future work,
+                                       Sec. V); outputs stay in input edge order and are
+                                       identical; 0: runs use the loaded numbering */
 #define KTRUSS_OPT_DEVICE_LOOP 6    /* 1 (default): rounds whose supports come from the
                                        decremental update run in a device-driven loop (one
                                        CUDA graph launch, conditional nodes, no host

@@ -30,7 +30,7 @@ HOST, DEVICE = 0, 1
 KERNEL_BALANCED, KERNEL_EDGE, KERNEL_COARSE, KERNEL_AUTO = 0, 1, 2, 3
 UPDATE_NEVER, UPDATE_ALWAYS, UPDATE_AUTO = 0, 1, 2
 OPT_SUPPORT_KERNEL, OPT_TIMING, OPT_UPDATE, OPT_LIGHT_MERGE, OPT_SMALL_EDGES = 1, 2, 3, 4, 5
-OPT_DEVICE_LOOP, OPT_SUPPORT_SHAPE = 6, 7
+OPT_DEVICE_LOOP, OPT_SUPPORT_SHAPE, OPT_REORDER = 6, 7, 8
 
 _lib = None
 
@@ -248,6 +248,12 @@ class Graph:
         stages, 1 (default) = 512-thread CTAs, three per SM, 2048-slot
         stages."""
         self.set_option(OPT_SUPPORT_SHAPE, shape)
+
+    def set_reorder(self, on: bool):
+        """KTRUSS_OPT_REORDER: runs start from the vertices renumbered by
+        ascending degree at load (True, default for single graphs) or from the
+        loaded numbering; outputs are in input edge order either way."""
+        self.set_option(OPT_REORDER, 1 if on else 0)
 
     def set_device_loop(self, on: bool):
         """KTRUSS_OPT_DEVICE_LOOP: rounds whose supports come from the update

@@ -13,6 +13,7 @@
 //        written here), continue while any edge is live.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <mutex>
@@ -135,6 +136,10 @@ struct ktruss_graph {
     int device = 0;
     // immutable loaded graph
     int32_t *rp0 = nullptr, *col0 = nullptr;
+    // the same graph with vertices numbered by ascending degree (single-graph
+    // handles): row pointers, columns, and the input slot of every slot
+    int32_t *rpR = nullptr, *colR = nullptr, *eidR = nullptr;
+    int reorder = 1;  // KTRUSS_OPT_REORDER: runs start from the relabelled graph
     // double-buffered live graph
     int32_t *rp[2] = {nullptr, nullptr}, *col[2] = {nullptr, nullptr}, *eid[2] = {nullptr, nullptr};
     int32_t *S = nullptr, *S2 = nullptr, *pos = nullptr;
@@ -375,6 +380,14 @@ float elapsed(cudaEvent_t a, cudaEvent_t b) {
     return ms;
 }
 
+// The graph a run starts from: the degree-ordered relabel of the loaded graph
+// (outputs through its input-slot map) when the handle has one and
+// KTRUSS_OPT_REORDER is on, else the loaded graph itself.
+kt::Live base_graph(const ktruss_graph *g) {
+    if (g->reorder && g->rpR) return kt::Live{g->rpR, g->colR, g->eidR, g->n, int32_t(g->m)};
+    return kt::Live{g->rp0, g->col0, nullptr, g->n, int32_t(g->m)};
+}
+
 // Launches the handle's device loop (built on first use) from control block
 // c0 on stream s, waits for it, and returns the final control block in *c1
 // and the round records it wrote in *recs.  seed, when given, is copied to
@@ -513,7 +526,13 @@ static int load_impl(ktruss_graph **out, int32_t n, int64_t m, const int32_t *ro
              A((void **)&g->listed_g, gb);
         g->G = G;
     }
-    if (ok) ok = A(&g->bs.base, kt::balanced_scratch_bytes(n, m));
+    if (ok && G == 0)
+        ok = A((void **)&g->rpR, rpb) && A((void **)&g->colR, eb) && A((void **)&g->eidR, eb);
+    if (ok) {
+        size_t sb = kt::balanced_scratch_bytes(n, m);
+        if (G == 0) sb = std::max(sb, kt::reorder_scratch_bytes(n, m));
+        ok = A(&g->bs.base, sb);
+    }
     if (ok) {
         const cudaError_t ce = al.commit();
         if (ce != cudaSuccess) {
@@ -557,6 +576,17 @@ static int load_impl(ktruss_graph **out, int32_t n, int64_t m, const int32_t *ro
     if (g->cnt_host->error != 0) {
         release(g);
         return KTRUSS_EINVAL;
+    }
+    if (G == 0) {
+        // the degree-ordered relabel (the balanced scratch is idle until the
+        // first run and serves as the sort's working memory)
+        e = kt::launch_reorder(g->rp0, g->col0, n, m, g->bs.base, g->rpR, g->colR, g->eidR, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            rc = map_cuda(e);
+            release(g);
+            return rc;
+        }
     }
     *out = g;
     return KTRUSS_OK;
@@ -618,7 +648,7 @@ int ktruss_run_batch(ktruss_graph *g, const int32_t *K, uint8_t *mask_out, int32
     const kt::UpdateScratch us = kt::update_scratch(&g->bs);
     const Trace trace("run_batch");
     int launches = 0, support_launches = 0, rounds = 0;
-    kt::Live cur{g->rp0, g->col0, nullptr, n, m};
+    kt::Live cur = base_graph(g);
     int buf = 0;
     int32_t *S = g->S, *S_next = g->S2;
     // Each graph takes its own choice between the update and a support step
@@ -754,6 +784,10 @@ int ktruss_set_option(ktruss_graph *g, int32_t key, int64_t value) {
             if (value != 0 && value != 1) return KTRUSS_EINVAL;
             g->bs.shape = int32_t(value);
             return KTRUSS_OK;
+        case KTRUSS_OPT_REORDER:
+            if (value != 0 && value != 1) return KTRUSS_EINVAL;
+            g->reorder = int(value);
+            return KTRUSS_OK;
         case KTRUSS_OPT_DEVICE_LOOP:
             if (value != 0 && value != 1) return KTRUSS_EINVAL;
             g->device_loop = int(value);
@@ -788,7 +822,7 @@ int ktruss_run(ktruss_graph *g, int32_t K, uint8_t *mask_out, int32_t *support_o
     const bool track = g->update_mode != KTRUSS_UPDATE_NEVER;
     const kt::UpdateScratch us = kt::update_scratch(&g->bs);
     const Trace trace("run");
-    kt::Live cur{g->rp0, g->col0, nullptr, n, m};
+    kt::Live cur = base_graph(g);
     // The next compaction writes buffer buf; the current graph's supports
     // are in Sb[buf ^ 1] (the loaded graph counts as buffer 1), so that a
     // graph in buffer p always has its supports in Sb[p].
@@ -981,7 +1015,7 @@ int ktruss_decompose(ktruss_graph *g, int32_t *trussness_out, int32_t *kmax_out,
     const kt::UpdateScratch us = kt::update_scratch(&g->bs);
     const Trace trace("decompose");
     int launches = 0, support_launches = 0, rounds = 0;
-    kt::Live cur{g->rp0, g->col0, nullptr, n, m};
+    kt::Live cur = base_graph(g);
     // buffers and supports as in ktruss_run: the graph in buffer p has its
     // supports in Sb[p]; the next compaction writes buffer buf
     int buf = 0;

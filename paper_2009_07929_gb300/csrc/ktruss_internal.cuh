@@ -307,6 +307,18 @@ void loop_graph_destroy(LoopGraph *lg);
 // st->ldeg = lower degree of every vertex in the live graph g (all its edges).
 cudaError_t launch_lower_degree(const Live &g, UpdateState *st, cudaStream_t s, int *launches);
 
+// ---- degree-ordered relabel (reorder.cu) -----------------------------------
+// Bytes of working memory launch_reorder needs for a graph of n vertices and
+// m edges.
+size_t reorder_scratch_bytes(int32_t n, int64_t m);
+// Numbers the vertices of the upper-triangular CSR (rp, col) by ascending
+// degree (ties by old id) and writes the relabelled strictly upper-triangular
+// CSR (rp_out[n+1], col_out[m], columns sorted) and, per slot, the input slot
+// of its edge (eid_out[m]).  scratch: reorder_scratch_bytes(n, m) bytes.
+cudaError_t launch_reorder(const int32_t *rp, const int32_t *col, int32_t n, int64_t m,
+                           void *scratch, int32_t *rp_out, int32_t *col_out, int32_t *eid_out,
+                           cudaStream_t s);
+
 // ---- batches (batch.cu) -----------------------------------------------------
 // gid[v] = graph of vertex v for vertex offsets vo[G+1].
 cudaError_t launch_graph_of_vertex(const int32_t *vo, int32_t G, int32_t n, int32_t *gid,

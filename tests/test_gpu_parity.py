@@ -525,20 +525,21 @@ def test_full_size_against_oracle_digests(kt, name):
         h.close()
 
 
-@pytest.mark.parametrize("name", ["rmat20", "rmat20r"])
+@pytest.mark.parametrize("name", ["rmat20", "rmat20r", "rmat23c"])
 def test_full_size_decomposition_against_oracle(kt, name):
     """ktruss_decompose (K = 3, 4, ... up to K_max, each K from the previous
-    truss) of the full R-MAT-20 graph, original ids and degree-relabelled,
-    against the oracle's truss decomposition by its second, independent
-    algorithm (sequential peeling; stored by tests/golden/make_golden.py):
-    every edge's trussness, hence the K-truss for every K at once."""
+    truss) of the full R-MAT-20 graph, original ids and degree-relabelled, and
+    of R-MAT-23 with planted cliques, against the oracle's truss decomposition
+    by its second, independent algorithm (sequential peeling; stored by
+    tests/golden/make_golden.py): every edge's trussness, hence the K-truss
+    for every K at once."""
     p = os.path.join(GOLDEN, f"{name}_trussness.json")
     if not os.path.exists(p):
         pytest.skip(f"no stored oracle decomposition for {name}")
     with open(p) as f:
         c = json.load(f)
     import torch
-    g = gg.workload(name, c["seed"])
+    g = gg.cached_workload(name, c["seed"])
     assert graph_digest(g) == c["graph_sha256"], "generator output changed"
     h = kt.load(torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col).cuda())
     tr_t, kmax = h.decompose()
@@ -564,6 +565,15 @@ def test_rmat23_cliques_k3_sampled_and_kmax_sweep(kt):
     tr_t, kmax_dec = h.decompose()
     torch.cuda.synchronize()
     tr = tr_t.cpu().numpy()
+    # when the oracle's decomposition of this graph is stored, the trussness
+    # every rung below is checked against is the oracle's, element by element
+    p = os.path.join(GOLDEN, "rmat23c_trussness.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            dec = json.load(f)
+        assert dec["graph_sha256"] == graph_digest(g)
+        assert sha(np.ascontiguousarray(tr, dtype="<i4")) == dec["trussness_sha256"]
+        assert kmax_dec == dec["kmax"]
     rng = np.random.default_rng(0)
     m_t, s_t = h.run(3)
     torch.cuda.synchronize()
@@ -606,14 +616,55 @@ def test_rmat23_cliques_k3_sampled_and_kmax_sweep(kt):
 def test_host_work_count_equals_library_merge_work(kt):
     """The benchmark's host count of the merge work W (sum over edges of the
     tail length plus the row-kappa length, from the CSR alone) equals the merge
-    work the library reports for the first support step."""
+    work the library reports for the first support step: on the loaded
+    numbering with KTRUSS_OPT_REORDER off, and on the degree-ordered relabel
+    (the generators' relabel of the same edges) with it on."""
     import sys
+    import torch
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     import bench
     for g in (gg.rmat(14, 16, seed=0), gg.rmat(12, 16, seed=1, relabel=True),
-              gg.workload("er2000", 0)):
-        _, _, st = gpu_run(kt, g, 3, kernel=0)
-        assert st.merge_work_per_round[0] == bench.support_work(g.row_ptr, g.col)["W"]
+              gg.workload("er2000", 0), gg.book(50)):
+        r = gg.from_edges(g.n, g.edges(), relabel=True)
+        for reorder, ref in ((False, g), (True, r)):
+            h = kt.load(torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col).cuda())
+            h.set_kernel(0)
+            h.set_reorder(reorder)
+            h.run(3)
+            torch.cuda.synchronize()
+            st = h.stats()
+            h.close()
+            assert st.merge_work_per_round[0] == bench.support_work(ref.row_ptr, ref.col)["W"]
+
+
+@pytest.mark.parametrize("kernel", [0, 1, 3])
+def test_reorder_on_and_off_match_oracle(kt, kernel):
+    """Runs from the degree-ordered relabel made at load (default) and from
+    the loaded numbering give the oracle's masks, supports and per-round
+    statistics in input edge order."""
+    import torch
+    cases = [gg.rmat(14, 16, 2), gg.rmat(12, 8, seed=4, n_cliques=6, clique_lo=10, clique_hi=30),
+             gg.workload("er2000", 5), gg.book(300), gg.star(40), gg.complete(20), gg.empty(9),
+             gg.triangle_strip(50), gg.from_edges(2, [(0, 1)])]
+    for g in cases:
+        for K in (3, 4, 7):
+            r = oracle.ktruss(g.row_ptr, g.col, K)
+            for reorder in (True, False):
+                h = kt.load(torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col).cuda())
+                h.set_kernel(kernel)
+                h.set_reorder(reorder)
+                m_t, s_t = h.run(K)
+                torch.cuda.synchronize()
+                st = h.stats()
+                tr, kmax = h.decompose()
+                torch.cuda.synchronize()
+                h.close()
+                where = (K, reorder, kernel)
+                assert np.array_equal(m_t.cpu().numpy(), r.mask), where
+                assert np.array_equal(s_t.cpu().numpy(), r.support), where
+                assert st.rounds == r.rounds and st.removed_per_round == r.removed_per_round
+                assert st.triangles_per_round == r.triangles_per_round, where
+                assert np.array_equal(tr.cpu().numpy(), oracle.truss_decomposition(g.row_ptr, g.col))
 
 
 # ------------------------------------------------ device-driven round loop

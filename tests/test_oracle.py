@@ -372,12 +372,13 @@ def test_tail_start_reading():
                 assert a.rounds == b.rounds
 
 
-@pytest.mark.parametrize("name", ["rmat20", "rmat20r"])
+@pytest.mark.parametrize("name", ["rmat20", "rmat20r", "rmat23c"])
 def test_decomposition_agrees_with_peeling_on_rmat20(name):
-    """At full R-MAT-20 size the oracle's two algorithms agree: the stored
-    Alg. 1 results (K = 3, 4, 8, 16) keep exactly the edges whose trussness,
-    from the stored sequential-peeling decomposition, is at least K; both
-    were taken on the same graph."""
+    """At full size (R-MAT-20, original ids and relabelled; R-MAT-23 with
+    planted cliques) the oracle's two algorithms agree: the stored Alg. 1
+    results (every stored K) keep exactly the edges whose trussness, from the
+    stored sequential-peeling decomposition, is at least K; both were taken on
+    the same graph."""
     import json
     import os
     here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
