@@ -88,12 +88,13 @@ extern "C" {
                                        slots (32 warps resident); 1 (default) = 512 threads,
                                        three CTAs per SM, stages of 2048 slots (48 warps);
                                        results identical */
-#define KTRUSS_OPT_REORDER 8        /* 1 (default): runs of a single-graph handle start from
-                                       its vertices renumbered by ascending degree (ties by
-                                       old id), made once at load on the device (graph
-                                       rebalancing by sorting, the paper's future work,
-                                       Sec. V); outputs stay in input edge order and are
-                                       identical; 0: runs use the loaded numbering */
+#define KTRUSS_OPT_REORDER 8        /* 1 (default): runs start from the handle's vertices
+                                       renumbered by ascending degree (ties by old id; in a
+                                       batch within each graph), made once at load on the
+                                       device (graph rebalancing by sorting, the paper's
+                                       future work, Sec. V); outputs stay in input edge
+                                       order and are identical; 0: runs use the loaded
+                                       numbering */
 #define KTRUSS_OPT_DEVICE_LOOP 6    /* 1 (default): rounds whose supports come from the
                                        decremental update run in a device-driven loop (one
                                        CUDA graph launch, conditional nodes, no host
@@ -267,7 +268,10 @@ int ktruss_server_status(const ktruss_server *srv, int32_t *queued, int32_t *act
  * CSR that skips every other request) when its removed edges that lie in
  * triangles exceed a quarter of its surviving edges and either number at
  * least 65536 or some other request is recomputed anyway.  Results do not
- * depend on it.  KTRUSS_EINVAL for another key or value. */
+ * depend on it.  Also KTRUSS_OPT_REORDER (1, default: each request's vertices
+ * are renumbered by ascending degree when it is admitted, on the device,
+ * working in the server's own scratch; 0: appended in their own numbering;
+ * results identical).  KTRUSS_EINVAL for another key or value. */
 int ktruss_server_set_option(ktruss_server *srv, int32_t key, int64_t value);
 
 /* Releases the server and every buffer it holds (NULL is a no-op). */

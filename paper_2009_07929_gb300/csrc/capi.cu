@@ -138,7 +138,7 @@ struct ktruss_graph {
     int32_t *rp0 = nullptr, *col0 = nullptr;
     // the same graph with vertices numbered by ascending degree (single-graph
     // handles): row pointers, columns, and the input slot of every slot
-    int32_t *rpR = nullptr, *colR = nullptr, *eidR = nullptr;
+    int32_t *rpR = nullptr, *colR = nullptr, *eidR = nullptr;  // (per graph in batches)
     int reorder = 1;  // KTRUSS_OPT_REORDER: runs start from the relabelled graph
     // double-buffered live graph
     int32_t *rp[2] = {nullptr, nullptr}, *col[2] = {nullptr, nullptr}, *eid[2] = {nullptr, nullptr};
@@ -526,11 +526,10 @@ static int load_impl(ktruss_graph **out, int32_t n, int64_t m, const int32_t *ro
              A((void **)&g->listed_g, gb);
         g->G = G;
     }
-    if (ok && G == 0)
-        ok = A((void **)&g->rpR, rpb) && A((void **)&g->colR, eb) && A((void **)&g->eidR, eb);
+    if (ok) ok = A((void **)&g->rpR, rpb) && A((void **)&g->colR, eb) && A((void **)&g->eidR, eb);
     if (ok) {
-        size_t sb = kt::balanced_scratch_bytes(n, m);
-        if (G == 0) sb = std::max(sb, kt::reorder_scratch_bytes(n, m));
+        const size_t sb =
+            std::max(kt::balanced_scratch_bytes(n, m), kt::reorder_scratch_bytes(n, m));
         ok = A(&g->bs.base, sb);
     }
     if (ok) {
@@ -577,10 +576,12 @@ static int load_impl(ktruss_graph **out, int32_t n, int64_t m, const int32_t *ro
         release(g);
         return KTRUSS_EINVAL;
     }
-    if (G == 0) {
-        // the degree-ordered relabel (the balanced scratch is idle until the
-        // first run and serves as the sort's working memory)
-        e = kt::launch_reorder(g->rp0, g->col0, n, m, g->bs.base, g->rpR, g->colR, g->eidR, s);
+    {
+        // the degree-ordered relabel, per graph for batches (the balanced
+        // scratch is idle until the first run and serves as the sorts'
+        // working memory)
+        e = kt::launch_reorder(g->rp0, g->col0, n, m, g->bs.base, g->rpR, g->colR, g->eidR, s,
+                               G > 0 ? g->gid : nullptr, G);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) {
             rc = map_cuda(e);

@@ -169,6 +169,7 @@ void balanced_side_destroy(BalancedScratch *bs);
 // Bytes of device scratch BalancedScratch needs for a graph of n vertices and
 // m edges (used for allocation at load time).
 size_t balanced_scratch_bytes(int32_t n, int64_t m);
+// (also large enough for launch_reorder of any graph within n vertices and m edges)
 cudaError_t balanced_scratch_alloc(BalancedScratch *bs, int32_t n, int64_t m);
 void balanced_scratch_free(BalancedScratch *bs);
 
@@ -314,10 +315,13 @@ size_t reorder_scratch_bytes(int32_t n, int64_t m);
 // Numbers the vertices of the upper-triangular CSR (rp, col) by ascending
 // degree (ties by old id) and writes the relabelled strictly upper-triangular
 // CSR (rp_out[n+1], col_out[m], columns sorted) and, per slot, the input slot
-// of its edge (eid_out[m]).  scratch: reorder_scratch_bytes(n, m) bytes.
+// of its edge (eid_out[m]).  With gid (batches of num_graphs graphs with
+// contiguous vertex ranges, gid[v] = graph of v) vertices are ordered by
+// graph first, so every graph keeps its range.  scratch:
+// reorder_scratch_bytes(n, m) bytes.
 cudaError_t launch_reorder(const int32_t *rp, const int32_t *col, int32_t n, int64_t m,
                            void *scratch, int32_t *rp_out, int32_t *col_out, int32_t *eid_out,
-                           cudaStream_t s);
+                           cudaStream_t s, const int32_t *gid = nullptr, int32_t num_graphs = 0);
 
 // ---- batches (batch.cu) -----------------------------------------------------
 // gid[v] = graph of vertex v for vertex offsets vo[G+1].
@@ -358,10 +362,12 @@ cudaError_t launch_batch_keep(const Live &g, const int32_t *S, const int32_t *gi
                               int32_t *listed_g = nullptr);
 
 // ---- request server (server_kernels.cu) --------------------------------------
-// Appends a request's device CSR at vertex base nb / edge base mb of the live CSR.
+// Appends a request's device CSR at vertex base nb / edge base mb of the live CSR
+// (emap, when given: the request-local input edge of each slot).
 cudaError_t launch_server_append(const int32_t *rp_in, const int32_t *col_in, int32_t n, int32_t m,
                                  int32_t nb, int32_t mb, int32_t slot, int32_t *rp, int32_t *col,
-                                 int32_t *eid, int32_t *gid, cudaStream_t s);
+                                 int32_t *eid, int32_t *gid, cudaStream_t s,
+                                 const int32_t *emap = nullptr);
 // Keep flags and per-slot kept / removed flags (= launch_batch_keep); removed edges with
 // S > 0 appended to list when given (count in *list_count, zero on entry) and
 // counted per slot in listed_s when given.

@@ -13,7 +13,8 @@
 // On the device, once per load:
 //   1. deg[v] = number of edges on v;
 //   2. vertices sorted stably by degree (radix sort of (deg, v)); rank r of v
-//      in that order is its new id (ties keep the old order);
+//      in that order is its new id (ties keep the old order); in a batch the
+//      sort key is (graph, degree), so that every graph keeps its vertex range;
 //   3. every edge (u, v) at input slot e becomes (min, max) of its new ids,
 //      keyed (row << 32 | col), sorted stably by key (radix sort), carrying e;
 //   4. row pointers from the sorted rows; the carried slots map every slot of
@@ -212,6 +213,15 @@ __global__ void degree_kernel(const int32_t *__restrict__ rp, const int32_t *__r
     for (int64_t e = t0; e < m; e += stride) atomicAdd(deg + col[e], 1u);
 }
 
+// Batches: key[v] = (graph of v) << 32 | degree of v, so that sorting keeps
+// every graph's vertices in its own contiguous range.
+__global__ void graph_key_kernel(const int32_t *__restrict__ gid, const uint32_t *__restrict__ deg,
+                                 int32_t n, uint64_t *__restrict__ key) {
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n; v += stride)
+        key[v] = (uint64_t(uint32_t(gid[v])) << 32) | deg[v];
+}
+
 __global__ void iota_kernel(int32_t *__restrict__ a, int64_t count) {
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < count; i += stride)
@@ -368,27 +378,30 @@ cudaError_t radix_sort(SortScratch &s, int64_t count, const int *shifts, int npa
 size_t reorder_scratch_bytes(int32_t n, int64_t m) {
     SortScratch s;
     const size_t a = sort_layout(nullptr, m, 8, int64_t(n) + 1, &s);
-    const size_t b = sort_layout(nullptr, n, 4, int64_t(n) + 1, &s);
-    return (a > b ? a : b) + align256((size_t(n) + 1) * 4) * 2;
+    const size_t b = sort_layout(nullptr, n, 8, int64_t(n) + 1, &s);
+    // degrees (n) beside the vertex sort, then new ids and row counts
+    return (a > b + align256(size_t(n) * 4) ? a : b + align256(size_t(n) * 4)) +
+           align256((size_t(n) + 1) * 4) * 2;
 }
 
 cudaError_t launch_reorder(const int32_t *rp, const int32_t *col, int32_t n, int64_t m,
                            void *scratch, int32_t *rp_out, int32_t *col_out, int32_t *eid_out,
-                           cudaStream_t st) {
+                           cudaStream_t st, const int32_t *gid, int32_t num_graphs) {
     if (n == 0) return cudaMemsetAsync(rp_out, 0, 4, st);
-    // two arrays of n + 1 ints at the end of the scratch: degrees / new ids
     SortScratch es, vs;
-    const size_t sort_bytes = [&] {
-        const size_t a = sort_layout(nullptr, m, 8, int64_t(n) + 1, &es);
-        const size_t b = sort_layout(nullptr, n, 4, int64_t(n) + 1, &vs);
-        return a > b ? a : b;
-    }();
+    const size_t a_bytes = sort_layout(nullptr, m, 8, int64_t(n) + 1, &es);
+    const size_t b_bytes = sort_layout(nullptr, n, 8, int64_t(n) + 1, &vs);
+    const size_t vb_bytes = b_bytes + align256(size_t(n) * 4);
+    const size_t sort_bytes = a_bytes > vb_bytes ? a_bytes : vb_bytes;
     char *base = static_cast<char *>(scratch);
+    // new ids and row counts after the sorts' memory; the degrees after the
+    // vertex sort's
     int32_t *newid = reinterpret_cast<int32_t *>(base + sort_bytes);
     int32_t *rowcnt = reinterpret_cast<int32_t *>(base + sort_bytes + align256((size_t(n) + 1) * 4));
-    // 1-2: degrees, vertices sorted by degree (stable: ties keep old ids)
-    sort_layout(base, n, 4, int64_t(n) + 1, &vs);
-    uint32_t *deg = static_cast<uint32_t *>(vs.keys[0]);
+    uint32_t *deg = reinterpret_cast<uint32_t *>(base + b_bytes);
+    // 1-2: degrees, vertices sorted by degree (batches: by graph, then
+    // degree), stably, so that ties keep their old order
+    sort_layout(base, n, gid ? 8 : 4, int64_t(n) + 1, &vs);
     cudaError_t e = cudaMemsetAsync(deg, 0, size_t(n) * 4, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(vs.mx, 0, 4, st);
     if (e != cudaSuccess) return e;
@@ -399,11 +412,20 @@ cudaError_t launch_reorder(const int32_t *rp, const int32_t *col, int32_t n, int
     e = cudaMemcpyAsync(&maxdeg, vs.mx, 4, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return e;
-    int shifts[8];
+    int shifts[16];
     int np = 0;
     for (int sh = 0; sh < bits_for(maxdeg); sh += 8) shifts[np++] = sh;
     int cur = 0;
-    e = radix_sort<uint32_t>(vs, n, shifts, np, &cur, st);
+    if (gid) {
+        graph_key_kernel<<<grid_for(n, 256), 256, 0, st>>>(gid, deg, n,
+                                                           static_cast<uint64_t *>(vs.keys[0]));
+        const int gb = bits_for(uint64_t(num_graphs > 0 ? num_graphs - 1 : 0));
+        for (int sh = 0; sh < gb; sh += 8) shifts[np++] = 32 + sh;
+        e = radix_sort<uint64_t>(vs, n, shifts, np, &cur, st);
+    } else {
+        e = cudaMemcpyAsync(vs.keys[0], deg, size_t(n) * 4, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = radix_sort<uint32_t>(vs, n, shifts, np, &cur, st);
+    }
     if (e != cudaSuccess) return e;
     rank_kernel<<<grid_for(n, 256), 256, 0, st>>>(vs.vals[cur], n, newid);
     // 3: edges keyed by (new row, new col), sorted, carrying the input slot

@@ -19,7 +19,7 @@ def kt():
     return kt
 
 
-def run_batch(kt, graphs, Ks, kernel=None, update=None):
+def run_batch(kt, graphs, Ks, kernel=None, update=None, reorder=None):
     import torch
     vo, rp, col, eo = kt.concat_graphs(graphs)
     h = kt.load_batch(vertex_offsets=vo, row_ptr=torch.from_numpy(rp).cuda(),
@@ -28,6 +28,8 @@ def run_batch(kt, graphs, Ks, kernel=None, update=None):
         h.set_kernel(kernel)
     if update is not None:
         h.set_update(update)
+    if reorder is not None:
+        h.set_reorder(reorder)
     mask, sup, rounds = h.run_batch(Ks)
     torch.cuda.synchronize()
     mask, sup = mask.cpu().numpy(), sup.cpu().numpy()
@@ -191,3 +193,19 @@ def test_full_batching_workload_against_oracle_digests(kt):
         assert digest_of_digests(sha(sup[a:b].tobytes())
                                  for a, b in zip(lo, hi)) == c["support_sha256"], update
     h.close()
+
+
+@pytest.mark.parametrize("reorder", [True, False])
+def test_batch_reorder_on_and_off(kt, reorder):
+    """A batch run from the per-graph degree-ordered relabel made at load
+    (default) and from the loaded numbering: every graph gets the oracle's
+    mask, supports and round count."""
+    gs, Ks = mixed_small_graphs()
+    gs = gs + [gg.rmat(13, 16, 7), gg.rmat(12, 16, 8, relabel=True)]
+    Ks = Ks + [5, 4]
+    mask, sup, rounds, eo, _ = run_batch(kt, gs, Ks, reorder=reorder)
+    for k, (g, K) in enumerate(zip(gs, Ks)):
+        r = oracle.ktruss(g.row_ptr, g.col, K)
+        assert np.array_equal(mask[eo[k]:eo[k + 1]], r.mask), k
+        assert np.array_equal(sup[eo[k]:eo[k + 1]], r.support), k
+        assert rounds[k] == r.rounds, k
