@@ -424,6 +424,12 @@ class Server:
         _check(lib().ktruss_server_set_option(self._h, OPT_UPDATE, mode),
                "ktruss_server_set_option")
 
+    def set_reorder(self, on: bool):
+        """KTRUSS_OPT_REORDER: requests relabelled by ascending degree at
+        admission (True, default) or appended in their own numbering."""
+        _check(lib().ktruss_server_set_option(self._h, OPT_REORDER, 1 if on else 0),
+               "ktruss_server_set_option")
+
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             lib().ktruss_server_free(self._h)

@@ -66,10 +66,14 @@ struct Slot {
     int32_t *dsup = nullptr;
     int32_t *din = nullptr;  // staged input: row_ptr then col
     size_t din_bytes = 0;
+    int32_t *dre = nullptr;  // degree-ordered relabel: row_ptr, col, input slot of each slot
+    size_t dre_bytes = 0;
 };
 
 // Device bytes of a request's staged input (row_ptr then col).
 size_t input_bytes(int32_t n, int64_t m) { return (size_t(n) + 1 + size_t(m)) * 4; }
+// Device bytes of a request's degree-ordered relabel (row_ptr, col, slot map).
+size_t relabel_bytes(int32_t n, int64_t m) { return (size_t(n) + 1 + 2 * size_t(m)) * 4; }
 
 constexpr int32_t kAutoSmallEdges = 1 << 17;
 
@@ -122,6 +126,7 @@ struct ktruss_server {
     bool any_valid = false;  // some live slot has upd_s = 1
     int32_t need_slots = 0;  // live slots with upd_s = 0
     int update_mode = KTRUSS_UPDATE_AUTO;
+    int reorder = 1;  // KTRUSS_OPT_REORDER: requests are relabelled by degree at admission
     int64_t next_ticket = 1;
     std::deque<Request> queue;
     std::vector<Slot> slot;
@@ -138,6 +143,7 @@ void server_release(ktruss_server *v) {
         if (sl.dmask) kt::cache_put(sl.dmask, size_t(sl.m));
         if (sl.dsup) kt::cache_put(sl.dsup, size_t(sl.m) * 4);
         if (sl.din) kt::cache_put(sl.din, sl.din_bytes);
+        if (sl.dre) kt::cache_put(sl.dre, sl.dre_bytes);
     }
     for (Request &r : v->queue)
         if (r.din) kt::cache_put(r.din, input_bytes(r.n, r.m));
@@ -306,6 +312,11 @@ void ktruss_server_free(ktruss_server *srv) { server_release(srv); }
 
 int ktruss_server_set_option(ktruss_server *srv, int32_t key, int64_t value) {
     if (!srv) return KTRUSS_EINVAL;
+    if (key == KTRUSS_OPT_REORDER) {
+        if (value != 0 && value != 1) return KTRUSS_EINVAL;
+        srv->reorder = int(value);
+        return KTRUSS_OK;
+    }
     if (key != KTRUSS_OPT_UPDATE) return KTRUSS_EINVAL;
     if (value != KTRUSS_UPDATE_NEVER && value != KTRUSS_UPDATE_ALWAYS &&
         value != KTRUSS_UPDATE_AUTO)
@@ -407,13 +418,16 @@ int ktruss_server_step(ktruss_server *srv, int32_t *num_done) {
         Slot &sl = srv->slot[size_t(sid)];
         {
             // take every buffer first, so that a failure leaves the request queued as it was
-            void *din = r.din, *dm = nullptr, *ds = nullptr;
+            void *din = r.din, *dm = nullptr, *ds = nullptr, *dre = nullptr;
+            const bool relabel = srv->reorder && r.m > 0;
             cudaError_t e = din ? cudaSuccess : kt::cache_get(input_bytes(r.n, r.m), &din);
             if (e == cudaSuccess) e = kt::cache_get(size_t(r.m), &dm);
             if (e == cudaSuccess && r.support_out) e = kt::cache_get(size_t(r.m) * 4, &ds);
+            if (e == cudaSuccess && relabel) e = kt::cache_get(relabel_bytes(r.n, r.m), &dre);
             if (e != cudaSuccess) {
                 cudaGetLastError();
                 if (dm) kt::cache_put(dm, size_t(r.m));
+                if (ds) kt::cache_put(ds, size_t(r.m) * 4);
                 if (din && !r.staged) kt::cache_put(din, input_bytes(r.n, r.m));
                 return map_err(e);
             }
@@ -421,6 +435,8 @@ int ktruss_server_step(ktruss_server *srv, int32_t *num_done) {
             sl.din_bytes = input_bytes(r.n, r.m);
             sl.dmask = static_cast<uint8_t *>(dm);
             sl.dsup = static_cast<int32_t *>(ds);
+            sl.dre = static_cast<int32_t *>(dre);
+            sl.dre_bytes = dre ? relabel_bytes(r.n, r.m) : 0;
             r.din = nullptr;
         }
         sl.used = true;
@@ -439,9 +455,20 @@ int ktruss_server_step(ktruss_server *srv, int32_t *num_done) {
                 SV_CK(cudaMemcpyAsync(dcol, r.col.get(), size_t(r.m) * 4, cudaMemcpyHostToDevice,
                                       s));
         }
+        // the request's vertices numbered by ascending degree (as a loaded
+        // graph's are), the balanced scratch serving as the sort's memory
+        // (it is idle during admission); slots map back to input edges
+        const int32_t *emap = nullptr;
+        if (sl.dre) {
+            int32_t *rpR = sl.dre, *colR = sl.dre + r.n + 1, *eidR = colR + r.m;
+            SV_CK(kt::launch_reorder(drp, dcol, r.n, r.m, srv->bs.base, rpR, colR, eidR, s));
+            drp = rpR;
+            dcol = colR;
+            emap = eidR;
+        }
         SV_CK(kt::launch_server_append(drp, dcol, r.n, int32_t(r.m), srv->n_live, srv->m_live, sid,
                                        srv->rp[srv->cur], srv->col[srv->cur], srv->eid[srv->cur],
-                                       srv->gid[srv->cur], s));
+                                       srv->gid[srv->cur], s, emap));
         ++launches;
         srv->ptr_host[2 * sid] = sl.dmask;
         srv->ptr_host[2 * sid + 1] = sl.dsup;
@@ -585,6 +612,7 @@ int ktruss_server_step(ktruss_server *srv, int32_t *num_done) {
             srv->done_rounds.push_back(srv->rounds_host[k]);
             ++finished;
             kt::cache_put(sl.din, sl.din_bytes);
+            if (sl.dre) kt::cache_put(sl.dre, sl.dre_bytes);
             kt::cache_put(sl.dmask, size_t(sl.m));
             if (sl.dsup) kt::cache_put(sl.dsup, size_t(sl.m) * 4);
             srv->used -= int64_t(sl.bytes);

@@ -19,10 +19,13 @@ constexpr int kWarpSpan = kCompactTile / kWarpsPerTile;
 
 // Appends a request's CSR (device copy of its input) at vertex base nb and
 // edge base mb of the live CSR.
+// emap (optional): request-local input edge of each slot of (rp_in, col_in)
+// (the request's degree-ordered relabel); else slot e is input edge e.
 __global__ void append_kernel(const int32_t *__restrict__ rp_in, const int32_t *__restrict__ col_in,
                               int32_t n, int32_t m, int32_t nb, int32_t mb, int32_t slot,
                               int32_t *__restrict__ rp, int32_t *__restrict__ col,
-                              int32_t *__restrict__ eid, int32_t *__restrict__ gid) {
+                              int32_t *__restrict__ eid, int32_t *__restrict__ gid,
+                              const int32_t *__restrict__ emap) {
     const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t v = t; v <= n; v += stride) {
@@ -31,7 +34,7 @@ __global__ void append_kernel(const int32_t *__restrict__ rp_in, const int32_t *
     }
     for (int64_t e = t; e < m; e += stride) {
         col[mb + e] = nb + col_in[e];
-        eid[mb + e] = int32_t(e);
+        eid[mb + e] = emap ? emap[e] : int32_t(e);
     }
 }
 
@@ -245,11 +248,13 @@ __global__ void server_decide_kernel(int32_t slots, const int32_t *__restrict__ 
 
 cudaError_t launch_server_append(const int32_t *rp_in, const int32_t *col_in, int32_t n, int32_t m,
                                  int32_t nb, int32_t mb, int32_t slot, int32_t *rp, int32_t *col,
-                                 int32_t *eid, int32_t *gid, cudaStream_t s) {
+                                 int32_t *eid, int32_t *gid, cudaStream_t s,
+                                 const int32_t *emap) {
     const int64_t work = int64_t(n > m ? n : m) + 1;
     int64_t blocks = (work + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
-    append_kernel<<<int(blocks), 256, 0, s>>>(rp_in, col_in, n, m, nb, mb, slot, rp, col, eid, gid);
+    append_kernel<<<int(blocks), 256, 0, s>>>(rp_in, col_in, n, m, nb, mb, slot, rp, col, eid, gid,
+                                               emap);
     return cudaGetLastError();
 }
 

@@ -683,7 +683,10 @@ size_t balanced_scratch_bytes(int32_t n, int64_t m) {
 
 cudaError_t balanced_scratch_alloc(BalancedScratch *bs, int32_t n, int64_t m) {
     void *p = nullptr;
-    cudaError_t e = cudaMalloc(&p, balanced_scratch_bytes(n, m));
+    // large enough to also serve as the degree-ordered relabel's working
+    // memory for any graph within the capacity (the server relabels requests)
+    const size_t a = balanced_scratch_bytes(n, m), b = reorder_scratch_bytes(n, m);
+    cudaError_t e = cudaMalloc(&p, a > b ? a : b);
     if (e != cudaSuccess) return e;
     bs->base = p;
     bs->cap_m = m;

@@ -208,3 +208,18 @@ def test_full_serving_workload_served_equals_solo(kt):
             assert sha(np.ascontiguousarray(mask, dtype=np.uint8)) == c["mask_sha256"], k
             assert sha(np.ascontiguousarray(sup, dtype="<i4")) == c["support_sha256"], k
     assert len(golden) == 0 or len(golden) >= 59
+
+
+@pytest.mark.parametrize("reorder", [True, False])
+def test_server_reorder_on_and_off(kt, reorder):
+    """Requests relabelled by degree at admission (default) and appended in
+    their own numbering give the oracle's results."""
+    reqs = requests_mixed()[:14]
+    srv = kt.Server(max_vertices=1 << 20, max_edges=1 << 22, max_requests=8)
+    srv.set_reorder(reorder)
+    _, _, results = kt.serve_poisson(srv, reqs, rate=None)
+    srv.close()
+    for k, ((g, K), (r, mask, sup)) in enumerate(zip(reqs, results)):
+        want = oracle.ktruss(g.row_ptr, g.col, K)
+        assert np.array_equal(mask, want.mask) and np.array_equal(sup, want.support), k
+        assert r == want.rounds, k
