@@ -323,7 +323,8 @@ typedef struct {
  * runs on it:
  * ktruss_run with K[0] when num_K == 1, or ktruss_run_batch with K[0..G) when
  * the handle is a batch of G graphs and num_K == G.  Candidates are tried one
- * option at a time (coordinate descent from the current settings), each run
+ * option at a time (coordinate descent from the current settings, a second
+ * pass over the options when the first changed any), each run
  * reps times (best time counts); the best settings are left set on the
  * handle and copied to *out (may be NULL).  Results of the runs are discarded
  * (device buffers owned by the handle).  The support kernel choice

@@ -1206,20 +1206,29 @@ int ktruss_autotune(ktruss_graph *g, const int32_t *K, int32_t num_K, int32_t re
                 {KTRUSS_OPT_LIGHT_MERGE, lights, 5, g->bs.light},
                 {KTRUSS_OPT_SMALL_EDGES, smalls, 4, g->small_edges},
                 {KTRUSS_OPT_UPDATE, updates, 3, g->update_mode}};
-    for (Axis &ax : axes) {
-        if (rc != KTRUSS_OK) break;
-        int64_t keep_val = ax.cur;
-        for (int i = 0; i < ax.count && rc == KTRUSS_OK; ++i) {
-            if (ax.vals[i] == ax.cur) continue;
-            ktruss_set_option(g, ax.key, ax.vals[i]);
-            float t = 0.f;
-            rc = measure(&t);
-            if (rc == KTRUSS_OK && t < best) {
-                best = t;
-                keep_val = ax.vals[i];
+    // coordinate descent: up to two passes over the axes, the second only
+    // when the first changed something (a later axis can move the best value
+    // of an earlier one)
+    for (int pass = 0; pass < 2 && rc == KTRUSS_OK; ++pass) {
+        bool changed = false;
+        for (Axis &ax : axes) {
+            if (rc != KTRUSS_OK) break;
+            int64_t keep_val = ax.cur;
+            for (int i = 0; i < ax.count && rc == KTRUSS_OK; ++i) {
+                if (ax.vals[i] == ax.cur) continue;
+                ktruss_set_option(g, ax.key, ax.vals[i]);
+                float t = 0.f;
+                rc = measure(&t);
+                if (rc == KTRUSS_OK && t < best) {
+                    best = t;
+                    keep_val = ax.vals[i];
+                }
             }
+            ktruss_set_option(g, ax.key, keep_val);
+            if (keep_val != ax.cur) changed = true;
+            ax.cur = keep_val;
         }
-        ktruss_set_option(g, ax.key, keep_val);
+        if (!changed) break;
     }
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
