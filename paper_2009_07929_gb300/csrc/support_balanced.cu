@@ -52,10 +52,6 @@ namespace {
 #endif
 constexpr int kStageRows = 256;         // staged rows per stage
 constexpr int kUnroll = KT_SUPPORT_UNROLL;  // 32-item windows in flight per warp
-#ifndef KT_SUPPORT_MIX_UNROLL
-#define KT_SUPPORT_MIX_UNROLL 2
-#endif
-constexpr int kMixUnroll = KT_SUPPORT_MIX_UNROLL;  // run-crossing windows in flight per warp
 #ifndef KT_SUPPORT_GRAIN
 #define KT_SUPPORT_GRAIN 0
 #endif

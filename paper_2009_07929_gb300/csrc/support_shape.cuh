@@ -116,116 +116,63 @@ __device__ __forceinline__ void build_runs(SupportSmem &sm, int32_t len, int32_t
     __syncthreads();
 }
 
-// Probes of the items [p, pe) of a batch's flat item space (p in run E).
-// Where the next 32 items lie inside one run, the run's parameters are
-// warp-uniform and a tight loop streams its windows (kUnroll loads in flight
-// per lane), counting the owner's hits in a register; a window that crosses
-// run boundaries maps each lane to its run with a bitmask of the run starts
-// inside the window.
+// Probes of the items [p, pe) of a batch's flat item space (p in run E).  The
+// warp walks the range in windows of 32 consecutive items, kUnroll windows
+// with their loads in flight at a time.  Each lane tracks the run of its own
+// item (runs are consecutive in item space, so a lane only moves forward,
+// crossing a run start when its item passes it) and keeps that run's probe
+// offset and region in registers, so a window costs the same whether it lies
+// inside one run or spans several.  A lane counts the hits of its current run
+// and adds them to the run's owner in shared memory when it moves to a run
+// with hits of its own, and at the end.
 __device__ __forceinline__ void probe_range(const SupportArgs &A, SupportSmem &sm, int32_t nruns,
                                             int32_t items, int32_t E, int32_t p, int32_t pe) {
     const int lane = threadIdx.x & 31;
-    while (p < pe) {
-        while (E + 1 < nruns && sm.b.rstart[E + 1] <= p) ++E;
-        const int32_t rend = min(pe, E + 1 < nruns ? sm.b.rstart[E + 1] : items);
-        if (rend - p >= 32) {
-            // ---- whole windows of run E: warp-uniform parameters
-            const int32_t nwin = (rend - p) >> 5;
-            const int32_t reg = sm.b.rreg[E];
-            const int32_t bb = reg & 0xffffff;
-            const int lb = reg >> 24;
-            const uint32_t bm = (1u << lb) - 1u;
-            const int sh = 32 - lb;
-            const int32_t *__restrict__ src = A.col + sm.b.rdel[E] + p + lane;
-            int32_t *__restrict__ dst = A.S + (src - A.col);
-            int32_t own = 0;
-            int32_t i = 0;
-            for (; i + kUnroll <= nwin; i += kUnroll) {
-                int32_t wv[kUnroll];
+    int32_t r = E, rnext = sm.b.rstart[E + 1];  // rstart[nruns] == items
+    int32_t del = sm.b.rdel[E], reg = sm.b.rreg[E];
+    int32_t orun = E, own = 0;
+    for (; p < pe; p += 32 * kUnroll) {
+        int32_t xv[kUnroll], gv[kUnroll], rv[kUnroll], wv[kUnroll];
 #pragma unroll
-                for (int u = 0; u < kUnroll; ++u) wv[u] = __ldg(src + 32 * (i + u));
-#pragma unroll
-                for (int u = 0; u < kUnroll; ++u) {
-                    const int32_t w = wv[u];
-                    const uint32_t fp4 = fingerprint(w) * 0x01010101u;
-                    uint32_t b = (uint32_t(w) * kHashMul) >> sh;
-                    for (;;) {
-                        const int32_t at = bb + int32_t(b);
-                        const uint32_t word = sm.fpw[at];
-                        int32_t q = -1;
-                        for (uint32_t mm = match_bytes(word, fp4); mm; mm &= mm - 1u) {
-                            const int32_t sl = sm.slots[4 * at + ((__ffs(mm) - 1) >> 3)];
-                            if (sm.vals[sl] == w) {
-                                q = sl;
-                                break;
-                            }
-                        }
-                        if (q >= 0) {
-                            atomicAdd(&sm.cnt[q], 1);
-                            atomicAdd(dst + 32 * (i + u), 1);
-                            ++own;
-                            break;
-                        }
-                        if ((word >> 24) == 0) break;
-                        b = (b + 1) & bm;
-                    }
+        for (int u = 0; u < kUnroll; ++u) {
+            const int32_t item = p + 32 * u + lane;
+            rv[u] = -1;
+            xv[u] = 0;
+            gv[u] = 0;
+            if (item < pe) {
+                if (rnext <= item) {
+                    do {
+                        ++r;
+                        rnext = sm.b.rstart[r + 1];
+                    } while (rnext <= item);
+                    del = sm.b.rdel[r];
+                    reg = sm.b.rreg[r];
                 }
+                rv[u] = r;
+                xv[u] = del + item;
+                gv[u] = reg;
             }
-            for (; i < nwin; ++i) {
-                const int32_t q = table_find(sm.fpw, sm.slots, sm.vals, bb, lb, __ldg(src + 32 * i));
-                if (q >= 0) {
-                    atomicAdd(&sm.cnt[q], 1);
-                    atomicAdd(dst + 32 * i, 1);
-                    ++own;
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) wv[u] = rv[u] >= 0 ? __ldg(A.col + xv[u]) : 0;
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            if (rv[u] < 0) continue;
+            const int32_t q = table_find(sm.fpw, sm.slots, sm.vals, gv[u] & 0xffffff, gv[u] >> 24,
+                                         wv[u]);
+            if (q >= 0) {
+                atomicAdd(&sm.cnt[q], 1);
+                atomicAdd(A.S + xv[u], 1);
+                if (rv[u] != orun) {
+                    if (own) atomicAdd(&sm.b.hit[sm.b.rseg[orun]], own);
+                    orun = rv[u];
+                    own = 0;
                 }
-            }
-            own = __reduce_add_sync(0xffffffffu, own);
-            if (lane == 0 && own) atomicAdd(&sm.b.hit[sm.b.rseg[E]], own);
-            p += nwin * 32;
-        } else {
-            // ---- windows crossing run boundaries: map lanes to runs with a
-            // bitmask of the run starts in each window; up to kMixUnroll such
-            // windows have their loads in flight together
-            int32_t x[kMixUnroll], rr[kMixUnroll], wv[kMixUnroll];
-            bool ok[kMixUnroll];
-#pragma unroll
-            for (int u = 0; u < kMixUnroll; ++u) ok[u] = false;
-#pragma unroll
-            for (int u = 0; u < kMixUnroll; ++u) {
-                if (u > 0) {
-                    if (p >= pe) break;
-                    while (E + 1 < nruns && sm.b.rstart[E + 1] <= p) ++E;
-                    if (!(E + 1 < nruns && sm.b.rstart[E + 1] < p + 32)) break;
-                }
-                const int32_t j = E + 1 + lane;
-                const int32_t s0 = j < nruns ? sm.b.rstart[j] : kIntMax;
-                const int32_t rel = s0 - p;
-                const uint32_t bits = __reduce_or_sync(0xffffffffu, rel < 32 ? (1u << rel) : 0u);
-                const int32_t r = E + __popc(bits & (0xffffffffu >> (31 - lane)));
-                const int32_t item = p + lane;
-                ok[u] = item < pe;
-                rr[u] = r;
-                x[u] = sm.b.rdel[r] + item;
-                E = __shfl_sync(0xffffffffu, r, 31);
-                p += 32;
-            }
-#pragma unroll
-            for (int u = 0; u < kMixUnroll; ++u) wv[u] = ok[u] ? __ldg(A.col + x[u]) : 0;
-#pragma unroll
-            for (int u = 0; u < kMixUnroll; ++u) {
-                if (!ok[u]) continue;
-                const int32_t reg = sm.b.rreg[rr[u]];
-                const int32_t bb = reg & 0xffffff;
-                const int lb = reg >> 24;
-                const int32_t q = table_find(sm.fpw, sm.slots, sm.vals, bb, lb, wv[u]);
-                if (q >= 0) {
-                    atomicAdd(&sm.cnt[q], 1);
-                    atomicAdd(A.S + x[u], 1);
-                    atomicAdd(&sm.b.hit[sm.b.rseg[rr[u]]], 1);
-                }
+                ++own;
             }
         }
     }
+    if (own) atomicAdd(&sm.b.hit[sm.b.rseg[orun]], own);
 }
 
 // Probing of all runs of a batch: an even split of the items over the warps
