@@ -678,6 +678,10 @@ def main():
 
     def e2e_step():
         hh = ctypes_load(lib, rp_h, col_h, n, m, st_ptr)
+        if args.no_reorder:
+            rc = lib.ktruss_set_option(hh, kt.OPT_REORDER, 0)
+            if rc != 0:
+                raise kt.KtrussError(rc, "ktruss_set_option")
         rc = lib.ktruss_run(hh, args.K, mask_h.data_ptr(), sup_h.data_ptr(), kt.HOST, st_ptr)
         if rc != 0:
             raise kt.KtrussError(rc, "ktruss_run")
