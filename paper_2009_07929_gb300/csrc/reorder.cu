@@ -15,16 +15,24 @@
 //   2. vertices sorted stably by degree (radix sort of (deg, v)); rank r of v
 //      in that order is its new id (ties keep the old order); in a batch the
 //      sort key is (graph, degree), so that every graph keeps its vertex range;
-//   3. every edge (u, v) at input slot e becomes (min, max) of its new ids,
-//      keyed (row << 32 | col), sorted stably by key (radix sort), carrying e;
-//   4. row pointers from the sorted rows; the carried slots map every slot of
-//      the relabelled CSR back to its input edge, so outputs land in input
-//      order.
+//   3. every edge (u, v) at input slot e becomes (row, col) = (min, max) of
+//      its new ids, counted into its row; row pointers are the exclusive scan
+//      of the counts;
+//   4. every edge is placed in its row through a per-row atomic cursor
+//      (carrying e), then every row is sorted by column in on-chip memory:
+//      rows of up to 32 by a bitonic network across the lanes of a warp, rows
+//      of up to kRowCap by a bitonic sort in the warp's shared memory, and the
+//      few longer rows, gathered into one list, by the radix sort below.  The
+//      columns of a row are distinct, so the result does not depend on the
+//      order in which the cursor placed them.  The carried slots map every
+//      slot of the relabelled CSR back to its input edge, so outputs land in
+//      input order.
 //
-// Radix sort: least significant digit first, 8-bit digits, one pass = a
-// per-tile digit histogram, an exclusive scan of the digit-major counts, and
-// a stable scatter: a tile of 4096 elements is split over 8 warps in order,
-// each warp walks its 512 elements 32 at a time and ranks equal digits with
+// Radix sort (the vertex order, and the rows longer than kRowCap): least
+// significant digit first, 8-bit digits, one pass = a per-tile digit
+// histogram, an exclusive scan of the digit-major counts, and a stable
+// scatter: a tile of 4096 elements is split over 8 warps in order, each warp
+// walks its 512 elements 32 at a time and ranks equal digits with
 // __match_any_sync, after the counts of the warps before it were added.
 #include <cstdint>
 
@@ -246,48 +254,214 @@ __global__ void max_kernel(const uint32_t *__restrict__ a, int64_t count, uint32
     if ((threadIdx.x & 31) == 0 && v) atomicMax(mx, v);
 }
 
-// key[e] = (min << 32) | max of the new ids of edge e's ends; val[e] = e.  A
-// thread takes 16 consecutive slots: the row of the first by binary search,
-// then row by row.
-constexpr int kKeySlots = 16;
-__global__ void edge_key_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
-                                int32_t n, int64_t m, const int32_t *__restrict__ newid,
-                                uint64_t *__restrict__ key, int32_t *__restrict__ val) {
-    const int64_t span = int64_t(gridDim.x) * blockDim.x * kKeySlots;
-    for (int64_t e0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) * kKeySlots; e0 < m;
-         e0 += span) {
-        int32_t lo = 0, hi = n - 1;
-        while (lo < hi) {
-            const int32_t mid = lo + ((hi - lo + 1) >> 1);
-            if (rp[mid] <= e0) lo = mid; else hi = mid - 1;
-        }
-        int32_t row = lo;
-        int64_t rend = rp[row + 1];
-        uint32_t a = uint32_t(newid[row]);
-        const int64_t e1 = e0 + kKeySlots < m ? e0 + kKeySlots : m;
-        for (int64_t e = e0; e < e1; ++e) {
-            while (e >= rend) {  // next non-empty row
-                ++row;
+// Largest i in [lo, hi] with a[i] <= x (a non-decreasing, a[lo] <= x).
+__device__ __forceinline__ int32_t last_le32(const int32_t *__restrict__ a, int32_t lo,
+                                             int32_t hi, int64_t x) {
+    while (lo < hi) {
+        const int32_t mid = lo + ((hi - lo + 1) >> 1);
+        if (a[mid] <= x) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Largest r in [0, n - 1] with rp[r] <= v (rp[0] = 0 <= v), found by the
+// whole warp: each pass probes 32 evenly spaced rows and keeps the gap between
+// the last probe at or below v and the first above it.  All lanes pass the
+// same v.
+__device__ __forceinline__ int32_t warp_row_of(const int32_t *__restrict__ rp, int32_t n,
+                                               int64_t v) {
+    const int lane = threadIdx.x & 31;
+    int64_t lo = 0, hi = int64_t(n) - 1;
+    while (hi - lo >= 32) {
+        const int64_t step = (hi - lo + 31) >> 5;
+        const int64_t p = min(lo + int64_t(lane + 1) * step, hi);
+        const int c = __popc(__ballot_sync(0xffffffffu, rp[p] <= v));
+        const int64_t nlo = c > 0 ? min(lo + int64_t(c) * step, hi) : lo;
+        const int64_t nhi = c < 32 ? min(lo + int64_t(c + 1) * step, hi) - 1 : hi;
+        lo = nlo;
+        hi = nhi;
+    }
+    const int64_t p = lo + lane;
+    const bool le = p <= hi && rp[p] <= v;
+    return int32_t(lo + __popc(__ballot_sync(0xffffffffu, le)) - 1);
+}
+
+// key[e] = (row << 32) | col of edge e in the new ids (row = the smaller end)
+// and rowcnt[row] += 1.  A warp takes windows of kKeyWin consecutive slots,
+// lane l the slots l, l + 32, ... (coalesced reads and writes); the window's
+// first row comes from a warp search, a lane's later rows from a forward
+// galloping search.
+constexpr int kKeyWin = 256;
+__global__ void __launch_bounds__(256)
+edge_key_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, int32_t n,
+                int64_t m, const int32_t *__restrict__ newid, uint64_t *__restrict__ key,
+                int32_t *__restrict__ rowcnt) {
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t base = gw * kKeyWin; base < m; base += nw * kKeyWin) {
+        int32_t row = warp_row_of(rp, n, base);
+        int32_t rend = rp[row + 1];
+        int32_t a = newid[row];
+        for (int j = 0; j < kKeyWin / 32; ++j) {
+            const int64_t e = base + lane + 32 * j;
+            if (e >= m) break;
+            if (rend <= e) {
+                // rows row+1 .. are at or below e: gallop to a bound above it
+                int64_t lo = row + 1, step = 1, hi = lo + 1;
+                while (hi <= n - 1 && rp[hi] <= e) {
+                    lo = hi;
+                    step <<= 1;
+                    hi = lo + step;
+                }
+                row = last_le32(rp, int32_t(lo), int32_t(min(hi - 1, int64_t(n) - 1)), e);
                 rend = rp[row + 1];
-                a = uint32_t(newid[row]);
+                a = newid[row];
             }
-            const uint32_t b = uint32_t(newid[col[e]]);
-            key[e] = a < b ? (uint64_t(a) << 32) | b : (uint64_t(b) << 32) | a;
-            val[e] = int32_t(e);
+            const int32_t b = newid[col[e]];
+            const int32_t lo = a < b ? a : b, hi = a < b ? b : a;
+            key[e] = (uint64_t(uint32_t(lo)) << 32) | uint32_t(hi);
+            atomicAdd(rowcnt + lo, 1);
         }
     }
 }
 
-// Relabelled CSR from the sorted keys: col, input slot, per-row counts.
-__global__ void csr_fill_kernel(const uint64_t *__restrict__ key, const int32_t *__restrict__ val,
-                                int64_t m, int32_t *__restrict__ col_out,
-                                int32_t *__restrict__ eid_out, int32_t *__restrict__ rowcnt) {
+// Places edge e in its row: the next free slot of the row (cursor[row],
+// starting at the row's first slot), with its column and input slot.
+__global__ void edge_place_kernel(const uint64_t *__restrict__ key, int64_t m,
+                                  int32_t *__restrict__ cursor, int32_t *__restrict__ col_out,
+                                  int32_t *__restrict__ eid_out) {
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < m; e += stride) {
         const uint64_t k = key[e];
-        col_out[e] = int32_t(uint32_t(k));
-        eid_out[e] = val[e];
-        atomicAdd(rowcnt + int32_t(k >> 32), 1);
+        const int32_t pos = atomicAdd(cursor + int32_t(k >> 32), 1);
+        col_out[pos] = int32_t(uint32_t(k));
+        eid_out[pos] = int32_t(e);
+    }
+}
+
+// Sorts every row of (col, eid) of length 2 .. kRowCap by column, in place.
+// A warp reads the lengths of 32 consecutive rows and sorts them one after
+// the other: a row of up to 32 in registers (one element per lane, a bitonic
+// network over lane shuffles), a longer one in the warp's shared array (a
+// bitonic sort over the next power of two, padded with the largest key).
+// Elements are packed (column << 32 | input slot); columns of a row are
+// distinct, so the packed order is the column order.
+constexpr int kRowCap = 1024;
+constexpr int kRowWarps = 4;
+__global__ void __launch_bounds__(32 * kRowWarps)
+row_sort_kernel(const int32_t *__restrict__ rp, int32_t n, int32_t *__restrict__ col,
+                int32_t *__restrict__ eid) {
+    __shared__ uint64_t sk[kRowWarps][kRowCap];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t gw = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    uint64_t *a = sk[w];
+    for (int64_t r0 = gw * 32; r0 < n; r0 += nw * 32) {
+        const int64_t r = r0 + lane;
+        int32_t b = 0, L = 0;
+        if (r < n) {
+            b = rp[r];
+            L = rp[r + 1] - b;
+        }
+        unsigned todo = __ballot_sync(0xffffffffu, L >= 2 && L <= kRowCap);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1u;
+            const int32_t rb = __shfl_sync(0xffffffffu, b, src);
+            const int32_t rl = __shfl_sync(0xffffffffu, L, src);
+            if (rl <= 32) {
+                uint64_t v = ~0ull;
+                if (lane < rl) v = (uint64_t(uint32_t(col[rb + lane])) << 32) | uint32_t(eid[rb + lane]);
+#pragma unroll
+                for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+                    for (int j = k >> 1; j > 0; j >>= 1) {
+                        const uint64_t o = __shfl_xor_sync(0xffffffffu, v, j);
+                        const bool keep_min = ((lane & j) == 0) == ((lane & k) == 0);
+                        v = keep_min ? (o < v ? o : v) : (o > v ? o : v);
+                    }
+                }
+                if (lane < rl) {
+                    col[rb + lane] = int32_t(uint32_t(v >> 32));
+                    eid[rb + lane] = int32_t(uint32_t(v));
+                }
+            } else {
+                int P = 64;
+                while (P < rl) P <<= 1;
+                for (int i = lane; i < P; i += 32)
+                    a[i] = i < rl ? (uint64_t(uint32_t(col[rb + i])) << 32) | uint32_t(eid[rb + i])
+                                  : ~0ull;
+                __syncwarp();
+                for (int k = 2; k <= P; k <<= 1) {
+                    for (int j = k >> 1; j > 0; j >>= 1) {
+                        for (int i = lane; i < (P >> 1); i += 32) {
+                            const int lo = ((i & ~(j - 1)) << 1) | (i & (j - 1));
+                            const int hi = lo + j;
+                            const uint64_t x = a[lo], y = a[hi];
+                            if ((x > y) == ((lo & k) == 0)) {
+                                a[lo] = y;
+                                a[hi] = x;
+                            }
+                        }
+                        __syncwarp();
+                    }
+                }
+                for (int i = lane; i < rl; i += 32) {
+                    const uint64_t v = a[i];
+                    col[rb + i] = int32_t(uint32_t(v >> 32));
+                    eid[rb + i] = int32_t(uint32_t(v));
+                }
+                __syncwarp();
+            }
+        }
+    }
+}
+
+// lcount[r] = length of row r if it is longer than kRowCap, else 0 (r < n);
+// lcount[n] = 0.
+__global__ void long_count_kernel(const int32_t *__restrict__ rp, int32_t n,
+                                  int32_t *__restrict__ lcount) {
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r <= n; r += stride) {
+        const int32_t L = r < n ? rp[r + 1] - rp[r] : 0;
+        lcount[r] = L > kRowCap ? L : 0;
+    }
+}
+
+// The rows longer than kRowCap, in row order, as (row << 32 | col, input
+// slot) at their offsets loff[row] of one list.
+__global__ void long_gather_kernel(const int32_t *__restrict__ rp, int32_t n,
+                                   const int32_t *__restrict__ loff,
+                                   const int32_t *__restrict__ col,
+                                   const int32_t *__restrict__ eid, uint64_t *__restrict__ key,
+                                   int32_t *__restrict__ val) {
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < n; r += stride) {
+        const int32_t b = rp[r], L = rp[r + 1] - b;
+        if (L <= kRowCap) continue;
+        const int32_t o = loff[r];
+        for (int32_t i = 0; i < L; ++i) {
+            key[o + i] = (uint64_t(uint32_t(r)) << 32) | uint32_t(col[b + i]);
+            val[o + i] = eid[b + i];
+        }
+    }
+}
+
+// Writes the sorted list back: element i of row r goes to the row's slot
+// i - loff[r] (rows keep their extents in the list, sorted by row first).
+__global__ void long_scatter_kernel(const uint64_t *__restrict__ key,
+                                    const int32_t *__restrict__ val, int64_t count,
+                                    const int32_t *__restrict__ rp,
+                                    const int32_t *__restrict__ loff, int32_t *__restrict__ col,
+                                    int32_t *__restrict__ eid) {
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < count; i += stride) {
+        const uint64_t k = key[i];
+        const int32_t r = int32_t(k >> 32);
+        const int64_t dst = rp[r] + (i - loff[r]);
+        col[dst] = int32_t(uint32_t(k));
+        eid[dst] = val[i];
     }
 }
 
@@ -435,25 +609,50 @@ cudaError_t launch_reorder(const int32_t *rp, const int32_t *col, int32_t n, int
         return e;
     }
     sort_layout(base, m, 8, int64_t(n) + 1, &es);
-    edge_key_kernel<<<grid_for((m + kKeySlots - 1) / kKeySlots, 256), 256, 0, st>>>(rp, col, n, m, newid,
-                                                      static_cast<uint64_t *>(es.keys[0]),
-                                                      es.vals[0]);
+    uint64_t *ekey = static_cast<uint64_t *>(es.keys[0]);
+    e = cudaMemsetAsync(rowcnt, 0, (size_t(n) + 1) * 4, st);
+    if (e != cudaSuccess) return e;
+    edge_key_kernel<<<grid_for((m + kKeyWin - 1) / kKeyWin * 32, 256), 256, 0, st>>>(
+        rp, col, n, m, newid, ekey, rowcnt);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // rp_out = exclusive scan of the row counts (n + 1 entries, the last is 0)
+    e = scan32(rowcnt, int64_t(n) + 1, rp_out, es.tsum, es.toff, st);
+    if (e != cudaSuccess) return e;
+    // 4: place every edge in its row (rowcnt turns into the per-row cursor),
+    // then sort the rows
+    e = cudaMemcpyAsync(rowcnt, rp_out, size_t(n) * 4, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return e;
+    edge_place_kernel<<<grid_for(m, 256), 256, 0, st>>>(ekey, m, rowcnt, col_out, eid_out);
+    row_sort_kernel<<<grid_for((int64_t(n) + 31) / 32 * 32, 32 * kRowWarps), 32 * kRowWarps, 0,
+                      st>>>(rp_out, n, col_out, eid_out);
+    // rows longer than kRowCap: one list (offsets loff in the cursor's memory,
+    // counts in the new ids' memory, both free now), sorted by (row, col)
+    int32_t *lcount = newid, *loff = rowcnt;
+    long_count_kernel<<<grid_for(int64_t(n) + 1, 256), 256, 0, st>>>(rp_out, n, lcount);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = scan32(lcount, int64_t(n) + 1, loff, es.tsum, es.toff, st);
+    int32_t total = 0;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&total, loff + n, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess || total == 0) return e;
+    long_gather_kernel<<<grid_for(n, 256), 256, 0, st>>>(rp_out, n, loff, col_out, eid_out,
+                                                        static_cast<uint64_t *>(es.keys[0]),
+                                                        es.vals[0]);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     const int vb = bits_for(uint64_t(n - 1));
     np = 0;
     for (int sh = 0; sh < vb; sh += 8) shifts[np++] = sh;        // column
     for (int sh = 0; sh < vb; sh += 8) shifts[np++] = 32 + sh;   // row
     cur = 0;
-    e = radix_sort<uint64_t>(es, m, shifts, np, &cur, st);
+    e = radix_sort<uint64_t>(es, total, shifts, np, &cur, st);
     if (e != cudaSuccess) return e;
-    // 4: CSR
-    e = cudaMemsetAsync(rowcnt, 0, (size_t(n) + 1) * 4, st);
-    if (e != cudaSuccess) return e;
-    csr_fill_kernel<<<grid_for(m, 256), 256, 0, st>>>(static_cast<const uint64_t *>(es.keys[cur]),
-                                                      es.vals[cur], m, col_out, eid_out, rowcnt);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    // rp_out = exclusive scan of the row counts (n + 1 entries, the last is 0)
-    return scan32(rowcnt, int64_t(n) + 1, rp_out, es.tsum, es.toff, st);
+    long_scatter_kernel<<<grid_for(total, 256), 256, 0, st>>>(
+        static_cast<const uint64_t *>(es.keys[cur]), es.vals[cur], total, rp_out, loff, col_out,
+        eid_out);
+    return cudaGetLastError();
 }
 
 }  // namespace kt

@@ -667,6 +667,37 @@ def test_reorder_on_and_off_match_oracle(kt, kernel):
                 assert np.array_equal(tr.cpu().numpy(), oracle.truss_decomposition(g.row_ptr, g.col))
 
 
+def test_relabel_rows_longer_than_on_chip_sort(kt):
+    """The relabel at load sorts rows of up to 1024 columns on chip and the
+    longer ones through one radix-sorted list.  Two planted cliques of 1100
+    and 1300 vertices in an R-MAT graph leave 350 relabelled rows above that
+    size: the runs from the relabel equal the oracle (K = 3 and K = 1100), and
+    the complete graph K_1100 (rows up to 1099) gives its closed form: every
+    edge in K_1100 - 2 = 1098 triangles, the whole graph the 1100-truss and
+    none of it the 1101-truss."""
+    import torch
+    g = gg.rmat(12, 8, seed=3, n_cliques=2, clique_lo=1100, clique_hi=1300)
+    for K in (3, 1100):
+        r = oracle.ktruss(g.row_ptr, g.col, K)
+        h = kt.load(torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col).cuda())
+        m_t, s_t = h.run(K)
+        torch.cuda.synchronize()
+        st = h.stats()
+        h.close()
+        assert np.array_equal(m_t.cpu().numpy(), r.mask), K
+        assert np.array_equal(s_t.cpu().numpy(), r.support), K
+        assert st.rounds == r.rounds and st.removed_per_round == r.removed_per_round, K
+    kn = gg.complete(1100)
+    h = kt.load(torch.from_numpy(kn.row_ptr).cuda(), torch.from_numpy(kn.col).cuda())
+    m_t, s_t = h.run(1100)
+    torch.cuda.synchronize()
+    assert bool((m_t == 1).all()) and bool((s_t == 1098).all())
+    m_t, s_t = h.run(1101)
+    torch.cuda.synchronize()
+    assert bool((m_t == 0).all()) and bool((s_t == 0).all())
+    h.close()
+
+
 # ------------------------------------------------ device-driven round loop
 
 def _run_loop(kt, g, K, loop, update):
