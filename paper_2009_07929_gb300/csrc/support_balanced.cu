@@ -48,7 +48,7 @@ namespace {
 
 // ----------------------------------------------------------- configuration
 #ifndef KT_SUPPORT_UNROLL
-#define KT_SUPPORT_UNROLL 4
+#define KT_SUPPORT_UNROLL 5
 #endif
 constexpr int kStageRows = 256;         // staged rows per stage
 constexpr int kUnroll = KT_SUPPORT_UNROLL;  // 32-item windows in flight per warp

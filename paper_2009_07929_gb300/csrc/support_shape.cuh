@@ -122,15 +122,15 @@ __device__ __forceinline__ void build_runs(SupportSmem &sm, int32_t len, int32_t
 // item (runs are consecutive in item space, so a lane only moves forward,
 // crossing a run start when its item passes it) and keeps that run's probe
 // offset and region in registers, so a window costs the same whether it lies
-// inside one run or spans several.  A lane counts the hits of its current run
-// and adds them to the run's owner in shared memory when it moves to a run
-// with hits of its own, and at the end.
+// inside one run or spans several.  Every hit adds one to the staged slot's
+// shared counter, to S at the probe position and to its run owner's shared
+// counter (a per-lane count carried across windows cost more registers than
+// the shared atomic it saves).
 __device__ __forceinline__ void probe_range(const SupportArgs &A, SupportSmem &sm, int32_t nruns,
                                             int32_t items, int32_t E, int32_t p, int32_t pe) {
     const int lane = threadIdx.x & 31;
     int32_t r = E, rnext = sm.b.rstart[E + 1];  // rstart[nruns] == items
     int32_t del = sm.b.rdel[E], reg = sm.b.rreg[E];
-    int32_t orun = E, own = 0;
     for (; p < pe; p += 32 * kUnroll) {
         int32_t xv[kUnroll], gv[kUnroll], rv[kUnroll], wv[kUnroll];
 #pragma unroll
@@ -163,16 +163,10 @@ __device__ __forceinline__ void probe_range(const SupportArgs &A, SupportSmem &s
             if (q >= 0) {
                 atomicAdd(&sm.cnt[q], 1);
                 atomicAdd(A.S + xv[u], 1);
-                if (rv[u] != orun) {
-                    if (own) atomicAdd(&sm.b.hit[sm.b.rseg[orun]], own);
-                    orun = rv[u];
-                    own = 0;
-                }
-                ++own;
+                atomicAdd(&sm.b.hit[sm.b.rseg[rv[u]]], 1);
             }
         }
     }
-    if (own) atomicAdd(&sm.b.hit[sm.b.rseg[orun]], own);
 }
 
 // Probing of all runs of a batch: an even split of the items over the warps
