@@ -774,6 +774,7 @@ def main():
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tot_ms / args.steps, 4),
+        "ms_per_step_median": round(float(np.median(step_ms)), 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC[args.workload] + f", K={args.K}", "K": args.K,
