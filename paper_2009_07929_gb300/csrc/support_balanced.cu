@@ -489,14 +489,14 @@ __global__ void active_rows_kernel(const int32_t *__restrict__ rcount,
     if (r == 0) aseg[tot->b] = tot->a;
 }
 
-// Counting-sort scatter of the segments by staged row (consumes rcount);
-// also records each segment's active-row rank.
+// Counting-sort scatter of the segments by staged row (consumes rcount).  A
+// segment is one 16-byte record (owner slot, probe start, item count,
+// active-row rank of its staged row), so its scatter is one random write.
 __global__ void scatter_kernel(const int32_t *__restrict__ ekey, const int32_t *__restrict__ epst,
                                const int32_t *__restrict__ eitems, int32_t m,
                                const int32_t *__restrict__ rstart,
                                const int32_t *__restrict__ arank, int32_t *__restrict__ rcount,
-                               int32_t *__restrict__ seg, int32_t *__restrict__ pst,
-                               int32_t *__restrict__ sitems, int32_t *__restrict__ sact) {
+                               int4 *__restrict__ srec) {
     const int lane = threadIdx.x & 31;
     const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const int32_t key = e < m ? ekey[e] : -1;
@@ -507,16 +507,13 @@ __global__ void scatter_kernel(const int32_t *__restrict__ ekey, const int32_t *
     if (lane == leader) old = atomicSub(rcount + key, __popc(peers));
     old = __shfl_sync(peers, old, leader);
     const int32_t pos = rstart[key] + old - 1 - __popc(peers & ((1u << lane) - 1u));
-    seg[pos] = int32_t(e);
-    pst[pos] = epst[e];
-    sitems[pos] = eitems[e];
-    sact[pos] = arank[key];
+    srec[pos] = make_int4(int32_t(e), epst[e], eitems[e], arank[key]);
 }
 
 struct ItemLoad {
-    const int32_t *sitems;
+    const int4 *srec;
     const Pair *tot;
-    __device__ long long operator()(int64_t i) const { return i < tot->a ? sitems[i] : 0; }
+    __device__ long long operator()(int64_t i) const { return i < tot->a ? srec[i].z : 0; }
 };
 struct ItemStore {
     long long *wp;
@@ -583,7 +580,11 @@ constexpr int kThreads = 512, kCap = 2048, kMinCtas = 3;
 size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Carve {
+    // seg, pst, sitems and sact are consecutive: the support step uses their
+    // memory as one array of 16-byte segment records (srec), the update as
+    // four int32 arrays
     int32_t *ekey, *epst, *eitems, *seg, *pst, *sitems, *sact;
+    int4 *srec;
     long long *wp;
     int32_t *rcount, *rstart, *arank, *arow, *aseg;
     Pair *rtile_sum, *rtile_off, *rtot;
@@ -611,6 +612,7 @@ size_t carve(void *base, int32_t n, int64_t m, Carve *c) {
     c->pst = reinterpret_cast<int32_t *>(take(size_t(m + 1) * 4));
     c->sitems = reinterpret_cast<int32_t *>(take(size_t(m + 1) * 4));
     c->sact = reinterpret_cast<int32_t *>(take(size_t(m + 1) * 4));
+    c->srec = reinterpret_cast<int4 *>(c->seg);
     c->wp = reinterpret_cast<long long *>(take(size_t(m + 2) * 8));
     c->rcount = reinterpret_cast<int32_t *>(take(size_t(n + 1) * 4));
     c->rstart = reinterpret_cast<int32_t *>(take(size_t(n + 1) * 4));
@@ -771,12 +773,11 @@ cudaError_t launch_support_balanced(const Live &g, int32_t *S, RoundCounters *cn
                                                                c.rtot, n, c.arow, c.aseg);
     trace_phase(s, "row scan + active rows");
     scatter_kernel<<<int((int64_t(m) + 255) / 256), 256, 0, s>>>(c.ekey, c.epst, c.eitems, m, c.rstart,
-                                                   c.arank, c.rcount, c.seg, c.pst, c.sitems,
-                                                   c.sact);
+                                                   c.arank, c.rcount, c.srec);
     trace_phase(s, "scatter");
     // item scan over the segments (at most m of them; entries past nseg are 0)
     const int32_t itiles = int32_t((int64_t(m) + kScanTile - 1) / kScanTile);
-    ItemLoad il{c.sitems, c.rtot};
+    ItemLoad il{c.srec, c.rtot};
     ItemStore is{c.wp};
     scan_reduce_kernel<long long, ItemLoad><<<itiles, kScanThreads, 0, s>>>(il, m, c.itile_sum,
                                                                           nullptr);
@@ -805,11 +806,11 @@ cudaError_t launch_support_balanced(const Live &g, int32_t *S, RoundCounters *cn
         if (e != cudaSuccess) return e;
     }
     if (shape == 0) {
-        shape0::SupportArgs A{g.rp, g.col, c.seg, c.pst, c.sact, c.wp, c.arow, c.aseg, c.plan,
+        shape0::SupportArgs A{g.rp, g.col, c.srec, c.wp, c.arow, c.aseg, c.plan,
                               c.bound, c.sched, S, &cnt->triangles, &cnt->error};
         shape0::support_kernel<<<blocks, shape0::kThreads, sizeof(shape0::SupportSmem), s>>>(A);
     } else {
-        shape1::SupportArgs A{g.rp, g.col, c.seg, c.pst, c.sact, c.wp, c.arow, c.aseg, c.plan,
+        shape1::SupportArgs A{g.rp, g.col, c.srec, c.wp, c.arow, c.aseg, c.plan,
                               c.bound, c.sched, S, &cnt->triangles, &cnt->error};
         shape1::support_kernel<<<blocks, shape1::kThreads, sizeof(shape1::SupportSmem), s>>>(A);
     }

@@ -44,7 +44,7 @@ static_assert(sizeof(SupportSmem) <= 227 * 1024, "support CTA exceeds shared mem
 
 struct SupportArgs {
     const int32_t *rp, *col;
-    const int32_t *seg, *pst, *sact;
+    const int4 *srec;  // segment records: owner slot, probe start, items, active-row rank
     const long long *wp;
     const int32_t *arow, *aseg;
     const ChunkPlan *plan;
@@ -267,7 +267,7 @@ __device__ void long_row(const SupportArgs &A, SupportSmem &sm, int32_t rbase, i
             const long long base = __ldg(A.wp + pos);
             const int32_t ka = int32_t(max(iA, base) - base);
             const int32_t kb = int32_t(min(iB, __ldg(A.wp + pos + 1)) - base);
-            const int32_t p0 = __ldg(A.pst + pos);
+            const int32_t p0 = __ldg(&A.srec[pos].y);
             sm.l.cur[j] = p0 + ka;
             sm.l.end[j] = p0 + max(ka, kb);
             sm.l.hit[j] = 0;
@@ -369,7 +369,7 @@ __device__ void long_row(const SupportArgs &A, SupportSmem &sm, int32_t rbase, i
         for (int32_t j = tid; j < nb; j += kThreads) {
             const int32_t v = sm.l.hit[j];
             if (v) {
-                atomicAdd(A.S + __ldg(A.seg + sb + j), v);
+                atomicAdd(A.S + __ldg(&A.srec[sb + j].x), v);
                 tri += v;
             }
         }
@@ -491,9 +491,10 @@ support_kernel(SupportArgs A) {
                     const int32_t ka = int32_t(max(iA, base) - base);
                     const int32_t kb = int32_t(min(iB, __ldg(A.wp + pos + 1)) - base);
                     len = kb - ka;
-                    pos0 = __ldg(A.pst + pos) + ka;
-                    key = __ldg(A.sact + pos) - a;
-                    sm.b.owner[tid] = __ldg(A.seg + pos);
+                    const int4 rec = __ldg(A.srec + pos);
+                    pos0 = rec.y + ka;
+                    key = rec.w - a;
+                    sm.b.owner[tid] = rec.x;
                     sm.b.hit[tid] = 0;
                 }
                 int32_t nruns, items;
