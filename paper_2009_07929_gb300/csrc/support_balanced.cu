@@ -362,9 +362,35 @@ scan_apply_kernel(Load ld, Store st, int64_t count, const V *__restrict__ tile_o
 }
 
 // --------------------------------------------------------- balance kernels
+// Largest r in [0, n - 1] with rp[r] <= v (rp non-decreasing, rp[0] = 0 <= v),
+// found by the whole warp: every pass probes 32 evenly spaced rows and keeps
+// the gap between the last probe at or below v and the first above it.  All
+// lanes pass the same v and get the same row.
+__device__ __forceinline__ int32_t warp_row_of(const int32_t *__restrict__ rp, int32_t n,
+                                               int64_t v) {
+    const int lane = threadIdx.x & 31;
+    int64_t lo = 0, hi = int64_t(n) - 1;
+    while (hi - lo >= 32) {
+        const int64_t step = (hi - lo + 31) >> 5;
+        const int64_t p = min(lo + int64_t(lane + 1) * step, hi);
+        const int c = __popc(__ballot_sync(0xffffffffu, __ldg(rp + p) <= v));
+        const int64_t nlo = c > 0 ? min(lo + int64_t(c) * step, hi) : lo;
+        const int64_t nhi = c < 32 ? min(lo + int64_t(c + 1) * step, hi) - 1 : hi;
+        lo = nlo;
+        hi = nhi;
+    }
+    const int64_t p = lo + lane;
+    const bool le = p <= hi && __ldg(rp + p) <= v;
+    return int32_t(lo + __popc(__ballot_sync(0xffffffffu, le)) - 1);
+}
+
 // Per live edge: staged row, probe start and item count; per staged row: the
-// number of segments; per round: the merge work sum(t + d).  Counts of equal
-// staged rows within a warp are aggregated into one atomic.
+// number of segments; per round: the merge work sum(t + d).  A warp takes a
+// window of kClassWin consecutive slots, lane l the slots l, l + 32, ... (so
+// loads and stores are coalesced); the window's first row comes from a warp
+// search, a lane's later rows from a forward galloping search.  Counts of
+// equal staged rows within a warp are aggregated into one atomic.
+constexpr int kClassWin = 32 * kEdgesPerThread;
 __global__ void __launch_bounds__(kEdgeThreads)
 classify_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, int32_t n,
                 int32_t m, int32_t *__restrict__ ekey, int32_t *__restrict__ epst,
@@ -373,33 +399,47 @@ classify_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
                 const uint8_t *__restrict__ skip, int32_t light) {
     __shared__ long long part[kEdgeThreads / 32];
     const int lane = threadIdx.x & 31;
-    const int64_t e0 = (int64_t(blockIdx.x) * kEdgeThreads + threadIdx.x) * kEdgesPerThread;
+    const int64_t base = (int64_t(blockIdx.x) * (kEdgeThreads / 32) + (threadIdx.x >> 5)) *
+                         kClassWin;
     long long merge = 0;
-    RowWalk rw{0, 0, 0};
-    if (e0 < m) rw.start(rp, n, int32_t(e0));
+    if (base < m) {  // warp-uniform
+        int32_t row = warp_row_of(rp, n, base);
+        int32_t rend = __ldg(rp + row + 1);
 #pragma unroll 1
-    for (int j = 0; j < kEdgesPerThread; ++j) {
-        const int64_t e = e0 + j;
-        int32_t key = -1;
-        if (e < m) {
-            rw.advance(rp, n, int32_t(e));
-            const int32_t kappa = __ldg(col + e);
-            const int32_t kb = __ldg(rp + kappa);
-            const int32_t d = __ldg(rp + kappa + 1) - kb;
-            const int32_t t = rw.rend - int32_t(e) - 1;
-            const bool skipped = skip && skip[gid[rw.row]];
-            if (!skipped) merge += (long long)t + d;
-            const int32_t items = (skipped || light_task(t, d, light)) ? 0 : min(t, d);
-            if (items > 0) {
-                const bool stage_kappa = t < d;
-                key = stage_kappa ? kappa : rw.row;
-                epst[e] = stage_kappa ? int32_t(e) + 1 : kb;
+        for (int j = 0; j < kEdgesPerThread; ++j) {
+            const int64_t e = base + lane + 32 * j;
+            int32_t key = -1;
+            if (e < m) {
+                if (rend <= e) {
+                    // rows row+1 .. are at or below e: gallop to a bound above it
+                    int64_t lo = row + 1, step = 1, hi = lo + 1;
+                    while (hi <= n - 1 && __ldg(rp + hi) <= e) {
+                        lo = hi;
+                        step <<= 1;
+                        hi = lo + step;
+                    }
+                    row = last_le(rp, int32_t(lo), int32_t(min(hi - 1, int64_t(n) - 1)),
+                                  int32_t(e));
+                    rend = __ldg(rp + row + 1);
+                }
+                const int32_t kappa = __ldg(col + e);
+                const int32_t kb = __ldg(rp + kappa);
+                const int32_t d = __ldg(rp + kappa + 1) - kb;
+                const int32_t t = rend - int32_t(e) - 1;
+                const bool skipped = skip && skip[gid[row]];
+                if (!skipped) merge += (long long)t + d;
+                const int32_t items = (skipped || light_task(t, d, light)) ? 0 : min(t, d);
+                if (items > 0) {
+                    const bool stage_kappa = t < d;
+                    key = stage_kappa ? kappa : row;
+                    epst[e] = stage_kappa ? int32_t(e) + 1 : kb;
+                }
+                ekey[e] = key;
+                eitems[e] = items;
             }
-            ekey[e] = key;
-            eitems[e] = items;
+            const uint32_t peers = __match_any_sync(0xffffffffu, key);
+            if (key >= 0 && lane == __ffs(peers) - 1) atomicAdd(rcount + key, __popc(peers));
         }
-        const uint32_t peers = __match_any_sync(0xffffffffu, key);
-        if (key >= 0 && lane == __ffs(peers) - 1) atomicAdd(rcount + key, __popc(peers));
     }
     merge = warp_sum_ll(merge);
     if (lane == 0) part[threadIdx.x >> 5] = merge;
