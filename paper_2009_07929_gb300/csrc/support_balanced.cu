@@ -216,13 +216,14 @@ __device__ __forceinline__ bool table_insert(uint32_t *fpw, uint16_t *slots, int
     return false;  // region full: cannot happen at load factor <= 1/4
 }
 
-// Local slot of column w in the region (bbase, lb), or -1.
+// Local slot of column w in the region starting at bucket bbase with
+// 2^(32 - sh) buckets (sh: the bucket shift of the hash), or -1.
 __device__ __forceinline__ int32_t table_find(const uint32_t *fpw, const uint16_t *slots,
-                                              const int32_t *vals, int32_t bbase, int lb,
+                                              const int32_t *vals, int32_t bbase, int sh,
                                               int32_t w) {
-    const uint32_t bm = (1u << lb) - 1u;
+    const uint32_t bm = 0xffffffffu >> sh;
     const uint32_t fp4 = fingerprint(w) * 0x01010101u;
-    uint32_t b = (uint32_t(w) * kHashMul) >> (32 - lb);
+    uint32_t b = (uint32_t(w) * kHashMul) >> sh;
     for (;;) {
         const int32_t at = bbase + int32_t(b);
         const uint32_t word = fpw[at];

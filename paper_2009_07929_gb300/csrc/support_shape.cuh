@@ -27,7 +27,7 @@ struct SupportSmem {
             int32_t hit[kBatch];      // batch: hits credited to segment j's owner
             int32_t rstart[kBatch + 1];  // runs: batch-local item offset of run r
             int32_t rdel[kBatch];     // runs: probe position of item i of run r is rdel[r] + i
-            int32_t rreg[kBatch];     // runs: region probed (first bucket | log2 buckets << 24)
+            int32_t rreg[kBatch];     // runs: region probed (region_word)
             int32_t rseg[kBatch];     // runs: segment of run r
         } b;
         struct {                      // long rows: segment j of the current batch
@@ -84,9 +84,11 @@ __device__ __forceinline__ unsigned long long block_excl_scan(unsigned long long
     return before + incl - v;
 }
 
-// Region word of a staged row: first bucket in the low 24 bits, log2 of the
-// bucket count above.
-__device__ __forceinline__ int32_t region_word(int32_t bbase, int lb) { return bbase | (lb << 24); }
+// Region word of a staged row: first bucket in the low 24 bits, the region's
+// bucket shift (32 - log2 of its bucket count) above.
+__device__ __forceinline__ int32_t region_word(int32_t bbase, int lb) {
+    return bbase | ((32 - lb) << 24);
+}
 
 // Builds the run list from per-thread (len, pos, reg, seg) proposals: runs of
 // positive length in thread order, each with its position offset and the
