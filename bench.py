@@ -359,8 +359,11 @@ def measure_batched(kt, gg, count, m_hi, seed=0, autotune=True):
     every graph preloaded into its own handle, then one ktruss_run per graph.
     Batched: the block-diagonal batch preloaded into one handle, then one
     ktruss_run_batch.  Both timed with CUDA events, graphs resident in HBM.
-    With autotune, ktruss_autotune picks the settings on the batch first and
-    both arms run with them."""
+    The plain arm runs with the library's defaults (what a caller running one
+    graph at a time gets); with autotune, ktruss_autotune picks the batch
+    arm's settings on the batch first (settings tuned for one batch of 4096
+    graphs are not the best ones for each graph alone: a per-edge/balanced
+    threshold tuned on the batch slowed the plain arm by a third)."""
     import torch
     progress(f"batched: generating {count} graphs, m up to {m_hi:g}")
     batch = gg.batch_config(count, seed=seed, m_lo=1e3, m_hi=m_hi)
@@ -374,7 +377,7 @@ def measure_batched(kt, gg, count, m_hi, seed=0, autotune=True):
     if autotune:
         # the library's autotuner picks the support kernel's CTA shape, the
         # merge/probe threshold, the per-edge/balanced threshold and the
-        # update rule on the batch; both arms then run with those settings
+        # update rule on the batch, for the batch arm
         progress("batched: autotuning on the batch")
         hb = kt.load_batch(vertex_offsets=vo, row_ptr=torch.from_numpy(rp).to(dev),
                            col=torch.from_numpy(col).to(dev))
@@ -391,7 +394,7 @@ def measure_batched(kt, gg, count, m_hi, seed=0, autotune=True):
 
     progress(f"batched: {edges} edges generated; loading plain handles")
     # plain
-    handles = [apply(kt.load(torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col).to(dev)))
+    handles = [kt.load(torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col).to(dev))
                for g in graphs]
     outs = [(torch.empty(max(g.m, 1), dtype=torch.uint8, device=dev)[:g.m],
              torch.empty(max(g.m, 1), dtype=torch.int32, device=dev)[:g.m]) for g in graphs]
@@ -431,6 +434,7 @@ def measure_batched(kt, gg, count, m_hi, seed=0, autotune=True):
             "speedup": round(plain_ms / batch_ms, 2), "batch_ms": round(batch_ms, 3),
             "plain_ms": round(plain_ms, 3), "batch_rounds": int(brounds),
             "max_graph_rounds": int(max(rounds)) if len(rounds) else 0,
+            "plain_settings": "library defaults",
             "autotuned": ({k: tune[k] for k in ("support_shape", "light_merge", "small_edges",
                                                   "update_mode", "trials")}
                           if tune is not None else None)}
