@@ -602,7 +602,7 @@ cudaError_t launch_reorder(const int32_t *rp, const int32_t *col, int32_t n, int
     }
     if (e != cudaSuccess) return e;
     rank_kernel<<<grid_for(n, 256), 256, 0, st>>>(vs.vals[cur], n, newid);
-    // 3: edges keyed by (new row, new col), sorted, carrying the input slot
+    // 3: every edge keyed by (new row, new col) and counted into its new row
     e = cudaGetLastError();
     if (e != cudaSuccess || m == 0) {
         if (e == cudaSuccess) e = cudaMemsetAsync(rp_out, 0, (size_t(n) + 1) * 4, st);
